@@ -1,0 +1,97 @@
+/*
+ * CPU oracle for exact butterfly counting (Wang, Lin, Qin, Zhang, Zhang,
+ * "Efficient Butterfly Counting for Large Bipartite Networks").
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the
+ * benchmark's CPU-baseline arm may load this library.  It shares no code,
+ * header, table or helper with the CUDA path; the two meet only through the
+ * seeded input generators.
+ *
+ * Every routine takes the U-side CSR of a simple bipartite graph:
+ *   r = |U|, l = |L|, off[r+1] (int32, off[0] = 0, off[r] = m), adj[m]
+ *   (int32 L-ids).  The edge at U-side slot k has edge id k.
+ * Outputs are caller-owned host arrays.  Return 0 on success, -1 on a
+ * malformed graph (bad offsets, ids out of range, duplicate edges), -2 on
+ * allocation failure.
+ *
+ * Parity status: every function below is pinned by tests against closed
+ * forms, the paper's worked examples, exhaustive enumeration on tiny graphs
+ * or cross-agreement with an independent definition (see tests/).
+ */
+#ifndef BFC_ORACLE_H
+#define BFC_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Definition 2 + Lemma 1 (Eq. 1, Eq. 2): for every unordered pair {x, y} of
+ * the chosen layer, c = |N(x) ∩ N(y)| by merging sorted lists; the total is
+ * the sum of C(c,2).  pair_layer: 0 = pairs of U vertices, 1 = pairs of L.
+ * O(|layer|^2 * d); for small graphs only. */
+int orc_brute_total(int32_t r, int32_t l, const int32_t *off, const int32_t *adj,
+                    int pair_layer, uint64_t *total);
+
+/* Eq. 1 for every vertex: ⋈_x = Σ_{y ≠ x in x's layer} C(|N(x) ∩ N(y)|, 2).
+ * pv_u[r], pv_l[l]. */
+int orc_brute_vertices(int32_t r, int32_t l, const int32_t *off, const int32_t *adj,
+                       uint64_t *pv_u, uint64_t *pv_l);
+
+/* Eq. 7 for every edge e = (u, v): ⋈_e = Σ_{w ∈ N(v), w ≠ u} (|N(u) ∩ N(w)| − 1),
+ * summed only over w that share at least one more neighbour with u (terms
+ * with |N(u) ∩ N(w)| = 1 contribute 0).  pe[m] in U-side slot order. */
+int orc_brute_edges(int32_t r, int32_t l, const int32_t *off, const int32_t *adj,
+                    uint64_t *pe);
+
+/* Algorithm 1 (BFC-IBS, layer priority).  The start layer S is U unless
+ * Σ_U deg² < Σ_L deg², in which case S = L; wedges (u, v, w) with
+ * w.id > u.id are hashed per start; total = Σ C(count, 2).  *wedges = number
+ * of wedges that pass the id filter.  *start_layer = 0 (U) or 1 (L). */
+int orc_ibs(int32_t r, int32_t l, const int32_t *off, const int32_t *adj,
+            uint64_t *total, uint64_t *wedges, int *start_layer);
+
+/* Definition 3 (priority) with global ids gid(v ∈ L) = v, gid(u ∈ U) = l + u,
+ * and Definition 4 (projection): rank_u[u] ∈ [0, r), rank_l[v] ∈ [0, l) are
+ * the per-layer ranks of the priority, 0 = lowest.  prio[n] (optional, may be
+ * NULL) receives p(x) ∈ [1, n] indexed by gid. */
+int orc_priority(int32_t r, int32_t l, const int32_t *off, const int32_t *adj,
+                 int32_t *rank_u, int32_t *rank_l, int32_t *prio);
+
+/* The projection graph G* (Definition 4) with every neighbour list sorted
+ * ascending by priority, in the unified id space of G*: L vertex v has id
+ * rank_l[v], U vertex u has id l + rank_u[u].  Outputs (n = r + l):
+ *   poff[n+1] (int64), padj[2m], peid[2m] (U-side slot of each entry),
+ *   cut[n]  = |{y ∈ N(x) : p(y) < p(x)}|,
+ *   work[n] = |{(y, z) : y ∈ N(x), p(y) < p(x), z ∈ N(y), p(z) < p(x)}|,
+ *             the wedges Algorithm 2 processes from start x. */
+int orc_projection(int32_t r, int32_t l, const int32_t *off, const int32_t *adj,
+                   int64_t *poff, int32_t *padj, int32_t *peid, int32_t *cut,
+                   uint64_t *work);
+
+/* Algorithm 2 (BFC-VP), run in parallel as Algorithm 5 prescribes: starts in
+ * non-ascending priority, handed dynamically to `threads` workers (OpenMP),
+ * each with its own dense count_wedge array and partial sum.
+ *   total  : ⋈_G
+ *   wedges : processed wedges (may be NULL)
+ *   pv_u/pv_l (may be NULL): per-vertex counts; pe (may be NULL): per-edge
+ *            counts in U-side slot order.  These take a second walk over the
+ *            same wedges, reading the final count_wedge of each end vertex.
+ * threads <= 0 uses the OpenMP default. */
+int orc_vp(int32_t r, int32_t l, const int32_t *off, const int32_t *adj, int threads,
+           uint64_t *total, uint64_t *wedges, uint64_t *pv_u, uint64_t *pv_l, uint64_t *pe);
+
+/* Algorithm 3 (BFC-VP++): projection, neighbour lists in descending
+ * priority, wedges whose end vertex has the highest priority, early break.
+ * Single thread.  *wedges = processed wedges. */
+int orc_vppp(int32_t r, int32_t l, const int32_t *off, const int32_t *adj,
+             uint64_t *total, uint64_t *wedges);
+
+/* Σ_{(u,v) ∈ E} min(deg u, deg v) (Lemma 3), Σ_U deg², Σ_L deg². */
+int orc_degree_stats(int32_t r, int32_t l, const int32_t *off, const int32_t *adj,
+                     uint64_t *tc_new, uint64_t *sum_du2, uint64_t *sum_dl2);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

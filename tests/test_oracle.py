@@ -1,0 +1,316 @@
+"""Pins for the CPU oracle: closed forms, the paper's worked examples,
+exhaustive enumeration on tiny graphs, and the identities the paper states.
+
+Nothing here touches a GPU.  Each pin is chosen so that a plausible slip in
+the oracle (a dropped term, a wrong comparison, a transposed layer, a wrong
+tie-break) makes at least one test fail.
+"""
+import hashlib
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from bfc_inputs import generators as G
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def c2(x):
+    return x * (x - 1) // 2
+
+
+# ---------------------------------------------------------------------------
+# the input generator itself
+# ---------------------------------------------------------------------------
+
+def test_splitmix64_published_vector():
+    # SplitMix64 from state 0: first output 0xE220A8397B1DCDAF (Steele et al.)
+    out = G.splitmix64_np(np.array([0], dtype=np.uint64), 0)
+    assert int(out[0]) == 0xE220A8397B1DCDAF
+
+
+def test_generators_numpy_torch_agree():
+    torch = pytest.importorskip("torch")
+    a = G.splitmix64_np(np.arange(4096, dtype=np.uint64), 99)
+    b = G.splitmix64_torch(torch.arange(4096), 99).numpy().view(np.uint64)
+    assert np.array_equal(a, b)
+    g1 = G.chung_lu_bipartite(3000, 2000, 20000, 2.1, 1.9, 5)
+    g2 = G.chung_lu_bipartite(3000, 2000, 20000, 2.1, 1.9, 5, device="cpu")
+    assert np.array_equal(g1.off_u, g2.off_u) and np.array_equal(g1.adj_u, g2.adj_u)
+
+
+def test_generator_shape_and_simplicity():
+    g = G.uniform_small()
+    assert (g.num_u, g.num_l, g.num_edges) == (2000, 3000, 20000)
+    u, v = g.edges()
+    assert np.unique(u * g.num_l + v).size == g.num_edges
+    h = G.chung_lu_bipartite(5000, 3000, 40000, 2.1, 2.1, 3)
+    assert h.num_edges == 40000
+    u, v = h.edges()
+    assert np.unique(u * h.num_l + v).size == h.num_edges
+    assert v.max() < h.num_l and u.max() < h.num_u
+
+
+def test_uniform_small_golden_graph():
+    gold = json.load(open(os.path.join(GOLDEN, "uniform_small.json")))
+    g = G.uniform_small()
+    assert hashlib.sha256(g.adj_u.tobytes()).hexdigest() == gold["graph"]["adj_sha256"]
+    assert hashlib.sha256(g.off_u.tobytes()).hexdigest() == gold["graph"]["off_sha256"]
+
+
+# ---------------------------------------------------------------------------
+# closed forms (Definition 2)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("a,b", [(2, 2), (3, 5), (5, 3), (4, 4), (1, 7), (6, 2), (7, 9)])
+def test_complete_bipartite(a, b):
+    g = G.complete_bipartite(a, b)
+    tot = c2(a) * c2(b)
+    r = oracle.vp(g, vertices=True, edges=True)
+    assert r["total"] == tot
+    assert oracle.brute_total(g, 0) == tot and oracle.brute_total(g, 1) == tot
+    assert oracle.ibs(g)[0] == tot
+    assert oracle.vppp(g)[0] == tot
+    assert np.all(r["pv_u"] == (a - 1) * c2(b))
+    assert np.all(r["pv_l"] == (b - 1) * c2(a))
+    assert np.all(r["pe"] == (a - 1) * (b - 1))
+    # processed wedges: the layer X holding the higher-priority vertices has
+    # x vertices of degree y; W = y * C(x, 2).  U wins ties (U ids > L ids).
+    if b >= a:     # U vertices have degree b >= a = degree of L vertices
+        x, y = a, b
+    else:
+        x, y = b, a
+    assert r["wedges"] == y * c2(x)
+    assert oracle.vppp(g)[1] == y * c2(x)
+
+
+@pytest.mark.parametrize("k", [3, 4, 5, 10])
+def test_long_cycles_have_none(k):
+    g = G.cycle(k)
+    assert oracle.vp(g)["total"] == 0
+    assert oracle.brute_total(g) == 0
+
+
+def test_c4():
+    g = G.cycle(2)
+    r = oracle.vp(g, vertices=True, edges=True)
+    assert r["total"] == 1
+    assert np.all(r["pe"] == 1) and np.all(r["pv_u"] == 1) and np.all(r["pv_l"] == 1)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_forests_stars_paths_have_none(seed):
+    for g in [G.random_forest(30 + seed, 25, seed), G.star(17 + seed), G.star(9, False),
+              G.path(11 + seed)]:
+        r = oracle.vp(g, vertices=True, edges=True)
+        assert r["total"] == 0
+        assert r["pe"].sum() == 0 and r["pv_u"].sum() == 0 and r["pv_l"].sum() == 0
+        assert oracle.ibs(g)[0] == 0 and oracle.vppp(g)[0] == 0
+
+
+def test_empty_and_isolated():
+    g = G.from_edges(5, 4, [], [])
+    assert oracle.vp(g)["total"] == 0 and oracle.vp(g)["wedges"] == 0
+    h = G.from_edges(6, 6, [0, 0, 1, 1], [0, 1, 0, 1])   # C4 plus isolated vertices
+    assert oracle.vp(h)["total"] == 1
+    assert oracle.brute_total(h) == 1
+
+
+def test_disjoint_union_is_additive():
+    a = G.complete_bipartite(4, 3)
+    b = G.uniform_bipartite(60, 50, 500, 3)
+    u = G.disjoint_union(a, b)
+    assert oracle.vp(u)["total"] == oracle.vp(a)["total"] + oracle.vp(b)["total"]
+
+
+# ---------------------------------------------------------------------------
+# the paper's worked examples
+# ---------------------------------------------------------------------------
+
+def test_paper_examples():
+    gold = json.load(open(os.path.join(GOLDEN, "paper_examples.json")))
+    for name, g in [("paper_fig2a", G.paper_fig2a()), ("paper_fig3", G.paper_fig3())]:
+        exp = gold[name]
+        r = oracle.vp(g)
+        assert r["wedges"] == exp["vp_wedges"]["value"], name
+        assert r["total"] == exp["total"]["value"], name
+        t, w, _ = oracle.ibs(g)
+        assert w == exp["ibs_wedges"]["value"], name
+        assert t == exp["total"]["value"]
+        assert oracle.vppp(g) == (exp["total"]["value"], exp["vp_wedges"]["value"])
+        assert oracle.brute_total(g, 0) == exp["total"]["value"]
+
+
+def test_paper_fig3_priority_order():
+    gold = json.load(open(os.path.join(GOLDEN, "paper_examples.json")))["paper_fig3"]
+    g = G.paper_fig3()
+    ru, rl, p = oracle.priority(g)
+    l = g.num_l
+
+    def gid(name):
+        return (l + int(name[1:])) if name[0] == "u" else int(name[1:])
+
+    n = g.num_u + g.num_l
+    top = [gid(x) for x in gold["priority_top"]["value"]]
+    assert [p[x] for x in top] == list(range(n, n - len(top), -1))
+    bottom = [gid(x) for x in gold["priority_bottom"]["value"]]
+    assert [p[x] for x in bottom] == [2, 1]
+    # per-layer ranks agree with p
+    assert ru[1] == g.num_u - 1 and ru[0] == g.num_u - 2
+    assert rl[1001] == l - 1 and rl[1000] == l - 2 and rl[0] == 0
+
+
+# ---------------------------------------------------------------------------
+# exhaustive enumeration on tiny graphs (Definition 2 taken literally)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("seed", range(120))
+def test_tiny_graphs_against_enumeration(seed):
+    r_ = 2 + seed % 6
+    l_ = 2 + (seed // 6) % 6
+    pnum = 1 + seed % 4
+    g = G.random_tiny(r_, l_, pnum, 5, seed)
+    ref = oracle.enumerate_butterflies(g)
+    vp = oracle.vp(g, threads=1, vertices=True, edges=True)
+    assert vp["total"] == ref["total"]
+    assert np.array_equal(vp["pv_u"], ref["pv_u"]) and np.array_equal(vp["pv_l"], ref["pv_l"])
+    assert np.array_equal(vp["pe"], ref["pe"])
+    assert oracle.brute_total(g, 0) == ref["total"] == oracle.brute_total(g, 1)
+    bu, bl = oracle.brute_vertices(g)
+    assert np.array_equal(bu, ref["pv_u"]) and np.array_equal(bl, ref["pv_l"])
+    assert np.array_equal(oracle.brute_edges(g), ref["pe"])
+    assert oracle.ibs(g)[0] == ref["total"]
+    assert oracle.vppp(g)[0] == ref["total"]
+
+
+# ---------------------------------------------------------------------------
+# identities on larger random graphs
+# ---------------------------------------------------------------------------
+
+def _graphs():
+    return [G.uniform_bipartite(300, 200, 3000, 11), G.uniform_bipartite(50, 400, 2500, 12),
+            G.chung_lu_bipartite(800, 500, 6000, 2.1, 2.1, 13),
+            G.chung_lu_bipartite(1500, 100, 8000, 2.5, 1.8, 14, max_l=600),
+            G.chung_lu_bipartite(400, 900, 5000, 1.9, 2.4, 15)]
+
+
+@pytest.mark.parametrize("gi", range(5))
+def test_identities(gi):
+    g = _graphs()[gi]
+    r = oracle.vp(g, threads=2, vertices=True, edges=True)
+    B = r["total"]
+    # Lemma 1, Eq. 2: Σ_U ⋈_u = Σ_L ⋈_v = 2 ⋈_G
+    assert int(r["pv_u"].sum()) == 2 * B == int(r["pv_l"].sum())
+    # every butterfly has four edges
+    assert int(r["pe"].sum()) == 4 * B
+    # every butterfly through x uses two of x's edges: Σ_{e ∋ x} ⋈_e = 2 ⋈_x
+    u, v = g.edges()
+    su = np.bincount(u, weights=r["pe"].astype(np.float64), minlength=g.num_u)
+    sl = np.bincount(v, weights=r["pe"].astype(np.float64), minlength=g.num_l)
+    assert np.array_equal(su.astype(np.uint64), 2 * r["pv_u"])
+    assert np.array_equal(sl.astype(np.uint64), 2 * r["pv_l"])
+    # Theorems 1 and 4 / Lemma 4: all orders agree, VP and VP++ process the same wedges
+    assert oracle.ibs(g)[0] == B == oracle.brute_total(g, 0) == oracle.brute_total(g, 1)
+    t3, w3 = oracle.vppp(g)
+    assert t3 == B and w3 == r["wedges"]
+    # Lemma 3: W <= Σ_E min(deg) <= min(Σ_U deg², Σ_L deg²)
+    tc, du2, dl2 = oracle.degree_stats(g)
+    assert r["wedges"] <= tc <= min(du2, dl2)
+    # the definitions per vertex / per edge
+    bu, bl = oracle.brute_vertices(g)
+    assert np.array_equal(bu, r["pv_u"]) and np.array_equal(bl, r["pv_l"])
+    assert np.array_equal(oracle.brute_edges(g), r["pe"])
+
+
+@pytest.mark.parametrize("gi", range(5))
+def test_relabel_and_list_order_invariance(gi):
+    g = _graphs()[gi]
+    B = oracle.vp(g)["total"]
+    assert oracle.vp(G.relabel(g, 5 + gi))["total"] == B
+    s = G.shuffle_lists(g, 9 + gi)
+    rs = oracle.vp(s, edges=True)
+    assert rs["total"] == B
+    # per-edge counts follow their edges through the shuffle
+    r0 = oracle.vp(g, edges=True)
+    u0, v0 = g.edges()
+    us, vs = s.edges()
+    k0 = dict(zip(zip(u0.tolist(), v0.tolist()), r0["pe"].tolist()))
+    assert all(k0[(a, b)] == c for a, b, c in zip(us.tolist(), vs.tolist(), rs["pe"].tolist()))
+
+
+def test_thread_count_invariance():
+    g = G.chung_lu_bipartite(3000, 2000, 30000, 2.1, 2.1, 21)
+    a = oracle.vp(g, threads=1, vertices=True, edges=True)
+    b = oracle.vp(g, threads=4, vertices=True, edges=True)
+    assert a["total"] == b["total"] and a["wedges"] == b["wedges"]
+    assert np.array_equal(a["pe"], b["pe"]) and np.array_equal(a["pv_u"], b["pv_u"])
+
+
+def test_uniform_small_golden_values():
+    gold = json.load(open(os.path.join(GOLDEN, "uniform_small.json")))
+    g = G.uniform_small()
+    r = oracle.vp(g, threads=2, vertices=True, edges=True)
+    assert r["total"] == gold["total"] == gold["brute_total"] == gold["ibs_total"]
+    assert r["wedges"] == gold["vp_wedges"]
+    assert hashlib.sha256(r["pe"].tobytes()).hexdigest() == gold["pe_sha256"]
+    assert hashlib.sha256(r["pv_u"].tobytes()).hexdigest() == gold["pv_u_sha256"]
+
+
+# ---------------------------------------------------------------------------
+# Definition 3 / Definition 4 and the per-start work (used by the GPU's
+# prepare parity tests)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("gi", range(5))
+def test_priority_and_projection(gi):
+    g = _graphs()[gi]
+    ru, rl, p = oracle.priority(g)
+    l, r = g.num_l, g.num_u
+    n = l + r
+    u, v = g.edges()
+    deg = np.concatenate([np.bincount(v, minlength=l), np.diff(g.off_u.astype(np.int64))])
+    # p sorts gids by (deg, gid): check against numpy's lexsort
+    order = np.lexsort((np.arange(n), deg))
+    assert np.array_equal(p[order], np.arange(1, n + 1))
+    assert sorted(ru.tolist()) == list(range(r)) and sorted(rl.tolist()) == list(range(l))
+    P = oracle.projection(g)
+    # structure preserved: mapping G* back gives the edge set of G
+    star_u, star_l = l + ru, rl
+    pairs_star = set()
+    for x in range(n):
+        for y in P["adj"][P["off"][x]:P["off"][x + 1]]:
+            pairs_star.add((x, int(y)))
+    pairs = {(int(star_u[a]), int(star_l[b])) for a, b in zip(u, v)}
+    assert pairs | {(b, a) for a, b in pairs} == pairs_star
+    # every list ascending; eid points back at the edge
+    for x in range(n):
+        seg = P["adj"][P["off"][x]:P["off"][x + 1]]
+        assert np.all(np.diff(seg) > 0)
+    for k in range(0, 2 * g.num_edges, 7):
+        x = int(np.searchsorted(P["off"], k, side="right") - 1)
+        y = int(P["adj"][k])
+        e = int(P["eid"][k])
+        uu, vv = (x, y) if x >= l else (y, x)
+        assert star_u[u[e]] == uu and star_l[v[e]] == vv
+    # Σ work = processed wedges of Algorithm 2
+    assert int(P["work"].sum()) == oracle.vp(g)["wedges"]
+    assert int(P["cut"].sum()) == g.num_edges   # every edge oriented exactly once
+
+
+def test_malformed_inputs_rejected():
+    g = G.complete_bipartite(3, 3)
+    bad = G.BipartiteCSR(3, 3, g.off_u.copy(), g.adj_u.copy())
+    bad.adj_u[4] = bad.adj_u[3]       # duplicate edge
+    with pytest.raises(ValueError):
+        oracle.vp(bad)
+    bad2 = G.BipartiteCSR(3, 3, g.off_u.copy(), g.adj_u.copy())
+    bad2.adj_u[0] = 7                 # id out of range
+    with pytest.raises(ValueError):
+        oracle.vp(bad2)
+    bad3 = G.BipartiteCSR(3, 3, g.off_u[::-1].copy(), g.adj_u.copy())
+    with pytest.raises(ValueError):
+        oracle.vp(bad3)
