@@ -1,0 +1,351 @@
+#!/usr/bin/env python3
+"""Benchmark of exact butterfly counting on one GB300 (or N replicas).
+
+Step = one pass of the whole single-graph hot path over one synthetic graph:
+prepare (degrees, priority ranks, projection + sorted lists, cut/work,
+schedule) followed by the wedge count and its reduction, with the CSR already
+resident in HBM.  Metric: processed wedges per second (W per step divided by
+the device time of the step).  Also reported: the count kernel against the
+HBM roofline, the CPU oracle timed on the host, and an end-to-end number
+through the C ABI from host buffers.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload powerlaw_20m|shopping_300m|uniform_small]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "wedges/s & %HBM roofline (1 graph); graphs/s and p99 latency batched vs per-graph"
+UNIT = "wedges/s"
+L2_FLUSH_BYTES = 512 << 20
+WORKLOADS = {
+    "powerlaw_20m": "chunglu_u1m_l500k_m20m_g2.1 (|U|=1M, |L|=500k, 20M edges, exponent 2.1 both layers, seed 2001+rank)",
+    "shopping_300m": "shopping_u10m_l100k_m300m (users exponent 2.5, items exponent 1.8, top item ~1M, seed 3001+rank)",
+    "uniform_small": "uniform_u2k_l3k_m20k (seed 1001+rank)",
+}
+
+
+def make_graph(name: str, rank: int, device):
+    from bfc_inputs import generators as G
+    if name == "powerlaw_20m":
+        return G.powerlaw_20m(seed=2001 + rank, device=device)
+    if name == "shopping_300m":
+        return G.shopping_300m(seed=3001 + rank, device=device)
+    if name == "uniform_small":
+        return G.uniform_small(seed=1001 + rank, device=device)
+    raise SystemExit(f"unknown workload {name}")
+
+
+def algorithmic_bytes(W: int, m: int, n: int) -> int:
+    """Bytes the count must move at least once: 4 B per processed wedge (the
+    end id), 12 B per oriented edge (middle id + the middle's offset), 12 B
+    per start (offset + cut)."""
+    return 4 * W + 12 * m + 12 * n
+
+
+def measured_peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return dict(hbm_gbs=float(d["hbm_gbs"]), source="measured")
+    return dict(hbm_gbs=6800.0, source="fallback")
+
+
+def count_kernel_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("count.cu", "bfc_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_1812_00283_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def recorded_traffic(workload: str):
+    """DRAM bytes per count launch from a committed ncu summary, if it was
+    taken on this workload with the current kernel source; else None."""
+    p = os.path.join(ROOT, "profiles", "count_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    if d.get("source_sha256") != count_kernel_hash() or d.get("workload") != workload:
+        return None
+    return int(d["dram_bytes_per_launch"])
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+    NAMES = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+
+    def __init__(self, device_id: str):
+        self.device_id = device_id
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.device_id, f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return dict(sm_mhz=None, sm_max_mhz=None, reasons=["nvidia-smi unavailable"])
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=5)
+        sm, smax, reasons = [], [], set()
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, flag in zip(self.NAMES, parts[3:7]):
+                if flag.lower().startswith("active"):
+                    reasons.add(name)
+        return dict(sm_mhz=statistics.median(sm) if sm else None,
+                    sm_max_mhz=max(smax) if smax else None, reasons=sorted(reasons),
+                    samples=len(sm))
+
+
+def dist_setup():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def run_reference(args, rank, world):
+    """The CPU oracle (Algorithm 2 scheduled as Algorithm 5) timed on the
+    host cores, on the same workload."""
+    if rank != 0:
+        return 0
+    import numpy as np  # noqa: F401
+
+    import oracle
+    from bfc_inputs import generators as G
+    g = make_graph(args.workload, 0, "cpu")
+    frac = 1.0 if args.steps + args.warmup <= 20 else 0.5
+    sample = g if frac == 1.0 else G.sample_u(g, frac, 77)
+    threads = os.cpu_count() or 1
+    times, W = [], 0
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        r = oracle.vp(sample, threads=threads)
+        dt = time.perf_counter() - t0
+        W = r["wedges"]
+        if i >= args.warmup:
+            times.append(dt)
+    v = W * len(times) / sum(times)
+    desc = (f"full {args.workload} graph" if frac == 1.0 else
+            f"{args.workload} graph restricted to a seeded {frac:.0%} of U")
+    desc += f", {sample.num_edges} edges, W={W}; oracle timed per step incl. its own preparation"
+    out = dict(metric=METRIC, value=v, unit=UNIT, impl="reference", n_gpus=world,
+               steps=args.steps, warmup=args.warmup, ms_per_step=1e3 * statistics.mean(times),
+               higher_is_better=True, scaling="weak", vs_baseline=None, dtype="u64",
+               data="synthetic", config=dict(workload=WORKLOADS[args.workload]),
+               cpu_baseline=dict(value=v, unit=UNIT, cores=threads, kind="oracle", sample=desc),
+               e2e=dict(value=v, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="powerlaw_20m", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    rank, world, local = dist_setup()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_1812_00283_gb300 import bfc
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    g = make_graph(args.workload, rank, dev)
+    off = torch.from_numpy(g.off_u).to(dev)
+    adj = torch.from_numpy(g.adj_u).to(dev)
+    r, l, m = g.num_u, g.num_l, g.num_edges
+    n = r + l
+    stream = torch.cuda.current_stream()
+    sp = stream.cuda_stream
+    total = torch.zeros(1, dtype=torch.int64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def one_step(ev=None):
+        if ev:
+            ev[0].record(stream)
+        h = bfc.bfc_prepare(r, l, m, off.data_ptr(), adj.data_ptr(), None, sp)
+        if ev:
+            ev[1].record(stream)
+        bfc.bfc_count(h, sp, total.data_ptr())
+        if ev:
+            ev[2].record(stream)
+        info = bfc.bfc_graph_info(h)
+        bfc.bfc_release(h)
+        if ev:
+            ev[3].record(stream)
+        return info
+
+    info = None
+    for _ in range(args.warmup):
+        flush.fill_(1)
+        info = one_step()
+    torch.cuda.synchronize()
+    expect = int(total.item()) & ((1 << 64) - 1)
+    W = int(info["wedges"])
+
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    props = torch.cuda.get_device_properties(dev)
+    clk = ClockSampler(f"GPU-{props.uuid}" if getattr(props, "uuid", None) else str(local))
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = bfc.bfc_kernel_launches()
+    clk.start()
+    for i in range(args.steps):
+        flush.fill_(i & 0xff)          # L2 flush between steps, outside the events
+        one_step(evs[i])
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    launches = bfc.bfc_kernel_launches() - launches0
+    if world > 1:
+        dist.barrier()
+    got = int(total.item()) & ((1 << 64) - 1)
+    if got != expect:
+        raise SystemExit(f"count changed between steps: {got} vs {expect}")
+
+    step_ms = [e[0].elapsed_time(e[3]) for e in evs]
+    prep_ms = [e[0].elapsed_time(e[1]) for e in evs]
+    count_ms = [e[1].elapsed_time(e[2]) for e in evs]
+    t_total = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([t_total], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_total = float(t.item())
+        w = torch.tensor([W], dtype=torch.int64, device=dev)
+        dist.all_reduce(w, op=dist.ReduceOp.SUM)
+        W_all = int(w.item())
+    else:
+        W_all = W
+    value = W_all * args.steps / (t_total / 1e3)
+
+    peaks = measured_peaks()
+    cnt_s = statistics.median(count_ms) / 1e3
+    B = algorithmic_bytes(W, m, n)
+    achieved = B / cnt_s / 1e9
+    traffic = recorded_traffic(args.workload)
+    roofline = dict(bound="hbm", achieved=achieved, peak=peaks["hbm_gbs"], unit="GB/s",
+                    frac=achieved / peaks["hbm_gbs"], traffic=traffic,
+                    kernel="k_count (bfc_count)", peak_source=peaks["source"],
+                    algorithmic_bytes_per_launch=B, count_ms_median=1e3 * cnt_s)
+
+    # end to end through the C ABI from pinned host buffers
+    e2e = None
+    if args.e2e_steps > 0:
+        off_h = torch.from_numpy(g.off_u).pin_memory()
+        adj_h = torch.from_numpy(g.adj_u).pin_memory()
+        ts = []
+        for i in range(args.e2e_steps + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            tot, wd = bfc.bfc_count_host(r, l, m, off_h.data_ptr(), adj_h.data_ptr(), None, sp)
+            ts.append(time.perf_counter() - t0)
+            if tot != expect or wd != W:
+                raise SystemExit("end-to-end count disagrees with the device-resident count")
+        ts = ts[1:]
+        e2e = dict(value=W / statistics.median(ts), unit=UNIT,
+                   h2d_bytes_per_step=4 * (r + 1) + 4 * m, d2h_bytes_per_step=8,
+                   ms_per_step=1e3 * statistics.median(ts),
+                   note="bfc_count_host: H2D of the CSR, prepare, count, D2H of the total")
+
+    cpu = None
+    verified = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        threads = os.cpu_count() or 1
+        t0 = time.perf_counter()
+        ref = oracle.vp(g, threads=threads)
+        dt = time.perf_counter() - t0
+        verified = (ref["total"] == expect and ref["wedges"] == W)
+        cpu = dict(value=ref["wedges"] / dt, unit=UNIT, cores=threads, kind="oracle",
+                   sample=f"one run of the oracle on the full {args.workload} graph "
+                          f"({m} edges, W={ref['wedges']}), incl. its own preparation, "
+                          f"{dt:.1f} s")
+
+    if rank == 0:
+        out = dict(
+            metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps,
+            warmup=args.warmup, ms_per_step=t_total / args.steps, higher_is_better=True,
+            scaling="weak", vs_baseline=None, dtype="u64", data="synthetic",
+            config=dict(workload=WORKLOADS[args.workload], num_u=r, num_l=l, num_edges=m,
+                        wedges_per_step=W, butterflies=expect,
+                        step="prepare (a1-a5) + count (a6-a7), CSR resident in HBM",
+                        l2="flushed between steps (512 MB write outside the timed events)",
+                        parallelism=f"replicas x{world} (independent graphs, no collective)",
+                        prepare_ms_median=statistics.median(prep_ms),
+                        count_ms_median=statistics.median(count_ms),
+                        count_only_wedges_per_s=W / cnt_s,
+                        bins=dict(dense_starts=info["dense_starts"], dense_items=info["dense_items"],
+                                  hash_starts=info["hash_starts"], warp_starts=info["warp_starts"]),
+                        oracle_agrees=verified),
+            roofline=roofline, cpu_baseline=cpu, e2e=e2e,
+            gpu_launches=launches, clocks=clocks)
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

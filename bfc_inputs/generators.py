@@ -149,6 +149,19 @@ def relabel(g: BipartiteCSR, seed: int) -> BipartiteCSR:
     return from_edges(g.num_u, g.num_l, pu[u], pl[v], g.name + "+relabelled", meta=g.meta)
 
 
+def sample_u(g: BipartiteCSR, frac: float, seed: int) -> BipartiteCSR:
+    """The subgraph of the edges of a seeded random fraction of U (same id
+    spaces; the other U vertices become isolated)."""
+    h = splitmix64_np(np.arange(g.num_u, dtype=np.uint64), seed)
+    keep = (h >> np.uint64(11)).astype(np.float64) / float(1 << 53) < frac
+    deg = np.diff(g.off_u.astype(np.int64))
+    mask = np.repeat(keep, deg)
+    off = np.zeros(g.num_u + 1, dtype=np.int64)
+    off[1:] = np.cumsum(np.where(keep, deg, 0))
+    return BipartiteCSR(g.num_u, g.num_l, off.astype(np.int32), g.adj_u[mask].copy(),
+                        f"{g.name}+u{frac}", dict(g.meta))
+
+
 def _perm_np(n: int, seed: int) -> np.ndarray:
     h = splitmix64_np(np.arange(n, dtype=np.uint64), seed).view(np.int64)
     order = np.argsort(h, kind="stable")

@@ -1,0 +1,183 @@
+/*
+ * libbfc — exact butterfly counting in bipartite graphs on one GB300 GPU.
+ *
+ * The method is the vertex-priority counting of Wang, Lin, Qin, Zhang and
+ * Zhang, "Efficient Butterfly Counting for Large Bipartite Networks":
+ *   - priority p(x) of Definition 3 (higher degree first, ties broken by id,
+ *     with every U id above every L id as Section 2 assumes);
+ *   - the projection of Definition 4 (vertices renumbered by per-layer
+ *     priority rank, L first, U offset by |L|) with neighbour lists sorted by
+ *     priority;
+ *   - Algorithm 2's wedge processing: for a start u, every middle v with
+ *     p(v) < p(u) and every end w with p(w) < p(u); the butterflies of the
+ *     pair (u, w) number C(count_wedge(w), 2) (Lemma 1);
+ *   - per-edge counts by the second wedge walk of Algorithm 4 (Eq. 7), and
+ *     per-vertex counts by the same walk (Eq. 1 / Eq. 2).
+ * All counts are exact unsigned 64-bit integers.
+ *
+ * Memory and streams
+ *   Every pointer whose name ends in _dev is device memory owned by the
+ *   caller; the library never frees it.  `stream` is a cudaStream_t passed
+ *   as void* (NULL = the legacy default stream).  The library allocates its
+ *   own working memory (the renumbered graph and schedule) from a
+ *   stream-ordered pool that it owns; bfc_release() returns it.
+ *
+ * Errors
+ *   Every int-returning call returns a bfc_status.  Nothing crosses the ABI
+ *   as an exception.  Outputs are defined only when the call returned
+ *   BFC_OK (and, for asynchronous calls, once bfc_sync() on the same graph
+ *   and stream returned BFC_OK).  bfc_last_error() gives a one-line message
+ *   for the calling thread's last failure.
+ *
+ * Graph contract
+ *   A simple bipartite graph G(U, L, E) with E ⊆ U × L (Section 2): no
+ *   duplicate edges.  It is given by its U-side CSR: off_u[num_u + 1]
+ *   (non-decreasing, off_u[0] = 0, off_u[num_u] = num_edges) and
+ *   adj_u[num_edges] (L ids in [0, num_l), any order within a list).  The
+ *   edge stored at slot k of adj_u has edge id k; per-edge outputs use it.
+ *   Isolated vertices are allowed.  Limits: num_edges <= 2^31 - 1,
+ *   num_u + num_l <= 2^31 - 2.
+ */
+#ifndef BFC_H
+#define BFC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum bfc_status {
+    BFC_OK = 0,
+    BFC_ERR_INVALID_ARGUMENT = 1, /* null pointer, negative or oversized sizes */
+    BFC_ERR_INVALID_GRAPH = 2,    /* offsets not a CSR, id out of range, duplicate edge */
+    BFC_ERR_OUT_OF_MEMORY = 3,    /* device or host allocation failed */
+    BFC_ERR_CUDA = 4,             /* a CUDA runtime call failed */
+    BFC_ERR_TIMEOUT = 5,          /* reserved: a bounded device wait gave up */
+    BFC_ERR_INTERNAL = 6          /* a kernel's own consistency check fired */
+} bfc_status;
+
+/* Opaque handle of a prepared graph; owned by the library. */
+typedef struct bfc_graph bfc_graph;
+
+/* U-side CSR in device memory (see "Graph contract"). */
+typedef struct bfc_csr {
+    int32_t num_u;          /* r = |U| */
+    int32_t num_l;          /* l = |L| */
+    int64_t num_edges;      /* m = |E| */
+    const int32_t *off_u;   /* device, [num_u + 1] */
+    const int32_t *adj_u;   /* device, [num_edges] */
+} bfc_csr;
+
+/* Tuning and checking knobs.  Call bfc_options_init() first; a NULL
+ * options pointer means the defaults. */
+typedef struct bfc_options {
+    int32_t validate;       /* 1 (default): reject duplicate edges.  Offsets and
+                               id ranges are always checked. */
+    int32_t warp_max_work;  /* starts with at most this many wedges are counted
+                               by one warp with a shared-memory hash table
+                               (default 256, range [0, 256]) */
+    int32_t hash_max_work;  /* starts with at most this many wedges (and more
+                               than warp_max_work) are counted by one CTA with
+                               a shared-memory hash table (default 16384,
+                               range [warp_max_work, 16384]); heavier starts
+                               get dense shared-memory counters over chunks of
+                               their end range */
+    int32_t num_ctas;       /* persistent grid size; 0 (default) = one CTA per SM */
+    int32_t reserved[12];   /* must be zero */
+} bfc_options;
+
+/* Figures of a prepared graph (host values). */
+typedef struct bfc_info {
+    int32_t num_u, num_l;
+    int64_t num_edges;
+    uint64_t wedges;          /* W: wedges Algorithm 2 processes (Section 4) */
+    uint64_t max_start_work;  /* largest per-start wedge count */
+    int64_t starts_with_work; /* starts u with at least one wedge */
+    int64_t warp_starts;      /* starts in the warp/hash bin */
+    int64_t hash_starts;      /* starts in the CTA/hash bin */
+    int64_t dense_starts;     /* starts in the CTA/dense bin */
+    int64_t dense_items;      /* (start, end-range chunk) work items of the dense bin */
+    int64_t device_bytes;     /* library-owned device memory held by the graph */
+    int32_t max_deg_u, max_deg_l;
+} bfc_info;
+
+/* What bfc_export() can copy out (for parity tests; layouts as stated). */
+typedef enum bfc_array {
+    BFC_RANK_U = 0,   /* int32[num_u]: per-layer priority rank of each U vertex (Definition 4) */
+    BFC_RANK_L = 1,   /* int32[num_l] */
+    BFC_PROJ_OFF = 2, /* int64[n + 1]: CSR offsets of the projection graph G*, n = num_u + num_l;
+                         ids of G*: L vertex v -> rank_l[v], U vertex u -> num_l + rank_u[u] */
+    BFC_PROJ_ADJ = 3, /* int32[2m]: neighbour ids in G*, each list ascending */
+    BFC_PROJ_EID = 4, /* int32[2m]: edge id (U-side slot) of each entry */
+    BFC_CUT = 5,      /* int32[n]: |{y in N(x) : p(y) < p(x)}| per vertex of G* */
+    BFC_WORK = 6      /* uint64[n]: wedges Algorithm 2 processes from each start x of G* */
+} bfc_array;
+
+void bfc_options_init(bfc_options *opt);
+
+/* Steps a1-a5 of the hot path: degrees, priority ranks (Definition 3),
+ * the projection G* with priority-sorted lists (Definition 4, Section 4's
+ * neighbour sort), the per-start orientation cut and exact wedge work, and
+ * the degree-binned, heaviest-first schedule (Section 6.2's dynamic
+ * scheduling).  Reads the caller's CSR on `stream`; the caller may free it
+ * once this call returns.  Synchronises `stream` (it needs sizes on the
+ * host).  On success *out owns library memory until bfc_release(). */
+int bfc_prepare(const bfc_csr *csr, const bfc_options *opt, void *stream, bfc_graph **out);
+
+/* Steps a6-a7: wedge enumeration with per-start aggregation (Algorithm 2)
+ * and the reduction to ⋈_G.  Writes one uint64 to total_dev.  Asynchronous
+ * on `stream`; no host synchronisation, no allocation. */
+int bfc_count(bfc_graph *g, void *stream, uint64_t *total_dev);
+
+/* Step a8: per-vertex counts ⋈_x (Eq. 1) in ORIGINAL ids: per_u_dev[num_u],
+ * per_l_dev[num_l] (either may be NULL), and the total if total_dev != NULL.
+ * Asynchronous; no allocation. */
+int bfc_count_vertices(bfc_graph *g, void *stream, uint64_t *per_u_dev, uint64_t *per_l_dev,
+                       uint64_t *total_dev);
+
+/* Step a9: per-edge counts ⋈_e (Eq. 7, Algorithm 4) indexed by edge id
+ * (U-side slot): per_edge_dev[num_edges]; plus the total if total_dev !=
+ * NULL.  Asynchronous; no allocation. */
+int bfc_count_edges(bfc_graph *g, void *stream, uint64_t *per_edge_dev, uint64_t *total_dev);
+
+/* Waits for `stream` and reports any error a kernel of this graph flagged
+ * since the last bfc_sync (BFC_ERR_INTERNAL), then clears the flag. */
+int bfc_sync(bfc_graph *g, void *stream);
+
+/* Host figures of a prepared graph. */
+int bfc_graph_info(const bfc_graph *g, bfc_info *out);
+
+/* Copies one internal array (see bfc_array) to caller-owned device memory
+ * dst_dev (size as listed), asynchronously on `stream`. */
+int bfc_export(const bfc_graph *g, int which, void *dst_dev, void *stream);
+
+/* End to end from HOST memory: copies the CSR to the device, prepares,
+ * counts, copies ⋈_G back to *total_host and frees everything it took.
+ * Synchronous.  off_u_host/adj_u_host may be pinned or pageable. */
+int bfc_count_host(int32_t num_u, int32_t num_l, int64_t num_edges, const int32_t *off_u_host,
+                   const int32_t *adj_u_host, const bfc_options *opt, void *stream,
+                   uint64_t *total_host, uint64_t *wedges_host);
+
+/* Frees the graph's library memory (stream-ordered on the stream of its
+ * last call).  NULL is ignored. */
+void bfc_release(bfc_graph *g);
+
+/* Static text for a status code. */
+const char *bfc_status_string(int status);
+
+/* One-line description of the calling thread's last failure ("" if none). */
+const char *bfc_last_error(void);
+
+/* Library version: major * 10000 + minor * 100 + patch. */
+int bfc_version(void);
+
+/* Number of CUDA kernels this library has launched in the process so far
+ * (all devices, all threads). */
+long long bfc_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BFC_H */

@@ -1,0 +1,177 @@
+"""Thin ctypes binding of libbfc (include/bfc.h): argument marshalling only.
+
+Every function keeps the C name.  Device pointers are plain integers (for
+example ``tensor.data_ptr()``); ``stream`` is a cudaStream_t as an integer
+(``torch.cuda.current_stream().cuda_stream``), 0 for the legacy default
+stream.  A non-OK status raises :class:`BfcError`.  There is no fallback:
+if libbfc.so is missing the import fails.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libbfc.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "bfc.h")
+
+c_int32, c_int64, c_uint64, c_void_p, c_int = (ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64,
+                                               ctypes.c_void_p, ctypes.c_int)
+
+BFC_OK = 0
+STATUS = {0: "BFC_OK", 1: "BFC_ERR_INVALID_ARGUMENT", 2: "BFC_ERR_INVALID_GRAPH",
+          3: "BFC_ERR_OUT_OF_MEMORY", 4: "BFC_ERR_CUDA", 5: "BFC_ERR_TIMEOUT",
+          6: "BFC_ERR_INTERNAL"}
+BFC_RANK_U, BFC_RANK_L, BFC_PROJ_OFF, BFC_PROJ_ADJ, BFC_PROJ_EID, BFC_CUT, BFC_WORK = range(7)
+
+
+class bfc_csr(ctypes.Structure):
+    _fields_ = [("num_u", c_int32), ("num_l", c_int32), ("num_edges", c_int64),
+                ("off_u", c_void_p), ("adj_u", c_void_p)]
+
+
+class bfc_options(ctypes.Structure):
+    _fields_ = [("validate", c_int32), ("warp_max_work", c_int32), ("hash_max_work", c_int32),
+                ("num_ctas", c_int32), ("reserved", c_int32 * 12)]
+
+
+class bfc_info(ctypes.Structure):
+    _fields_ = [("num_u", c_int32), ("num_l", c_int32), ("num_edges", c_int64),
+                ("wedges", c_uint64), ("max_start_work", c_uint64),
+                ("starts_with_work", c_int64), ("warp_starts", c_int64), ("hash_starts", c_int64),
+                ("dense_starts", c_int64), ("dense_items", c_int64), ("device_bytes", c_int64),
+                ("max_deg_u", c_int32), ("max_deg_l", c_int32)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class BfcError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__(f"{where}: {STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libbfc.so not built ({LIB_PATH}); run `python -m paper_1812_00283_gb300.build`")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+_SIGS = {
+    "bfc_options_init": (None, [ctypes.POINTER(bfc_options)]),
+    "bfc_prepare": (c_int, [ctypes.POINTER(bfc_csr), ctypes.POINTER(bfc_options), c_void_p,
+                            ctypes.POINTER(c_void_p)]),
+    "bfc_count": (c_int, [c_void_p, c_void_p, c_void_p]),
+    "bfc_count_vertices": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "bfc_count_edges": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "bfc_sync": (c_int, [c_void_p, c_void_p]),
+    "bfc_graph_info": (c_int, [c_void_p, ctypes.POINTER(bfc_info)]),
+    "bfc_export": (c_int, [c_void_p, c_int, c_void_p, c_void_p]),
+    "bfc_count_host": (c_int, [c_int32, c_int32, c_int64, c_void_p, c_void_p,
+                               ctypes.POINTER(bfc_options), c_void_p, ctypes.POINTER(c_uint64),
+                               ctypes.POINTER(c_uint64)]),
+    "bfc_release": (None, [c_void_p]),
+    "bfc_status_string": (ctypes.c_char_p, [c_int]),
+    "bfc_last_error": (ctypes.c_char_p, []),
+    "bfc_version": (c_int, []),
+    "bfc_kernel_launches": (ctypes.c_longlong, []),
+}
+for _name, (_res, _args) in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+
+def header_functions() -> list[str]:
+    """Names of the functions include/bfc.h declares."""
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(bfc_\w+)\s*\(", text)))
+
+
+def _check(rc: int, where: str):
+    if rc != BFC_OK:
+        raise BfcError(rc, where, (_lib.bfc_last_error() or b"").decode())
+
+
+def bfc_options_init(**overrides) -> bfc_options:
+    o = bfc_options()
+    _lib.bfc_options_init(ctypes.byref(o))
+    for k, v in overrides.items():
+        setattr(o, k, v)
+    return o
+
+
+def bfc_prepare(num_u: int, num_l: int, num_edges: int, off_u: int, adj_u: int,
+                options: bfc_options | None = None, stream: int = 0) -> int:
+    """Steps a1-a5; returns an opaque graph handle (int)."""
+    csr = bfc_csr(num_u, num_l, num_edges, off_u, adj_u)
+    h = c_void_p()
+    _check(_lib.bfc_prepare(ctypes.byref(csr), ctypes.byref(options) if options else None,
+                            stream, ctypes.byref(h)), "bfc_prepare")
+    return h.value
+
+
+def bfc_count(g: int, stream: int, total_dev: int):
+    _check(_lib.bfc_count(g, stream, total_dev), "bfc_count")
+
+
+def bfc_count_vertices(g: int, stream: int, per_u_dev: int | None, per_l_dev: int | None,
+                       total_dev: int | None):
+    _check(_lib.bfc_count_vertices(g, stream, per_u_dev, per_l_dev, total_dev),
+           "bfc_count_vertices")
+
+
+def bfc_count_edges(g: int, stream: int, per_edge_dev: int, total_dev: int | None):
+    _check(_lib.bfc_count_edges(g, stream, per_edge_dev, total_dev), "bfc_count_edges")
+
+
+def bfc_sync(g: int, stream: int = 0):
+    _check(_lib.bfc_sync(g, stream), "bfc_sync")
+
+
+def bfc_graph_info(g: int) -> dict:
+    info = bfc_info()
+    _check(_lib.bfc_graph_info(g, ctypes.byref(info)), "bfc_graph_info")
+    return info.as_dict()
+
+
+def bfc_export(g: int, which: int, dst_dev: int, stream: int = 0):
+    _check(_lib.bfc_export(g, which, dst_dev, stream), "bfc_export")
+
+
+def bfc_count_host(num_u: int, num_l: int, num_edges: int, off_u_host: int, adj_u_host: int,
+                   options: bfc_options | None = None, stream: int = 0) -> tuple[int, int]:
+    """End to end from host memory: returns (total, processed wedges)."""
+    t = c_uint64(0)
+    w = c_uint64(0)
+    _check(_lib.bfc_count_host(num_u, num_l, num_edges, off_u_host, adj_u_host,
+                               ctypes.byref(options) if options else None, stream,
+                               ctypes.byref(t), ctypes.byref(w)), "bfc_count_host")
+    return int(t.value), int(w.value)
+
+
+def bfc_release(g: int):
+    _lib.bfc_release(g)
+
+
+def bfc_status_string(status: int) -> str:
+    return _lib.bfc_status_string(status).decode()
+
+
+def bfc_last_error() -> str:
+    return (_lib.bfc_last_error() or b"").decode()
+
+
+def bfc_version() -> int:
+    return int(_lib.bfc_version())
+
+
+def bfc_kernel_launches() -> int:
+    return int(_lib.bfc_kernel_launches())
+
+
+def library():
+    """The loaded ctypes library (for symbol checks)."""
+    return _lib

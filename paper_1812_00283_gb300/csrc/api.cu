@@ -1,0 +1,318 @@
+// C-ABI entry points of libbfc (declared in include/bfc.h).
+#include <cstdio>
+#include <atomic>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+
+#include "bfc_internal.cuh"
+
+namespace bfc {
+
+int gather_vertices(Graph *g, cudaStream_t s, uint64_t *per_u, uint64_t *per_l);
+
+namespace {
+thread_local std::string g_last_error;
+std::mutex g_pool_mutex;
+cudaMemPool_t g_pools[64] = {};
+}  // namespace
+
+void set_last_error(const std::string &msg) { g_last_error = msg; }
+
+namespace {
+std::atomic<long long> g_launches{0};
+}
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+int cuda_fail(cudaError_t e, const char *what) {
+    g_last_error = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    if (e == cudaErrorMemoryAllocation) return BFC_ERR_OUT_OF_MEMORY;
+    return BFC_ERR_CUDA;
+}
+
+static cudaError_t get_pool(cudaMemPool_t *out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_pool_mutex);
+    if (!g_pools[dev]) {
+        cudaMemPoolProps props;
+        memset(&props, 0, sizeof(props));
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool;
+        e = cudaMemPoolCreate(&pool, &props);
+        if (e != cudaSuccess) return e;
+        uint64_t thr = ~0ull;   // keep freed blocks cached for reuse
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+        g_pools[dev] = pool;
+    }
+    *out = g_pools[dev];
+    return cudaSuccess;
+}
+
+cudaError_t pool_alloc(void **p, size_t bytes, cudaStream_t s) {
+    cudaMemPool_t pool;
+    cudaError_t e = get_pool(&pool);
+    if (e != cudaSuccess) return e;
+    return cudaMallocFromPoolAsync(p, bytes, pool, s);
+}
+
+void pool_free(void *p, cudaStream_t s) {
+    if (p) cudaFreeAsync(p, s);
+}
+
+}  // namespace bfc
+
+using bfc::Graph;
+
+struct bfc_graph {
+    Graph g;
+};
+
+static int check_options(const bfc_options *o) {
+    if (o->warp_max_work < 0 || o->warp_max_work > bfc::kWarpMaxWork) {
+        bfc::set_last_error("warp_max_work must lie in [0, 256]");
+        return BFC_ERR_INVALID_ARGUMENT;
+    }
+    if (o->hash_max_work < o->warp_max_work || o->hash_max_work > bfc::kHashMaxWork) {
+        bfc::set_last_error("hash_max_work must lie in [warp_max_work, 16384]");
+        return BFC_ERR_INVALID_ARGUMENT;
+    }
+    if (o->num_ctas < 0) {
+        bfc::set_last_error("num_ctas must be >= 0");
+        return BFC_ERR_INVALID_ARGUMENT;
+    }
+    for (int i = 0; i < 12; ++i)
+        if (o->reserved[i] != 0) {
+            bfc::set_last_error("reserved option fields must be zero");
+            return BFC_ERR_INVALID_ARGUMENT;
+        }
+    return BFC_OK;
+}
+
+extern "C" {
+
+void bfc_options_init(bfc_options *opt) {
+    if (!opt) return;
+    memset(opt, 0, sizeof(*opt));
+    opt->validate = 1;
+    opt->warp_max_work = bfc::kWarpMaxWork;
+    opt->hash_max_work = bfc::kHashMaxWork;
+    opt->num_ctas = 0;
+}
+
+int bfc_prepare(const bfc_csr *csr, const bfc_options *opt_in, void *stream, bfc_graph **out) {
+    bfc::set_last_error("");
+    if (!csr || !out) { bfc::set_last_error("null argument"); return BFC_ERR_INVALID_ARGUMENT; }
+    *out = nullptr;
+    bfc_options opt;
+    if (opt_in) opt = *opt_in; else bfc_options_init(&opt);
+    int rc = check_options(&opt);
+    if (rc) return rc;
+    if (csr->num_u < 0 || csr->num_l < 0 || csr->num_edges < 0) {
+        bfc::set_last_error("negative size"); return BFC_ERR_INVALID_ARGUMENT;
+    }
+    if (csr->num_edges > 2147483647LL) {
+        bfc::set_last_error("num_edges exceeds 2^31 - 1"); return BFC_ERR_INVALID_ARGUMENT;
+    }
+    if ((int64_t)csr->num_u + (int64_t)csr->num_l > 2147483646LL) {
+        bfc::set_last_error("num_u + num_l exceeds 2^31 - 2"); return BFC_ERR_INVALID_ARGUMENT;
+    }
+    if (!csr->off_u || (csr->num_edges > 0 && !csr->adj_u)) {
+        bfc::set_last_error("null CSR pointer"); return BFC_ERR_INVALID_ARGUMENT;
+    }
+    if (csr->num_edges > 0 && csr->num_l == 0) {
+        bfc::set_last_error("edges with an empty L layer"); return BFC_ERR_INVALID_GRAPH;
+    }
+    bfc_graph *h = new (std::nothrow) bfc_graph();
+    if (!h) { bfc::set_last_error("host allocation failed"); return BFC_ERR_OUT_OF_MEMORY; }
+    Graph *g = &h->g;
+    cudaError_t e = cudaGetDevice(&g->device);
+    if (e != cudaSuccess) { delete h; return bfc::cuda_fail(e, "cudaGetDevice"); }
+    e = cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device);
+    if (e != cudaSuccess) { delete h; return bfc::cuda_fail(e, "cudaDeviceGetAttribute"); }
+    int smem_optin = 0;
+    e = cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, g->device);
+    if (e != cudaSuccess) { delete h; return bfc::cuda_fail(e, "cudaDeviceGetAttribute"); }
+    if (smem_optin < bfc::kCounterBytes + 32 * 1024) {
+        delete h;
+        bfc::set_last_error("device has too little shared memory per block");
+        return BFC_ERR_CUDA;
+    }
+    g->grid = opt.num_ctas > 0 ? opt.num_ctas : g->num_sms;
+    rc = bfc::prepare_graph(csr, &opt, static_cast<cudaStream_t>(stream), g);
+    if (rc != BFC_OK) {
+        g->mem.release();
+        cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+        delete h;
+        return rc;
+    }
+    *out = h;
+    return BFC_OK;
+}
+
+static int count_common(bfc_graph *h, void *stream, int mode, uint64_t *per_a, uint64_t *per_b,
+                        uint64_t *total_dev) {
+    bfc::set_last_error("");
+    if (!h) { bfc::set_last_error("null graph"); return BFC_ERR_INVALID_ARGUMENT; }
+    Graph *g = &h->g;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    g->stream = s;
+    unsigned long long *pv = nullptr, *pe = nullptr;
+    if (mode == bfc::kModeVertices) {
+        pv = g->pv;
+        BFC_CUDA(cudaMemsetAsync(pv, 0, sizeof(unsigned long long) * (size_t)(g->n > 0 ? g->n : 1), s));
+    } else if (mode == bfc::kModeEdges) {
+        pe = reinterpret_cast<unsigned long long *>(per_a);
+        if (g->m > 0) BFC_CUDA(cudaMemsetAsync(pe, 0, sizeof(uint64_t) * (size_t)g->m, s));
+    }
+    int rc = bfc::launch_count(g, s, mode, pv, pe);
+    if (rc) return rc;
+    if (mode == bfc::kModeVertices) {
+        rc = bfc::gather_vertices(g, s, per_a, per_b);
+        if (rc) return rc;
+    }
+    if (total_dev)
+        BFC_CUDA(cudaMemcpyAsync(total_dev, g->acc, sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
+    return BFC_OK;
+}
+
+int bfc_count(bfc_graph *g, void *stream, uint64_t *total_dev) {
+    if (!total_dev) { bfc::set_last_error("null total_dev"); return BFC_ERR_INVALID_ARGUMENT; }
+    return count_common(g, stream, bfc::kModeTotal, nullptr, nullptr, total_dev);
+}
+
+int bfc_count_vertices(bfc_graph *g, void *stream, uint64_t *per_u_dev, uint64_t *per_l_dev,
+                       uint64_t *total_dev) {
+    return count_common(g, stream, bfc::kModeVertices, per_u_dev, per_l_dev, total_dev);
+}
+
+int bfc_count_edges(bfc_graph *g, void *stream, uint64_t *per_edge_dev, uint64_t *total_dev) {
+    if (!g) { bfc::set_last_error("null graph"); return BFC_ERR_INVALID_ARGUMENT; }
+    if (!per_edge_dev && g->g.m > 0) {
+        bfc::set_last_error("null per_edge_dev"); return BFC_ERR_INVALID_ARGUMENT;
+    }
+    return count_common(g, stream, bfc::kModeEdges, per_edge_dev, nullptr, total_dev);
+}
+
+int bfc_sync(bfc_graph *h, void *stream) {
+    bfc::set_last_error("");
+    if (!h) { bfc::set_last_error("null graph"); return BFC_ERR_INVALID_ARGUMENT; }
+    Graph *g = &h->g;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int herr = 0;
+    BFC_CUDA(cudaMemcpyAsync(&herr, g->err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    BFC_CUDA(cudaStreamSynchronize(s));
+    if (herr) {
+        BFC_CUDA(cudaMemsetAsync(g->err, 0, sizeof(int), s));
+        BFC_CUDA(cudaStreamSynchronize(s));
+        char buf[96];
+        snprintf(buf, sizeof(buf), "kernel consistency check fired (flags 0x%x)", herr);
+        bfc::set_last_error(buf);
+        return BFC_ERR_INTERNAL;
+    }
+    return BFC_OK;
+}
+
+int bfc_graph_info(const bfc_graph *h, bfc_info *out) {
+    if (!h || !out) { bfc::set_last_error("null argument"); return BFC_ERR_INVALID_ARGUMENT; }
+    *out = h->g.info;
+    return BFC_OK;
+}
+
+int bfc_export(const bfc_graph *h, int which, void *dst, void *stream) {
+    if (!h || !dst) { bfc::set_last_error("null argument"); return BFC_ERR_INVALID_ARGUMENT; }
+    const Graph *g = &h->g;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const void *src = nullptr;
+    size_t bytes = 0;
+    switch (which) {
+        case BFC_RANK_U: src = g->rank_u; bytes = 4 * (size_t)g->r; break;
+        case BFC_RANK_L: src = g->rank_l; bytes = 4 * (size_t)g->l; break;
+        case BFC_PROJ_OFF: src = g->off; bytes = 8 * ((size_t)g->n + 1); break;
+        case BFC_PROJ_ADJ: src = g->adj; bytes = 4 * (size_t)(2 * g->m); break;
+        case BFC_PROJ_EID: src = g->eid; bytes = 4 * (size_t)(2 * g->m); break;
+        case BFC_CUT: src = g->cut; bytes = 4 * (size_t)g->n; break;
+        case BFC_WORK: src = g->work; bytes = 8 * (size_t)g->n; break;
+        default: bfc::set_last_error("unknown array"); return BFC_ERR_INVALID_ARGUMENT;
+    }
+    if (bytes) BFC_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, s));
+    return BFC_OK;
+}
+
+int bfc_count_host(int32_t num_u, int32_t num_l, int64_t num_edges, const int32_t *off_u_host,
+                   const int32_t *adj_u_host, const bfc_options *opt, void *stream,
+                   uint64_t *total_host, uint64_t *wedges_host) {
+    bfc::set_last_error("");
+    if (!off_u_host || (num_edges > 0 && !adj_u_host) || !total_host || num_u < 0 ||
+        num_edges < 0 || num_edges > 2147483647LL) {
+        bfc::set_last_error("invalid host CSR arguments");
+        return BFC_ERR_INVALID_ARGUMENT;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    bfc::Allocs in;
+    in.stream = s;
+    int32_t *off = nullptr, *adj = nullptr;
+    if (in.get(&off, (size_t)num_u + 1) != cudaSuccess ||
+        in.get(&adj, (size_t)(num_edges > 0 ? num_edges : 1)) != cudaSuccess) {
+        in.release();
+        bfc::set_last_error("device allocation failed");
+        return BFC_ERR_OUT_OF_MEMORY;
+    }
+    int rc = BFC_OK;
+    cudaError_t e = cudaMemcpyAsync(off, off_u_host, sizeof(int32_t) * ((size_t)num_u + 1),
+                                    cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && num_edges > 0)
+        e = cudaMemcpyAsync(adj, adj_u_host, sizeof(int32_t) * (size_t)num_edges,
+                            cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) rc = bfc::cuda_fail(e, "cudaMemcpyAsync(H2D)");
+    bfc_graph *g = nullptr;
+    if (rc == BFC_OK) {
+        bfc_csr csr{num_u, num_l, num_edges, off, adj};
+        rc = bfc_prepare(&csr, opt, stream, &g);
+    }
+    if (rc == BFC_OK) rc = count_common(g, stream, bfc::kModeTotal, nullptr, nullptr, nullptr);
+    if (rc == BFC_OK) {
+        e = cudaMemcpyAsync(total_host, g->g.acc, sizeof(uint64_t), cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) rc = bfc::cuda_fail(e, "cudaMemcpyAsync(D2H)");
+    }
+    if (rc == BFC_OK) rc = bfc_sync(g, stream);
+    if (rc == BFC_OK && wedges_host) *wedges_host = g->g.info.wedges;
+    if (g) bfc_release(g);
+    in.release();
+    cudaStreamSynchronize(s);
+    return rc;
+}
+
+void bfc_release(bfc_graph *h) {
+    if (!h) return;
+    h->g.mem.stream = h->g.stream;
+    h->g.mem.release();
+    delete h;
+}
+
+const char *bfc_status_string(int status) {
+    switch (status) {
+        case BFC_OK: return "BFC_OK";
+        case BFC_ERR_INVALID_ARGUMENT: return "BFC_ERR_INVALID_ARGUMENT";
+        case BFC_ERR_INVALID_GRAPH: return "BFC_ERR_INVALID_GRAPH";
+        case BFC_ERR_OUT_OF_MEMORY: return "BFC_ERR_OUT_OF_MEMORY";
+        case BFC_ERR_CUDA: return "BFC_ERR_CUDA";
+        case BFC_ERR_TIMEOUT: return "BFC_ERR_TIMEOUT";
+        case BFC_ERR_INTERNAL: return "BFC_ERR_INTERNAL";
+        default: return "BFC_ERR_UNKNOWN";
+    }
+}
+
+const char *bfc_last_error(void) { return bfc::g_last_error.c_str(); }
+
+int bfc_version(void) { return 100; }
+
+long long bfc_kernel_launches(void) { return bfc::g_launches.load(std::memory_order_relaxed); }
+
+}  // extern "C"

@@ -1,0 +1,168 @@
+// Internal declarations of libbfc (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "bfc.h"
+
+namespace bfc {
+
+// ---------------------------------------------------------------------------
+// Sizes
+// ---------------------------------------------------------------------------
+constexpr int kScanThreads = 512;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanThreads * kScanItems;     // 4096 elements per block
+
+constexpr int kSortThreads = 256;                         // 8 warps
+constexpr int kSortItems = 16;                            // per thread
+constexpr int kSortTile = kSortThreads * kSortItems;      // 4096 keys per tile
+constexpr int kSortWarpSpan = kSortTile / (kSortThreads / 32);  // 512 consecutive keys per warp
+
+constexpr int kCountThreads = 1024;                       // 32 warps, one CTA per SM
+constexpr int kCountWarps = kCountThreads / 32;
+constexpr int kCounterBytes = 192 * 1024;                 // dynamic shared memory for counters
+constexpr int kDense16 = kCounterBytes / 2;               // 98,304 packed 16-bit counters
+constexpr int kDense32 = kCounterBytes / 4;               // 49,152 32-bit counters
+constexpr int kHashMaxSlots = 32768;                      // CTA hash: 128 KB keys + 64 KB counts
+constexpr int kHashMaxWork = kHashMaxSlots / 2;           // 16,384 wedges
+constexpr int kWarpRegion = kCounterBytes / kCountWarps;  // 6 KB of counters per warp
+constexpr int kWarpSlots = 512;                           // warp hash: 2 KB keys + 2 KB counts
+constexpr int kWarpMaxWork = kWarpSlots / 2;              // 256 wedges
+constexpr uint32_t kNarrowMaxCut = 65535;                 // counts fit 16 bits when cut <= this
+
+// device error bits (graph-owned error word)
+constexpr int kErrBadOffsets = 1;
+constexpr int kErrBadId = 2;
+constexpr int kErrDuplicate = 4;
+constexpr int kErrHashFull = 8;
+constexpr int kErrBounds = 16;
+
+// ---------------------------------------------------------------------------
+// Host-side error reporting
+// ---------------------------------------------------------------------------
+void set_last_error(const std::string &msg);
+// Counts kernel launches made by the library (reported by bfc_kernel_launches).
+void note_launch();
+int cuda_fail(cudaError_t e, const char *what);
+
+#define BFC_CUDA(call)                                  \
+    do {                                                \
+        cudaError_t e_ = (call);                        \
+        if (e_ != cudaSuccess) return ::bfc::cuda_fail(e_, #call); \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// Stream-ordered allocations from the library's pool
+// ---------------------------------------------------------------------------
+cudaError_t pool_alloc(void **p, size_t bytes, cudaStream_t s);
+void pool_free(void *p, cudaStream_t s);
+
+// A list of pool allocations released together.
+struct Allocs {
+    static constexpr int kMax = 64;
+    void *ptr[kMax];
+    size_t bytes[kMax];
+    int n = 0;
+    size_t total = 0;
+    cudaStream_t stream = nullptr;
+    template <typename T>
+    cudaError_t get(T **p, size_t count) {
+        if (n >= kMax) return cudaErrorMemoryAllocation;
+        size_t b = count * sizeof(T);
+        if (b == 0) b = 16;
+        b = (b + 255) & ~size_t(255);
+        void *q = nullptr;
+        cudaError_t e = pool_alloc(&q, b, stream);
+        if (e != cudaSuccess) return e;
+        ptr[n] = q;
+        bytes[n] = b;
+        ++n;
+        total += b;
+        *p = static_cast<T *>(q);
+        return cudaSuccess;
+    }
+    void release() {
+        for (int i = n - 1; i >= 0; --i) pool_free(ptr[i], stream);
+        n = 0;
+        total = 0;
+    }
+};
+
+// ---------------------------------------------------------------------------
+// The prepared graph
+// ---------------------------------------------------------------------------
+struct Graph {
+    int32_t r = 0, l = 0, n = 0;
+    int64_t m = 0;
+    bfc_options opt{};
+    bfc_info info{};
+    cudaStream_t stream = nullptr;   // stream of the last call (for stream-ordered release)
+    int device = 0;
+    int num_sms = 0;
+    int grid = 0;
+
+    Allocs mem;          // everything below lives in `mem`
+    int32_t *rank_u = nullptr, *rank_l = nullptr;  // original id -> rank in layer
+    int64_t *off = nullptr;   // [n+1] CSR of G*
+    int32_t *adj = nullptr;   // [2m]
+    int32_t *eid = nullptr;   // [2m]
+    int32_t *plen = nullptr;  // [2m] wedges through each middle slot (0 if not a middle slot)
+    int32_t *cut = nullptr;   // [n]
+    uint64_t *work = nullptr; // [n]
+    int2 *cta_items = nullptr;    // (start, chunk) / (start, -1 = hash)
+    int32_t *warp_items = nullptr;
+    int64_t n_cta_items = 0, n_warp_items = 0;
+    int *cursors = nullptr;        // [2] work-queue cursors of the count kernel
+    unsigned long long *acc = nullptr;  // [1] device accumulator for ⋈_G
+    unsigned long long *pv = nullptr;   // [n] per-vertex scratch in G* ids (allocated on demand? no: in prepare)
+    int *err = nullptr;            // device error word
+};
+
+// ---------------------------------------------------------------------------
+// Primitives (scan_sort.cu)
+// ---------------------------------------------------------------------------
+// Exclusive prefix sum of n elements; writes n+1 outputs (out[n] = total).
+// `tmp` must hold scan_tmp_elems(n) elements of T.
+template <typename T>
+size_t scan_tmp_elems(int64_t n);
+template <typename T>
+cudaError_t scan_exclusive(const T *in, T *out, int64_t n, T *tmp, cudaStream_t s);
+// Inclusive running maximum (int32).
+size_t max_scan_tmp_elems(int64_t n);
+cudaError_t max_scan_inclusive(const int32_t *in, int32_t *out, int64_t n, int32_t *tmp,
+                               cudaStream_t s);
+
+// Stable LSD radix sort of (uint64 key, int32 value) pairs on key bits
+// [begin_bit, end_bit).  Ping-pongs between (k0, v0) and (k1, v1); returns
+// 0 if the result is in (k0, v0), 1 if in (k1, v1).  `hist` needs
+// radix_hist_elems(n) uint32 and `scan_tmp` scan_tmp_elems<uint32_t>(..).
+size_t radix_hist_elems(int64_t n);
+cudaError_t radix_sort_pairs(uint64_t *k0, int32_t *v0, uint64_t *k1, int32_t *v1, int64_t n,
+                             int begin_bit, int end_bit, uint32_t *hist, uint32_t *scan_tmp,
+                             cudaStream_t s, int *which);
+
+// Device-wide max / sum reductions into one element (result in device memory).
+cudaError_t reduce_max_i32(const int32_t *in, int64_t n, int32_t *out, cudaStream_t s);
+cudaError_t reduce_max_u64(const uint64_t *in, int64_t n, unsigned long long *out, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Prepare and count (prepare.cu, count.cu)
+// ---------------------------------------------------------------------------
+int prepare_graph(const bfc_csr *csr, const bfc_options *opt, cudaStream_t s, Graph *g);
+enum CountMode { kModeTotal = 0, kModeVertices = 1, kModeEdges = 2 };
+int launch_count(Graph *g, cudaStream_t s, int mode, unsigned long long *pv_proj,
+                 unsigned long long *pe);
+int count_smem_setup(int device);
+
+// small helpers
+inline int bits_for(uint64_t x) {  // bits needed to represent x (0 for x = 0)
+    int b = 0;
+    while (x) { ++b; x >>= 1; }
+    return b;
+}
+
+}  // namespace bfc

@@ -1,0 +1,516 @@
+// Steps a6-a9: wedge enumeration with per-start aggregation (Algorithm 2),
+// the reduction to ⋈_G, and the per-vertex / per-edge second walk
+// (Algorithm 4 in the orientation of Algorithm 2).
+//
+// One persistent launch, one CTA of 1024 threads per SM.  Each CTA first
+// takes CTA work items from a global queue (heaviest first, Section 6.2's
+// dynamic scheduling with the exact per-start workload), then its 32 warps
+// take single light starts from a second queue.
+//
+//   dense item (x, c): the wedges of start x whose end lies in the c-th
+//       chunk of x's end range [0, rank(x)); count_wedge is a dense array in
+//       shared memory (16-bit counts when cut[x] <= 65535, else 32-bit).
+//       Chunks split the END range, so every pair (x, w) is aggregated by
+//       exactly one item and C(count, 2) is never split.
+//   hash item (x): a start with at most 16,384 wedges; count_wedge is an
+//       open-addressing hash table in shared memory.
+//   warp item (x): a start with at most 256 wedges, one warp, a per-warp
+//       hash table.
+//
+// Aggregation uses the running form of Lemma 1: adding old = count_wedge(w)
+// before each increment gives Σ_w C(count_wedge(w), 2) exactly.
+#include "bfc_internal.cuh"
+
+#ifndef BFC_CHECKED
+#define BFC_CHECKED 1
+#endif
+
+namespace bfc {
+
+namespace {
+
+struct CountParams {
+    const int64_t *__restrict__ off;
+    const int32_t *__restrict__ adj;
+    const int32_t *__restrict__ eid;
+    const int32_t *__restrict__ plen;
+    const int32_t *__restrict__ cut;
+    const uint64_t *__restrict__ work;
+    const int2 *__restrict__ cta_items;
+    const int32_t *__restrict__ warp_items;
+    int64_t n_cta;
+    int64_t n_warp;
+    int *cursors;
+    unsigned long long *acc;
+    unsigned long long *pv;   // [n] in G* ids
+    unsigned long long *pe;   // [m] by edge id
+    int64_t adj_len;
+    int32_t l;
+    int *err;
+};
+
+struct SharedCTA {
+    long long excl[kCountThreads];      // exclusive prefix of batch lengths
+    long long src[kCountThreads];       // adjacency position of a batch entry minus its prefix
+    unsigned long long msum[kCountThreads];  // second walk: Σ δ per middle of the batch
+    long long wtot[32];
+    unsigned long long red[32];
+    int item;
+};
+
+__device__ __forceinline__ unsigned long long c2(unsigned long long c) {
+    return c < 2 ? 0ull : c * (c - 1) / 2;
+}
+
+__device__ __forceinline__ int lower_bound_g(const int32_t *a, int len, int32_t key) {
+    int lo = 0, hi = len;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (__ldg(a + mid) < key) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// Exclusive block scan of one int64 per thread (1024 threads).
+__device__ __forceinline__ long long block_excl_scan(long long v, SharedCTA &sh, long long *total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    long long x = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        long long o = __shfl_up_sync(0xffffffffu, x, d);
+        if (lane >= d) x += o;
+    }
+    if (lane == 31) sh.wtot[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        long long w = sh.wtot[lane];
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            long long o = __shfl_up_sync(0xffffffffu, w, d);
+            if (lane >= d) w += o;
+        }
+        sh.wtot[lane] = w;
+    }
+    __syncthreads();
+    long long before = warp > 0 ? sh.wtot[warp - 1] : 0;
+    *total = sh.wtot[31];
+    return before + x - v;
+}
+
+__device__ __forceinline__ unsigned long long block_sum(unsigned long long v, SharedCTA &sh) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+    __syncthreads();
+    if (lane == 0) sh.red[warp] = v;
+    __syncthreads();
+    unsigned long long t = 0;
+    if (warp == 0) {
+        t = sh.red[lane];
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) t += __shfl_xor_sync(0xffffffffu, t, d);
+    }
+    return t;   // valid in warp 0
+}
+
+// last j in [0, 1024) with excl[j] <= k (excl[0] = 0 <= k)
+__device__ __forceinline__ int batch_entry(const long long *excl, long long k) {
+    int lo = 0, hi = kCountThreads;
+#pragma unroll
+    for (int it = 0; it < 10; ++it) {
+        int mid = (lo + hi) >> 1;
+        if (excl[mid] <= k) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ uint32_t hash_slot(int32_t key, uint32_t mask) {
+    return ((uint32_t)key * 0x9E3779B1u) & mask;
+}
+
+// Finds (inserting if absent) the slot of `key`.  Returns -1 if the table is
+// full, which the slot sizing rules out.
+__device__ __forceinline__ int hash_find(int32_t *keys, uint32_t mask, int32_t key, bool insert) {
+    uint32_t h = hash_slot(key, mask);
+    for (uint32_t probe = 0; probe <= mask; ++probe) {
+        int32_t k = *((volatile int32_t *)(keys + h));
+        if (k == key) return (int)h;
+        if (k == -1) {
+            if (!insert) return -1;
+            int32_t prev = atomicCAS(keys + h, -1, key);
+            if (prev == -1 || prev == key) return (int)h;
+        }
+        h = (h + 1) & mask;
+    }
+    return -1;
+}
+
+// 16-bit counters packed two per 32-bit word
+__device__ __forceinline__ uint32_t inc16(uint32_t *w32, int idx) {
+    const uint32_t sh = (uint32_t)(idx & 1) << 4;
+    uint32_t old = atomicAdd(w32 + (idx >> 1), 1u << sh);
+    return (old >> sh) & 0xffffu;
+}
+__device__ __forceinline__ uint32_t get16(const uint32_t *w32, int idx) {
+    const uint32_t sh = (uint32_t)(idx & 1) << 4;
+    return (w32[idx >> 1] >> sh) & 0xffffu;
+}
+
+enum CounterKind { kDenseNarrow = 0, kDenseWide = 1, kHash = 2 };
+
+// One walk over the wedges of start x whose ends fall in [lb+lo, lb+hi).
+// kSecond = false: count (returns Σ old, i.e. Σ C(count, 2)).
+// kSecond = true : read the final counts and attribute δ = count − 1.
+template <int MODE, int KIND, bool kSecond>
+__device__ unsigned long long cta_walk(const CountParams &p, int32_t x, int32_t lb, int32_t lo,
+                                       int32_t hi, int32_t R, uint32_t hmask, unsigned char *ctr,
+                                       SharedCTA &sh) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t e0 = p.off[x];
+    const int32_t nmid = p.cut[x];
+    uint32_t *w32 = reinterpret_cast<uint32_t *>(ctr);
+    int32_t *hkeys = reinterpret_cast<int32_t *>(ctr);
+    uint32_t *hcnt = reinterpret_cast<uint32_t *>(ctr + (size_t)(hmask + 1) * 4);
+    const int32_t span = hi - lo;
+    unsigned long long acc = 0;
+    for (int32_t mb = 0; mb < nmid; mb += kCountThreads) {
+        const int32_t j = mb + tid;
+        long long len = 0, src = 0;
+        int32_t v = 0;
+        int64_t e = 0;
+        if (j < nmid) {
+            e = e0 + j;
+            v = p.adj[e];
+            const int32_t pl = p.plen[e];
+            const int64_t b = p.off[v];
+            int32_t s0 = 0, s1 = pl;
+            if (KIND != kHash) {
+                if (lo > 0) s0 = lower_bound_g(p.adj + b, pl, lb + lo);
+                if (hi < R) s1 = lower_bound_g(p.adj + b, pl, lb + hi);
+            }
+            len = s1 - s0;
+            src = b + s0;
+        }
+        long long total;
+        const long long excl = block_excl_scan(len, sh, &total);
+        sh.excl[tid] = excl;
+        sh.src[tid] = src - excl;
+        if (kSecond) sh.msum[tid] = 0;
+        __syncthreads();
+        for (long long k0 = (long long)warp * 32; k0 < total; k0 += kCountThreads) {
+            const long long k = k0 + lane;
+            if (k < total) {
+                const int q = batch_entry(sh.excl, k);
+                const long long pos = sh.src[q] + k;
+#if BFC_CHECKED
+                if (pos < 0 || pos >= p.adj_len) { atomicOr(p.err, kErrBounds); continue; }
+#endif
+                const int32_t w = __ldg(p.adj + pos);
+                uint32_t c;
+                if (KIND == kHash) {
+                    const int slot = hash_find(hkeys, hmask, w - lb, !kSecond);
+                    if (slot < 0) { atomicOr(p.err, kErrHashFull); continue; }
+                    if (!kSecond) { acc += inc16(hcnt, slot); continue; }
+                    c = get16(hcnt, slot);
+                } else {
+                    const int idx = w - lb - lo;
+#if BFC_CHECKED
+                    if (idx < 0 || idx >= span) { atomicOr(p.err, kErrBounds); continue; }
+#endif
+                    if (!kSecond) {
+                        acc += (KIND == kDenseWide) ? atomicAdd(w32 + idx, 1u) : inc16(w32, idx);
+                        continue;
+                    }
+                    c = (KIND == kDenseWide) ? w32[idx] : get16(w32, idx);
+                }
+                if (kSecond) {
+                    const unsigned long long delta = (unsigned long long)c - 1ull;
+                    if (delta) {
+                        if (MODE == kModeEdges) atomicAdd(p.pe + __ldg(p.eid + pos), delta);
+                        atomicAdd(sh.msum + q, delta);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        if (kSecond && j < nmid) {
+            const unsigned long long d = sh.msum[tid];
+            if (d) {
+                if (MODE == kModeVertices) atomicAdd(p.pv + v, d);
+                if (MODE == kModeEdges) atomicAdd(p.pe + __ldg(p.eid + e), d);
+            }
+        }
+    }
+    (void)span;
+    return acc;
+}
+
+template <int MODE, int KIND>
+__device__ unsigned long long cta_item_body(const CountParams &p, int32_t x, int32_t lb,
+                                            int32_t lo, int32_t hi, int32_t R, uint32_t hmask,
+                                            unsigned char *ctr, SharedCTA &sh) {
+    unsigned long long acc = cta_walk<MODE, KIND, false>(p, x, lb, lo, hi, R, hmask, ctr, sh);
+    if (MODE != kModeTotal) {
+        __syncthreads();
+        if (MODE == kModeVertices) {
+            // ends: each pair (x, w) adds C(count, 2) to ⋈_w
+            if (KIND == kHash) {
+                const int32_t *hkeys = reinterpret_cast<const int32_t *>(ctr);
+                const uint32_t *hcnt = reinterpret_cast<const uint32_t *>(ctr + (size_t)(hmask + 1) * 4);
+                for (uint32_t s = threadIdx.x; s <= hmask; s += kCountThreads) {
+                    const int32_t k = hkeys[s];
+                    if (k >= 0) {
+                        const unsigned long long b = c2(get16(hcnt, (int)s));
+                        if (b) atomicAdd(p.pv + lb + k, b);
+                    }
+                }
+            } else {
+                const uint32_t *w32 = reinterpret_cast<const uint32_t *>(ctr);
+                for (int32_t i = threadIdx.x; i < hi - lo; i += kCountThreads) {
+                    const uint32_t c = (KIND == kDenseWide) ? w32[i] : get16(w32, i);
+                    if (c >= 2) atomicAdd(p.pv + lb + lo + i, c2(c));
+                }
+            }
+        }
+        cta_walk<MODE, KIND, true>(p, x, lb, lo, hi, R, hmask, ctr, sh);
+        if (MODE == kModeVertices) {
+            const unsigned long long t = block_sum(acc, sh);
+            if (threadIdx.x == 0 && t) atomicAdd(p.pv + x, t);
+        }
+    }
+    return acc;
+}
+
+__device__ __forceinline__ void zero_smem(unsigned char *p, int bytes, uint32_t fill) {
+    uint4 *q = reinterpret_cast<uint4 *>(p);
+    const int n16 = (bytes + 15) >> 4;
+    const uint4 f = make_uint4(fill, fill, fill, fill);
+    for (int i = threadIdx.x; i < n16; i += kCountThreads) q[i] = f;
+}
+
+template <int MODE>
+__device__ unsigned long long cta_item(const CountParams &p, int2 item, unsigned char *ctr,
+                                       SharedCTA &sh) {
+    const int32_t x = item.x;
+    const int32_t lb = x >= p.l ? p.l : 0;
+    const int32_t R = x - lb;
+    unsigned long long acc;
+    if (item.y >= 0) {
+        const bool wide = (uint32_t)p.cut[x] > kNarrowMaxCut;
+        const int32_t S = wide ? kDense32 : kDense16;
+        const int32_t lo = item.y * S;
+        const int32_t hi = min(R, lo + S);
+        const int32_t span = hi - lo;
+        zero_smem(ctr, wide ? span * 4 : ((span + 1) >> 1) * 4, 0u);
+        __syncthreads();
+        acc = wide ? cta_item_body<MODE, kDenseWide>(p, x, lb, lo, hi, R, 0, ctr, sh)
+                   : cta_item_body<MODE, kDenseNarrow>(p, x, lb, lo, hi, R, 0, ctr, sh);
+    } else {
+        const unsigned long long w = p.work[x];
+        const unsigned long long bound = w < (unsigned long long)R ? w : (unsigned long long)R;
+        uint32_t cap = 64;
+        while (cap < 2 * bound && cap < (uint32_t)kHashMaxSlots) cap <<= 1;
+        zero_smem(ctr, (int)cap * 4, 0xffffffffu);           // keys = -1
+        zero_smem(ctr + (size_t)cap * 4, (int)cap * 2, 0u);  // packed 16-bit counts
+        __syncthreads();
+        acc = cta_item_body<MODE, kHash>(p, x, lb, 0, R, R, cap - 1, ctr, sh);
+    }
+    __syncthreads();
+    return acc;
+}
+
+// ---- warp items -------------------------------------------------------------
+template <int MODE, bool kSecond>
+__device__ unsigned long long warp_walk(const CountParams &p, int32_t x, int32_t lb, uint32_t mask,
+                                        int32_t *keys, uint32_t *cnt, unsigned long long *msum) {
+    const int lane = threadIdx.x & 31;
+    const int64_t e0 = p.off[x];
+    const int32_t nmid = p.cut[x];
+    unsigned long long acc = 0;
+    for (int32_t mb = 0; mb < nmid; mb += 32) {
+        const int32_t j = mb + lane;
+        int32_t len = 0, v = 0;
+        int64_t src = 0, e = 0;
+        if (j < nmid) {
+            e = e0 + j;
+            v = p.adj[e];
+            len = p.plen[e];
+            src = p.off[v];
+        }
+        int32_t incl = len;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            int32_t o = __shfl_up_sync(0xffffffffu, incl, d);
+            if (lane >= d) incl += o;
+        }
+        const int32_t total = __shfl_sync(0xffffffffu, incl, 31);
+        const int64_t base = src - (int64_t)(incl - len);
+        if (kSecond) msum[lane] = 0;
+        __syncwarp();
+        for (int32_t k0 = 0; k0 < total; k0 += 32) {
+            const int32_t k = k0 + lane;
+            int q = 0;   // number of entries whose inclusive prefix is <= k
+#pragma unroll
+            for (int sft = 16; sft >= 1; sft >>= 1) {
+                const int32_t val = __shfl_sync(0xffffffffu, incl, q + sft - 1);
+                if (val <= k) q += sft;
+            }
+            q = min(q, 31);
+            const int64_t b = __shfl_sync(0xffffffffu, base, q);
+            if (k < total) {
+                const int64_t pos = b + k;
+#if BFC_CHECKED
+                if (pos < 0 || pos >= p.adj_len) { atomicOr(p.err, kErrBounds); continue; }
+#endif
+                const int32_t w = __ldg(p.adj + pos);
+                const int slot = hash_find(keys, mask, w - lb, !kSecond);
+                if (slot < 0) { atomicOr(p.err, kErrHashFull); continue; }
+                if (!kSecond) {
+                    acc += atomicAdd(cnt + slot, 1u);
+                } else {
+                    const unsigned long long delta = (unsigned long long)cnt[slot] - 1ull;
+                    if (delta) {
+                        if (MODE == kModeEdges) atomicAdd(p.pe + __ldg(p.eid + pos), delta);
+                        atomicAdd(msum + q, delta);
+                    }
+                }
+            }
+        }
+        __syncwarp();
+        if (kSecond && j < nmid) {
+            const unsigned long long d = msum[lane];
+            if (d) {
+                if (MODE == kModeVertices) atomicAdd(p.pv + v, d);
+                if (MODE == kModeEdges) atomicAdd(p.pe + __ldg(p.eid + e), d);
+            }
+        }
+        __syncwarp();
+    }
+    return acc;
+}
+
+template <int MODE>
+__device__ unsigned long long warp_item(const CountParams &p, int32_t x, unsigned char *region) {
+    const int lane = threadIdx.x & 31;
+    const int32_t lb = x >= p.l ? p.l : 0;
+    const int32_t R = x - lb;
+    const unsigned long long w = p.work[x];
+    const unsigned long long bound = w < (unsigned long long)R ? w : (unsigned long long)R;
+    uint32_t cap = 32;
+    while (cap < 2 * bound && cap < (uint32_t)kWarpSlots) cap <<= 1;
+    int32_t *keys = reinterpret_cast<int32_t *>(region);
+    uint32_t *cnt = reinterpret_cast<uint32_t *>(region + kWarpSlots * 4);
+    unsigned long long *msum = reinterpret_cast<unsigned long long *>(region + kWarpSlots * 8);
+    for (uint32_t s = lane; s < cap; s += 32) { keys[s] = -1; cnt[s] = 0; }
+    __syncwarp();
+    unsigned long long acc = warp_walk<MODE, false>(p, x, lb, cap - 1, keys, cnt, msum);
+    if (MODE != kModeTotal) {
+        __syncwarp();
+        if (MODE == kModeVertices) {
+            for (uint32_t s = lane; s < cap; s += 32) {
+                const int32_t k = keys[s];
+                if (k >= 0 && cnt[s] >= 2) atomicAdd(p.pv + lb + k, c2(cnt[s]));
+            }
+        }
+        warp_walk<MODE, true>(p, x, lb, cap - 1, keys, cnt, msum);
+        if (MODE == kModeVertices) {
+            unsigned long long t = acc;
+#pragma unroll
+            for (int d = 16; d > 0; d >>= 1) t += __shfl_xor_sync(0xffffffffu, t, d);
+            if (lane == 0 && t) atomicAdd(p.pv + x, t);
+        }
+    }
+    __syncwarp();
+    return acc;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kCountThreads, 1) k_count(CountParams p) {
+    extern __shared__ __align__(16) unsigned char ctr[];
+    __shared__ SharedCTA sh;
+    unsigned long long acc = 0;
+    // phase 1: CTA items, heaviest first
+    for (;;) {
+        if (threadIdx.x == 0) sh.item = atomicAdd(p.cursors, 1);
+        __syncthreads();
+        const int64_t it = sh.item;
+        __syncthreads();
+        if (it >= p.n_cta) break;
+        acc += cta_item<MODE>(p, p.cta_items[it], ctr, sh);
+    }
+    // phase 2: warp items
+    {
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        unsigned char *region = ctr + (size_t)warp * kWarpRegion;
+        for (;;) {
+            int it = 0;
+            if (lane == 0) it = atomicAdd(p.cursors + 1, 1);
+            it = __shfl_sync(0xffffffffu, it, 0);
+            if (it >= p.n_warp) break;
+            acc += warp_item<MODE>(p, p.warp_items[it], region);
+        }
+    }
+    // a7: reduction of the per-thread partial sums
+    const unsigned long long t = block_sum(acc, sh);
+    if (threadIdx.x == 0 && t) atomicAdd(p.acc, t);
+}
+
+__global__ void k_gather_vertices(const unsigned long long *__restrict__ pv,
+                                  const int32_t *__restrict__ rank_u,
+                                  const int32_t *__restrict__ rank_l, int32_t r, int32_t l,
+                                  uint64_t *per_u, uint64_t *per_l) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < r && per_u) per_u[i] = pv[l + rank_u[i]];
+    if (i < l && per_l) per_l[i] = pv[rank_l[i]];
+}
+
+template <int MODE>
+cudaError_t setup_one() {
+    return cudaFuncSetAttribute(k_count<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                kCounterBytes);
+}
+
+}  // namespace
+
+int count_smem_setup(int device) {
+    static bool done[64] = {false};
+    if (device < 0 || device >= 64) return BFC_ERR_INVALID_ARGUMENT;
+    if (done[device]) return BFC_OK;
+    BFC_CUDA(setup_one<kModeTotal>());
+    BFC_CUDA(setup_one<kModeVertices>());
+    BFC_CUDA(setup_one<kModeEdges>());
+    done[device] = true;
+    return BFC_OK;
+}
+
+int launch_count(Graph *g, cudaStream_t s, int mode, unsigned long long *pv_proj,
+                 unsigned long long *pe) {
+    int rc = count_smem_setup(g->device);
+    if (rc) return rc;
+    CountParams p;
+    p.off = g->off; p.adj = g->adj; p.eid = g->eid; p.plen = g->plen; p.cut = g->cut;
+    p.work = g->work; p.cta_items = g->cta_items; p.warp_items = g->warp_items;
+    p.n_cta = g->n_cta_items; p.n_warp = g->n_warp_items;
+    p.cursors = g->cursors; p.acc = g->acc; p.pv = pv_proj; p.pe = pe;
+    p.adj_len = 2 * g->m; p.l = g->l; p.err = g->err;
+    BFC_CUDA(cudaMemsetAsync(g->cursors, 0, 2 * sizeof(int), s));
+    BFC_CUDA(cudaMemsetAsync(g->acc, 0, sizeof(unsigned long long), s));
+    const int grid = g->grid;
+    if (mode == kModeTotal) k_count<kModeTotal><<<grid, kCountThreads, kCounterBytes, s>>>(p);
+    else if (mode == kModeVertices) k_count<kModeVertices><<<grid, kCountThreads, kCounterBytes, s>>>(p);
+    else k_count<kModeEdges><<<grid, kCountThreads, kCounterBytes, s>>>(p);
+    note_launch();
+    BFC_CUDA(cudaGetLastError());
+    return BFC_OK;
+}
+
+int gather_vertices(Graph *g, cudaStream_t s, uint64_t *per_u, uint64_t *per_l) {
+    const int64_t nmax = g->r > g->l ? g->r : g->l;
+    if (nmax == 0) return BFC_OK;
+    k_gather_vertices<<<(unsigned)((nmax + 255) / 256), 256, 0, s>>>(g->pv, g->rank_u, g->rank_l,
+                                                                      g->r, g->l, per_u, per_l); note_launch();
+    BFC_CUDA(cudaGetLastError());
+    return BFC_OK;
+}
+
+}  // namespace bfc

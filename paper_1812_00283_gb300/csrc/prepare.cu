@@ -1,0 +1,508 @@
+// Steps a1-a5 of the hot path: degrees, priority ranks, the projection
+// graph G* with priority-sorted neighbour lists, the per-start orientation
+// cut and exact wedge work, and the degree-binned schedule.
+//
+// Paper: Definition 3 (priority), Definition 4 (projection, Section 5.2),
+// Section 4 (neighbour lists sorted by priority, early termination; the bin
+// sort of Theorem 2's proof), Section 6.2 (workload of a start vertex and
+// heaviest-first dynamic scheduling, Eq. 5).
+#include <algorithm>
+#include <vector>
+
+#include "bfc_internal.cuh"
+
+namespace bfc {
+
+namespace {
+
+constexpr int kT = 256;
+
+inline unsigned blocks_for(int64_t n, int t = kT) {
+    int64_t b = (n + t - 1) / t;
+    if (b < 1) b = 1;
+    return (unsigned)b;
+}
+
+// ----- validation (always on: every later index depends on it) -------------
+__global__ void k_check_offsets(const int32_t *__restrict__ off, int32_t r, int64_t m, int *err) {
+    int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (u > r) return;
+    if (u == 0 && off[0] != 0) atomicOr(err, kErrBadOffsets);
+    if (u < r && off[u + 1] < off[u]) atomicOr(err, kErrBadOffsets);
+    if (u == r && (int64_t)off[r] != m) atomicOr(err, kErrBadOffsets);
+}
+
+__global__ void k_check_ids(const int32_t *__restrict__ adj, int64_t m, int32_t l, int *err) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < m;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        int32_t v = adj[k];
+        if (v < 0 || v >= l) atomicOr(err, kErrBadId);
+    }
+}
+
+// ----- a1: degrees -----------------------------------------------------------
+__global__ void k_deg_u(const int32_t *__restrict__ off, int32_t r, int32_t *deg_u,
+                        int32_t *heads) {
+    int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= r) return;
+    int32_t d = off[u + 1] - off[u];
+    deg_u[u] = d;
+    if (d > 0) heads[off[u]] = (int32_t)u;   // row owning slot off[u]; rows via max-scan
+}
+
+__global__ void k_deg_l(const int32_t *__restrict__ adj, int64_t m, int32_t *deg_l) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < m;
+         k += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&deg_l[adj[k]], 1);
+}
+
+// ----- a2: priority ranks ----------------------------------------------------
+// keys = degree, values = vertex id (ascending), so a stable sort by degree
+// orders each layer by (deg, id): Definition 3 restricted to one layer.
+__global__ void k_iota_keys(const int32_t *__restrict__ deg, int32_t n, uint64_t *keys,
+                            int32_t *vals) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    keys[i] = (uint64_t)(uint32_t)deg[i];
+    vals[i] = (int32_t)i;
+}
+
+// rank[order[i]] = i; degree of G* vertex (base + i) = sorted key
+__global__ void k_ranks(const uint64_t *__restrict__ sorted_deg, const int32_t *__restrict__ order,
+                        int32_t n, int32_t *rank, int32_t *deg_star, int32_t base) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    rank[order[i]] = (int32_t)i;
+    deg_star[base + i] = (int32_t)sorted_deg[i];
+}
+
+// ----- a3: projection + sorted adjacency -------------------------------------
+// U-side composite key (rank_u, rank_l): sorting it lists every U vertex's
+// neighbours in ascending L rank, i.e. ascending priority.
+__global__ void k_edge_keys(const int32_t *__restrict__ rows, const int32_t *__restrict__ adj_u,
+                            const int32_t *__restrict__ rank_u, const int32_t *__restrict__ rank_l,
+                            int64_t m, int bl, uint64_t *keys, int32_t *vals) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < m;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        keys[k] = ((uint64_t)(uint32_t)rank_u[rows[k]] << bl) | (uint64_t)(uint32_t)rank_l[adj_u[k]];
+        vals[k] = (int32_t)k;
+    }
+}
+
+__global__ void k_dup_check(const uint64_t *__restrict__ keys, int64_t m, int *err) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x + 1; k < m;
+         k += (int64_t)gridDim.x * blockDim.x)
+        if (keys[k] == keys[k - 1]) atomicOr(err, kErrDuplicate);
+}
+
+// U-side lists occupy G* slots [m, 2m); also builds the swapped key
+// (rank_l, rank_u) whose stable sort on the rank_l bits yields the L side.
+__global__ void k_emit_u_side(const uint64_t *__restrict__ keys, const int32_t *__restrict__ vals,
+                              int64_t m, int bl, int bu, int32_t l, int32_t *adj_star,
+                              int32_t *eid_star, int32_t *rows_star, uint64_t *keys2,
+                              int32_t *vals2) {
+    const uint64_t mask_l = (bl >= 64) ? ~0ull : ((1ull << bl) - 1ull);
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < m;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t key = keys[k];
+        uint32_t ru = (uint32_t)(key >> bl);
+        uint32_t rl = (uint32_t)(key & mask_l);
+        adj_star[m + k] = (int32_t)rl;
+        eid_star[m + k] = vals[k];
+        rows_star[m + k] = l + (int32_t)ru;
+        keys2[k] = ((uint64_t)rl << bu) | (uint64_t)ru;
+        vals2[k] = vals[k];
+    }
+}
+
+__global__ void k_emit_l_side(const uint64_t *__restrict__ keys2, const int32_t *__restrict__ vals2,
+                              int64_t m, int bu, int32_t l, int32_t *adj_star, int32_t *eid_star,
+                              int32_t *rows_star) {
+    const uint64_t mask_u = (1ull << bu) - 1ull;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < m;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t key = keys2[k];
+        adj_star[k] = l + (int32_t)(key & mask_u);
+        eid_star[k] = vals2[k];
+        rows_star[k] = (int32_t)(key >> bu);
+    }
+}
+
+__global__ void k_deg_to_i64(const int32_t *__restrict__ d, int32_t n, int64_t *out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = d[i];
+}
+
+// ----- a4: orientation cut and per-start work ---------------------------------
+// cut[x] = |{y in N(x): p(y) < p(x)}|.  Lists are ascending in priority and
+// the degree of G* ids is non-decreasing inside a layer, so the cut is a
+// lower bound on degree: for x in L a U neighbour of equal degree has higher
+// priority (U ids > L ids); for x in U an L neighbour of equal degree is lower.
+__global__ void k_cut(const int64_t *__restrict__ off, const int32_t *__restrict__ adj,
+                      const int32_t *__restrict__ deg_star, int32_t n, int32_t l, int32_t *cut) {
+    int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= n) return;
+    const int64_t b = off[x];
+    int64_t lo = 0, hi = off[x + 1] - b;
+    const int32_t dx = deg_star[x];
+    const bool in_u = x >= l;
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        int32_t dy = deg_star[adj[b + mid]];
+        bool lower = in_u ? (dy <= dx) : (dy < dx);
+        if (lower) lo = mid + 1; else hi = mid;
+    }
+    cut[x] = (int32_t)lo;
+}
+
+// plen[e] for a middle slot e = (x, v): the number of ends w in N(v) with
+// p(w) < p(x), i.e. the prefix of v's ascending list below x.
+__global__ void k_plen(const int64_t *__restrict__ off, const int32_t *__restrict__ adj,
+                       const int32_t *__restrict__ rows, const int32_t *__restrict__ cut,
+                       int64_t slots, int32_t *plen) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < slots;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t x = rows[e];
+        int32_t out = 0;
+        if (e - off[x] < cut[x]) {
+            const int32_t v = adj[e];
+            const int64_t b = off[v];
+            int64_t lo = 0, hi = off[v + 1] - b;
+            while (lo < hi) {
+                int64_t mid = (lo + hi) >> 1;
+                if (adj[b + mid] < x) lo = mid + 1; else hi = mid;
+            }
+            out = (int32_t)lo;
+        }
+        plen[e] = out;
+    }
+}
+
+// work[x] = Σ plen over x's middle slots; one warp per start.
+__global__ void k_work(const int64_t *__restrict__ off, const int32_t *__restrict__ cut,
+                       const int32_t *__restrict__ plen, int32_t n, uint64_t *work,
+                       unsigned long long *total) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    unsigned long long tot = 0;
+    for (int64_t x = warp; x < n; x += nwarps) {
+        const int64_t b = off[x];
+        const int32_t c = cut[x];
+        unsigned long long s = 0;
+        for (int32_t j = lane; j < c; j += 32) s += (unsigned)plen[b + j];
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) s += __shfl_xor_sync(0xffffffffu, s, d);
+        if (lane == 0) work[x] = s;
+        tot += s;
+    }
+    if (lane == 0 && tot) atomicAdd(total, tot);
+}
+
+// ----- a5: bins and schedule ---------------------------------------------------
+__global__ void k_sched_keys(const uint64_t *__restrict__ work, int32_t n, uint64_t maxw,
+                             uint64_t *keys, int32_t *vals) {
+    int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= n) return;
+    keys[x] = maxw - work[x];   // ascending key = descending work; zero work last
+    vals[x] = (int32_t)x;
+}
+
+// counts[0] = dense starts, [1] = hash starts, [2] = warp starts
+__global__ void k_classify(const uint64_t *__restrict__ work, int32_t n, uint64_t warp_max,
+                           uint64_t hash_max, unsigned long long *counts) {
+    unsigned long long c0 = 0, c1 = 0, c2 = 0;
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
+         x += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t w = work[x];
+        if (w > hash_max) ++c0;
+        else if (w > warp_max) ++c1;
+        else if (w > 0) ++c2;
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        c0 += __shfl_xor_sync(0xffffffffu, c0, d);
+        c1 += __shfl_xor_sync(0xffffffffu, c1, d);
+        c2 += __shfl_xor_sync(0xffffffffu, c2, d);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (c0) atomicAdd(&counts[0], c0);
+        if (c1) atomicAdd(&counts[1], c1);
+        if (c2) atomicAdd(&counts[2], c2);
+    }
+}
+
+__device__ __forceinline__ int32_t dense_chunks(int32_t x, int32_t l, int32_t cut) {
+    const int64_t R = x >= l ? x - l : x;
+    const int64_t S = cut > (int32_t)kNarrowMaxCut ? kDense32 : kDense16;
+    return (int32_t)((R + S - 1) / S);
+}
+
+__global__ void k_chunk_counts(const int32_t *__restrict__ order, int64_t n_dense, int32_t l,
+                               const int32_t *__restrict__ cut, int64_t *nch) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_dense) return;
+    int32_t x = order[i];
+    nch[i] = dense_chunks(x, l, cut[x]);
+}
+
+__global__ void k_emit_items(const int32_t *__restrict__ order, int64_t n_dense, int64_t n_hash,
+                             int64_t n_warp, const int64_t *__restrict__ nch_scan, int32_t l,
+                             const int32_t *__restrict__ cut, int2 *cta_items, int32_t *warp_items) {
+    const int64_t total_dense = nch_scan[n_dense];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_dense + n_hash + n_warp;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int32_t x = order[i];
+        if (i < n_dense) {
+            int64_t o = nch_scan[i];
+            int32_t k = dense_chunks(x, l, cut[x]);
+            for (int32_t c = 0; c < k; ++c) cta_items[o + c] = make_int2(x, c);
+        } else if (i < n_dense + n_hash) {
+            cta_items[total_dense + (i - n_dense)] = make_int2(x, -1);
+        } else {
+            warp_items[i - n_dense - n_hash] = x;
+        }
+    }
+}
+
+unsigned grid_stride_blocks(int64_t n) {
+    int64_t b = (n + kT - 1) / kT;
+    if (b > 152 * 64) b = 152 * 64;
+    if (b < 1) b = 1;
+    return (unsigned)b;
+}
+
+}  // namespace
+
+int prepare_graph(const bfc_csr *csr, const bfc_options *opt, cudaStream_t s, Graph *g) {
+    const int32_t r = csr->num_u, l = csr->num_l;
+    const int64_t m = csr->num_edges;
+    const int32_t n = r + l;
+    g->r = r; g->l = l; g->n = n; g->m = m;
+    g->opt = *opt;
+    g->stream = s;
+    g->mem.stream = s;
+
+    Allocs tmp;
+    tmp.stream = s;
+    struct TmpGuard { Allocs *a; ~TmpGuard() { a->release(); } } guard{&tmp};
+
+#define GET(allocs, ptr, cnt)                                                         \
+    do {                                                                              \
+        cudaError_t e_ = (allocs).get(&(ptr), (size_t)(cnt));                         \
+        if (e_ != cudaSuccess) {                                                      \
+            set_last_error(std::string("device allocation failed: ") + #ptr);         \
+            return BFC_ERR_OUT_OF_MEMORY;                                             \
+        }                                                                             \
+    } while (0)
+
+    // ---- kept arrays
+    GET(g->mem, g->err, 4);
+    GET(g->mem, g->rank_u, r);
+    GET(g->mem, g->rank_l, l);
+    GET(g->mem, g->off, (int64_t)n + 1);
+    GET(g->mem, g->adj, 2 * m);
+    GET(g->mem, g->eid, 2 * m);
+    GET(g->mem, g->plen, 2 * m);
+    GET(g->mem, g->cut, n);
+    GET(g->mem, g->work, n);
+    GET(g->mem, g->cursors, 4);
+    GET(g->mem, g->acc, 2);
+    GET(g->mem, g->pv, n);
+    BFC_CUDA(cudaMemsetAsync(g->err, 0, 4 * sizeof(int), s));
+
+    // ---- validation of the caller's CSR (memory safety of everything below)
+    k_check_offsets<<<blocks_for((int64_t)r + 1), kT, 0, s>>>(csr->off_u, r, m, g->err); note_launch();
+    BFC_CUDA(cudaGetLastError());
+    int herr = 0;
+    BFC_CUDA(cudaMemcpyAsync(&herr, g->err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    BFC_CUDA(cudaStreamSynchronize(s));
+    if (herr) { set_last_error("off_u is not a CSR offset array of num_edges entries"); return BFC_ERR_INVALID_GRAPH; }
+    if (m > 0) {
+        k_check_ids<<<grid_stride_blocks(m), kT, 0, s>>>(csr->adj_u, m, l, g->err); note_launch();
+        BFC_CUDA(cudaGetLastError());
+        BFC_CUDA(cudaMemcpyAsync(&herr, g->err, sizeof(int), cudaMemcpyDeviceToHost, s));
+        BFC_CUDA(cudaStreamSynchronize(s));
+        if (herr) { set_last_error("adj_u holds an id outside [0, num_l)"); return BFC_ERR_INVALID_GRAPH; }
+    }
+
+    // ---- temporaries
+    const int64_t nsort = std::max<int64_t>({(int64_t)r, (int64_t)l, m, (int64_t)n, 1});
+    uint64_t *k0, *k1;
+    int32_t *v0, *v1, *deg_u, *deg_l, *deg_star, *rows, *rows_star, *heads, *order_u, *order_l;
+    uint32_t *hist, *hist_tmp;
+    int64_t *scan64_tmp, *deg64;
+    int32_t *maxdeg;
+    unsigned long long *red;
+    GET(tmp, k0, nsort + 1); GET(tmp, k1, nsort + 1);
+    GET(tmp, v0, nsort); GET(tmp, v1, nsort);
+    GET(tmp, deg_u, r); GET(tmp, deg_l, l); GET(tmp, deg_star, n);
+    GET(tmp, rows, m); GET(tmp, heads, m); GET(tmp, rows_star, 2 * m);
+    GET(tmp, order_u, r); GET(tmp, order_l, l);
+    GET(tmp, hist, radix_hist_elems(nsort));
+    GET(tmp, hist_tmp, scan_tmp_elems<uint32_t>((int64_t)radix_hist_elems(nsort)));
+    GET(tmp, scan64_tmp, std::max(scan_tmp_elems<int64_t>((int64_t)n + 1),
+                                  max_scan_tmp_elems(m)));
+    GET(tmp, deg64, (int64_t)n + 1);
+    GET(tmp, maxdeg, 4);
+    GET(tmp, red, 8);
+
+    // ---- a1: degrees (and the head of each U row for the slot -> row map)
+    BFC_CUDA(cudaMemsetAsync(deg_l, 0, sizeof(int32_t) * std::max<int64_t>(l, 1), s));
+    BFC_CUDA(cudaMemsetAsync(heads, 0, sizeof(int32_t) * std::max<int64_t>(m, 1), s));
+    if (r > 0) { k_deg_u<<<blocks_for(r), kT, 0, s>>>(csr->off_u, r, deg_u, heads); note_launch(); }
+    if (m > 0) { k_deg_l<<<grid_stride_blocks(m), kT, 0, s>>>(csr->adj_u, m, deg_l); note_launch(); }
+    BFC_CUDA(cudaGetLastError());
+    BFC_CUDA(reduce_max_i32(deg_u, r, maxdeg, s));
+    BFC_CUDA(reduce_max_i32(deg_l, l, maxdeg + 1, s));
+    int32_t hmax[2] = {0, 0};
+    BFC_CUDA(cudaMemcpyAsync(hmax, maxdeg, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    BFC_CUDA(cudaStreamSynchronize(s));
+    g->info.max_deg_u = hmax[0];
+    g->info.max_deg_l = hmax[1];
+
+    // ---- a2: per-layer priority ranks by a stable sort on degree
+    int which = 0;
+    if (r > 0) {
+        k_iota_keys<<<blocks_for(r), kT, 0, s>>>(deg_u, r, k0, v0); note_launch();
+        BFC_CUDA(cudaGetLastError());
+        BFC_CUDA(radix_sort_pairs(k0, v0, k1, v1, r, 0, bits_for((uint64_t)hmax[0]), hist,
+                                  hist_tmp, s, &which));
+        const uint64_t *ks = which ? k1 : k0;
+        const int32_t *vs = which ? v1 : v0;
+        BFC_CUDA(cudaMemcpyAsync(order_u, vs, sizeof(int32_t) * r, cudaMemcpyDeviceToDevice, s));
+        k_ranks<<<blocks_for(r), kT, 0, s>>>(ks, vs, r, g->rank_u, deg_star, l); note_launch();
+        BFC_CUDA(cudaGetLastError());
+    }
+    if (l > 0) {
+        k_iota_keys<<<blocks_for(l), kT, 0, s>>>(deg_l, l, k0, v0); note_launch();
+        BFC_CUDA(cudaGetLastError());
+        BFC_CUDA(radix_sort_pairs(k0, v0, k1, v1, l, 0, bits_for((uint64_t)hmax[1]), hist,
+                                  hist_tmp, s, &which));
+        const uint64_t *ks = which ? k1 : k0;
+        const int32_t *vs = which ? v1 : v0;
+        BFC_CUDA(cudaMemcpyAsync(order_l, vs, sizeof(int32_t) * l, cudaMemcpyDeviceToDevice, s));
+        k_ranks<<<blocks_for(l), kT, 0, s>>>(ks, vs, l, g->rank_l, deg_star, 0); note_launch();
+        BFC_CUDA(cudaGetLastError());
+    }
+
+    // ---- a3: G* offsets and priority-sorted lists
+    if (n > 0) {
+        k_deg_to_i64<<<blocks_for(n), kT, 0, s>>>(deg_star, n, deg64); note_launch();
+        BFC_CUDA(cudaGetLastError());
+    }
+    BFC_CUDA(scan_exclusive<int64_t>(deg64, g->off, n, scan64_tmp, s));
+    const int bu = bits_for(r > 0 ? (uint64_t)(r - 1) : 0);
+    const int bl = bits_for(l > 0 ? (uint64_t)(l - 1) : 0);
+    if (m > 0) {
+        BFC_CUDA(max_scan_inclusive(heads, rows, m, (int32_t *)scan64_tmp, s));
+        k_edge_keys<<<grid_stride_blocks(m), kT, 0, s>>>(rows, csr->adj_u, g->rank_u, g->rank_l, m,
+                                                          bl, k0, v0); note_launch();
+        BFC_CUDA(cudaGetLastError());
+        BFC_CUDA(radix_sort_pairs(k0, v0, k1, v1, m, 0, bu + bl, hist, hist_tmp, s, &which));
+        uint64_t *ks = which ? k1 : k0;
+        int32_t *vs = which ? v1 : v0;
+        uint64_t *ko = which ? k0 : k1;
+        int32_t *vo = which ? v0 : v1;
+        if (opt->validate) {
+            k_dup_check<<<grid_stride_blocks(m), kT, 0, s>>>(ks, m, g->err); note_launch();
+            BFC_CUDA(cudaGetLastError());
+        }
+        k_emit_u_side<<<grid_stride_blocks(m), kT, 0, s>>>(ks, vs, m, bl, bu, l, g->adj, g->eid,
+                                                            rows_star, ko, vo); note_launch();
+        BFC_CUDA(cudaGetLastError());
+        // stable sort of the (rank_l, rank_u) keys on the rank_l bits only:
+        // the input is already ascending in rank_u within each rank_l
+        int which2 = 0;
+        BFC_CUDA(radix_sort_pairs(ko, vo, ks, vs, m, bu, bu + bl, hist, hist_tmp, s, &which2));
+        const uint64_t *k2 = which2 ? ks : ko;
+        const int32_t *v2 = which2 ? vs : vo;
+        k_emit_l_side<<<grid_stride_blocks(m), kT, 0, s>>>(k2, v2, m, bu, l, g->adj, g->eid,
+                                                            rows_star); note_launch();
+        BFC_CUDA(cudaGetLastError());
+        if (opt->validate) {
+            BFC_CUDA(cudaMemcpyAsync(&herr, g->err, sizeof(int), cudaMemcpyDeviceToHost, s));
+            BFC_CUDA(cudaStreamSynchronize(s));
+            if (herr & kErrDuplicate) { set_last_error("duplicate edge"); return BFC_ERR_INVALID_GRAPH; }
+        }
+    }
+
+    // ---- a4: cut, per-middle prefix lengths, per-start work, W
+    BFC_CUDA(cudaMemsetAsync(red, 0, 8 * sizeof(unsigned long long), s));
+    if (n > 0) {
+        k_cut<<<blocks_for(n), kT, 0, s>>>(g->off, g->adj, deg_star, n, l, g->cut); note_launch();
+        BFC_CUDA(cudaGetLastError());
+    }
+    if (m > 0) {
+        k_plen<<<grid_stride_blocks(2 * m), kT, 0, s>>>(g->off, g->adj, rows_star, g->cut, 2 * m,
+                                                         g->plen); note_launch();
+        BFC_CUDA(cudaGetLastError());
+    }
+    if (n > 0) {
+        k_work<<<grid_stride_blocks((int64_t)n * 32), kT, 0, s>>>(g->off, g->cut, g->plen, n,
+                                                                   g->work, red); note_launch();
+        BFC_CUDA(cudaGetLastError());
+        BFC_CUDA(reduce_max_u64(g->work, n, red + 1, s));
+    }
+    unsigned long long hred[2] = {0, 0};
+    BFC_CUDA(cudaMemcpyAsync(hred, red, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    BFC_CUDA(cudaStreamSynchronize(s));
+    g->info.wedges = hred[0];
+    g->info.max_start_work = hred[1];
+
+    // ---- a5: heaviest-first order and bins
+    const uint64_t warp_max = (uint64_t)opt->warp_max_work;
+    const uint64_t hash_max = (uint64_t)opt->hash_max_work;
+    int64_t n_dense = 0, n_hash = 0, n_warp = 0, n_items = 0;
+    if (n > 0 && hred[0] > 0) {
+        k_sched_keys<<<blocks_for(n), kT, 0, s>>>(g->work, n, hred[1], k0, v0); note_launch();
+        BFC_CUDA(cudaGetLastError());
+        BFC_CUDA(radix_sort_pairs(k0, v0, k1, v1, n, 0, bits_for(hred[1]), hist, hist_tmp, s,
+                                  &which));
+        const int32_t *order = which ? v1 : v0;
+        k_classify<<<grid_stride_blocks(n), kT, 0, s>>>(g->work, n, warp_max, hash_max, red + 2); note_launch();
+        BFC_CUDA(cudaGetLastError());
+        unsigned long long hc[3];
+        BFC_CUDA(cudaMemcpyAsync(hc, red + 2, 3 * sizeof(unsigned long long),
+                                 cudaMemcpyDeviceToHost, s));
+        BFC_CUDA(cudaStreamSynchronize(s));
+        n_dense = (int64_t)hc[0]; n_hash = (int64_t)hc[1]; n_warp = (int64_t)hc[2];
+        int64_t *nch = deg64;   // reuse: n_dense + 1 <= n + 1 entries
+        if (n_dense > 0) {
+            k_chunk_counts<<<blocks_for(n_dense), kT, 0, s>>>(order, n_dense, l, g->cut, nch); note_launch();
+            BFC_CUDA(cudaGetLastError());
+        }
+        // the sorted keys are no longer needed; the other key buffer holds the scan
+        int64_t *nch_scan = reinterpret_cast<int64_t *>(which ? k0 : k1);
+        BFC_CUDA(scan_exclusive<int64_t>(nch, nch_scan, n_dense, scan64_tmp, s));
+        int64_t h_dense_items = 0;
+        BFC_CUDA(cudaMemcpyAsync(&h_dense_items, nch_scan + n_dense, sizeof(int64_t),
+                                 cudaMemcpyDeviceToHost, s));
+        BFC_CUDA(cudaStreamSynchronize(s));
+        n_items = h_dense_items + n_hash;
+        GET(g->mem, g->cta_items, std::max<int64_t>(n_items, 1));
+        GET(g->mem, g->warp_items, std::max<int64_t>(n_warp, 1));
+        if (n_dense + n_hash + n_warp > 0) {
+            k_emit_items<<<grid_stride_blocks(n_dense + n_hash + n_warp), kT, 0, s>>>(
+                order, n_dense, n_hash, n_warp, nch_scan, l, g->cut, g->cta_items, g->warp_items); note_launch();
+            BFC_CUDA(cudaGetLastError());
+        }
+        g->info.dense_items = h_dense_items;
+    } else {
+        GET(g->mem, g->cta_items, 1);
+        GET(g->mem, g->warp_items, 1);
+    }
+    g->n_cta_items = n_items;
+    g->n_warp_items = n_warp;
+    g->info.num_u = r; g->info.num_l = l; g->info.num_edges = m;
+    g->info.starts_with_work = n_dense + n_hash + n_warp;
+    g->info.dense_starts = n_dense;
+    g->info.hash_starts = n_hash;
+    g->info.warp_starts = n_warp;
+    g->info.device_bytes = (int64_t)g->mem.total;
+    BFC_CUDA(cudaStreamSynchronize(s));
+#undef GET
+    return BFC_OK;
+}
+
+}  // namespace bfc

@@ -1,0 +1,95 @@
+"""The C-ABI library loads and exports everything include/bfc.h declares;
+argument checks that happen before any CUDA call.  No GPU needed."""
+import ctypes
+import os
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def bfc():
+    from paper_1812_00283_gb300 import build
+    build.build()
+    from paper_1812_00283_gb300 import bfc as b
+    return b
+
+
+def test_exports_every_declared_symbol(bfc):
+    names = bfc.header_functions()
+    assert "bfc_prepare" in names and "bfc_count_edges" in names
+    lib = bfc.library()
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_headers_all_checked(bfc):
+    inc = os.path.join(ROOT, "include")
+    assert sorted(os.listdir(inc)) == ["bfc.h"]
+
+
+def test_version_and_strings(bfc):
+    assert bfc.bfc_version() >= 100
+    for code, name in bfc.STATUS.items():
+        assert bfc.bfc_status_string(code) == name
+    assert bfc.bfc_status_string(99) == "BFC_ERR_UNKNOWN"
+
+
+def test_options_defaults(bfc):
+    o = bfc.bfc_options_init()
+    assert (o.validate, o.warp_max_work, o.hash_max_work, o.num_ctas) == (1, 256, 16384, 0)
+
+
+def test_struct_layouts_match_header(bfc, tmp_path):
+    # compile a probe against the public header and compare sizes/offsets with ctypes
+    import subprocess
+    src = tmp_path / "probe.c"
+    src.write_text('''
+#include <stdio.h>
+#include <stddef.h>
+#include "bfc.h"
+int main(void) {
+  printf("%zu %zu %zu\\n", sizeof(bfc_csr), sizeof(bfc_options), sizeof(bfc_info));
+  printf("%zu %zu %zu\\n", offsetof(bfc_csr, adj_u), offsetof(bfc_options, reserved),
+         offsetof(bfc_info, max_deg_l));
+  return 0;
+}
+''')
+    exe = tmp_path / "probe"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()
+    sizes = [int(x) for x in out]
+    assert sizes[:3] == [ctypes.sizeof(bfc.bfc_csr), ctypes.sizeof(bfc.bfc_options),
+                         ctypes.sizeof(bfc.bfc_info)]
+    assert sizes[3:] == [bfc.bfc_csr.adj_u.offset, bfc.bfc_options.reserved.offset,
+                         bfc.bfc_info.max_deg_l.offset]
+
+
+@pytest.mark.parametrize("case", ["null", "negative", "too_many_edges", "bad_option", "null_ptr"])
+def test_argument_errors_before_cuda(bfc, case):
+    lib = bfc.library()
+    h = ctypes.c_void_p()
+    opts = bfc.bfc_options_init()
+    if case == "null":
+        rc = lib.bfc_prepare(None, None, None, ctypes.byref(h))
+    else:
+        csr = bfc.bfc_csr(3, 3, 4, 1234, 5678)
+        if case == "negative":
+            csr.num_u = -1
+        elif case == "too_many_edges":
+            csr.num_edges = 1 << 31
+        elif case == "bad_option":
+            opts.warp_max_work = 100000
+        elif case == "null_ptr":
+            csr.off_u = None
+        rc = lib.bfc_prepare(ctypes.byref(csr), ctypes.byref(opts), None, ctypes.byref(h))
+    assert rc == 1
+    assert bfc.bfc_last_error()
+
+
+def test_null_graph_calls(bfc):
+    lib = bfc.library()
+    assert lib.bfc_count(None, None, None) == 1
+    assert lib.bfc_sync(None, None) == 1
+    lib.bfc_release(None)
