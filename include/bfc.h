@@ -85,7 +85,10 @@ typedef struct bfc_options {
                                get dense shared-memory counters over chunks of
                                their end range */
     int32_t num_ctas;       /* persistent grid size; 0 (default) = one CTA per SM */
-    int32_t reserved[12];   /* must be zero */
+    int32_t wide_positions; /* 1: count with 64-bit adjacency positions even when
+                               32 bits suffice (they are used automatically when
+                               the graph has 2^30 edges or more); default 0 */
+    int32_t reserved[11];   /* must be zero */
 } bfc_options;
 
 /* Figures of a prepared graph (host values). */

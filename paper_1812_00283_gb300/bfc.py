@@ -33,7 +33,7 @@ class bfc_csr(ctypes.Structure):
 
 class bfc_options(ctypes.Structure):
     _fields_ = [("validate", c_int32), ("warp_max_work", c_int32), ("hash_max_work", c_int32),
-                ("num_ctas", c_int32), ("reserved", c_int32 * 12)]
+                ("num_ctas", c_int32), ("wide_positions", c_int32), ("reserved", c_int32 * 11)]
 
 
 class bfc_info(ctypes.Structure):

@@ -87,7 +87,11 @@ static int check_options(const bfc_options *o) {
         bfc::set_last_error("num_ctas must be >= 0");
         return BFC_ERR_INVALID_ARGUMENT;
     }
-    for (int i = 0; i < 12; ++i)
+    if (o->wide_positions != 0 && o->wide_positions != 1) {
+        bfc::set_last_error("wide_positions must be 0 or 1");
+        return BFC_ERR_INVALID_ARGUMENT;
+    }
+    for (int i = 0; i < 11; ++i)
         if (o->reserved[i] != 0) {
             bfc::set_last_error("reserved option fields must be zero");
             return BFC_ERR_INVALID_ARGUMENT;

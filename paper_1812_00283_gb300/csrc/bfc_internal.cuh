@@ -33,6 +33,9 @@ constexpr int kWarpRegion = kCounterBytes / kCountWarps;  // 6 KB of counters pe
 constexpr int kWarpSlots = 512;                           // warp hash: 2 KB keys + 2 KB counts
 constexpr int kWarpMaxWork = kWarpSlots / 2;              // 256 wedges
 constexpr uint32_t kNarrowMaxCut = 65535;                 // counts fit 16 bits when cut <= this
+constexpr int kChunkUnit = kDense32;                      // end-range chunk unit of the boundary table
+static_assert(kDense16 % kChunkUnit == 0, "narrow chunks must be whole table units");
+constexpr int64_t kChunkTableMaxEntries = 1ll << 29;      // 2 GB of int32 at most
 
 // device error bits (graph-owned error word)
 constexpr int kErrBadOffsets = 1;
@@ -120,6 +123,11 @@ struct Graph {
     unsigned long long *acc = nullptr;  // [1] device accumulator for ⋈_G
     unsigned long long *pv = nullptr;   // [n] per-vertex scratch in G* ids (allocated on demand? no: in prepare)
     int *err = nullptr;            // device error word
+    // chunk-boundary table: for vertex v of G*, entry c is the position in
+    // N(v) of the first neighbour whose rank in its layer is >= c * kChunkUnit
+    int32_t *coff = nullptr;
+    int32_t coff_u1 = 0;   // entries per L vertex (its neighbours are U vertices)
+    int32_t coff_l1 = 0;   // entries per U vertex
 };
 
 // ---------------------------------------------------------------------------

@@ -44,15 +44,27 @@ struct CountParams {
     unsigned long long *acc;
     unsigned long long *pv;   // [n] in G* ids
     unsigned long long *pe;   // [m] by edge id
+    const int32_t *__restrict__ coff;  // chunk-boundary table (nullable)
+    int32_t coff_u1, coff_l1;          // entries per L vertex / per U vertex
     int64_t adj_len;
     int32_t l;
     int *err;
 };
 
+// Middles per batch: two per thread when adjacency positions fit 32 bits,
+// one otherwise (shared memory holds the compacted batch).
+template <typename Pos>
+struct Batch {
+    static constexpr int kSize = sizeof(Pos) == 4 ? 2 * kCountThreads : kCountThreads;
+    static constexpr int kPer = kSize / kCountThreads;
+};
+
+template <int MODE, typename Pos>
 struct SharedCTA {
-    long long excl[kCountThreads];      // exclusive prefix of batch lengths
-    long long src[kCountThreads];       // adjacency position of a batch entry minus its prefix
-    unsigned long long msum[kCountThreads];  // second walk: Σ δ per middle of the batch
+    static constexpr int kB = Batch<Pos>::kSize;
+    int32_t start[kB + 1];              // compacted batch: exclusive prefix of run lengths (+ sentinel)
+    Pos src[kB];                        // compacted batch: adjacency position of a run minus its prefix
+    unsigned long long msum[MODE == kModeTotal ? 1 : kB];  // second walk: Σ δ per compacted middle
     long long wtot[32];
     unsigned long long red[32];
     int item;
@@ -72,7 +84,8 @@ __device__ __forceinline__ int lower_bound_g(const int32_t *a, int len, int32_t 
 }
 
 // Exclusive block scan of one int64 per thread (1024 threads).
-__device__ __forceinline__ long long block_excl_scan(long long v, SharedCTA &sh, long long *total) {
+template <class SH>
+__device__ __forceinline__ long long block_excl_scan(long long v, SH &sh, long long *total) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     long long x = v;
 #pragma unroll
@@ -97,7 +110,8 @@ __device__ __forceinline__ long long block_excl_scan(long long v, SharedCTA &sh,
     return before + x - v;
 }
 
-__device__ __forceinline__ unsigned long long block_sum(unsigned long long v, SharedCTA &sh) {
+template <class SH>
+__device__ __forceinline__ unsigned long long block_sum(unsigned long long v, SH &sh) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
@@ -113,13 +127,12 @@ __device__ __forceinline__ unsigned long long block_sum(unsigned long long v, Sh
     return t;   // valid in warp 0
 }
 
-// last j in [0, 1024) with excl[j] <= k (excl[0] = 0 <= k)
-__device__ __forceinline__ int batch_entry(const long long *excl, long long k) {
-    int lo = 0, hi = kCountThreads;
-#pragma unroll
-    for (int it = 0; it < 10; ++it) {
+// largest j in [0, n) with a[j] <= k, given a[0] <= k and a ascending
+__device__ __forceinline__ int last_le(const int32_t *a, int n, int32_t k) {
+    int lo = 0, hi = n;
+    while (hi - lo > 1) {
         int mid = (lo + hi) >> 1;
-        if (excl[mid] <= k) lo = mid; else hi = mid;
+        if (a[mid] <= k) lo = mid; else hi = mid;
     }
     return lo;
 }
@@ -158,98 +171,184 @@ __device__ __forceinline__ uint32_t get16(const uint32_t *w32, int idx) {
 
 enum CounterKind { kDenseNarrow = 0, kDenseWide = 1, kHash = 2 };
 
+// The counter operation for one wedge (x, middle, w) whose end id is w and
+// whose end sits at adjacency slot pos.  First walk: increment count_wedge(w)
+// and return the old value.  Second walk: read the final count and attribute
+// δ = count − 1 to the edge (middle, w) and to the middle's batch sum.
+template <int MODE, int KIND, bool kSecond, typename Pos>
+__device__ __forceinline__ unsigned long long wedge_op(const CountParams &p, int32_t w,
+                                                       Pos pos, int q, int32_t lb, int32_t lo,
+                                                       int32_t span, uint32_t hmask,
+                                                       unsigned char *ctr,
+                                                       unsigned long long *msum) {
+    uint32_t *w32 = reinterpret_cast<uint32_t *>(ctr);
+    uint32_t c;
+    if (KIND == kHash) {
+        int32_t *hkeys = reinterpret_cast<int32_t *>(ctr);
+        uint32_t *hcnt = reinterpret_cast<uint32_t *>(ctr + (size_t)(hmask + 1) * 4);
+        const int slot = hash_find(hkeys, hmask, w - lb, !kSecond);
+        if (slot < 0) { atomicOr(p.err, kErrHashFull); return 0; }
+        if (!kSecond) return inc16(hcnt, slot);
+        c = get16(hcnt, slot);
+    } else {
+        const int idx = w - lb - lo;
+#if BFC_CHECKED
+        if ((uint32_t)idx >= (uint32_t)span) { atomicOr(p.err, kErrBounds); return 0; }
+#endif
+        if (!kSecond) return (KIND == kDenseWide) ? atomicAdd(w32 + idx, 1u) : inc16(w32, idx);
+        c = (KIND == kDenseWide) ? w32[idx] : get16(w32, idx);
+    }
+    const unsigned long long delta = (unsigned long long)c - 1ull;
+    if (delta) {
+        if (MODE == kModeEdges) atomicAdd(p.pe + __ldg(p.eid + pos), delta);
+        atomicAdd(msum + q, delta);
+    }
+    return 0;
+}
+
 // One walk over the wedges of start x whose ends fall in [lb+lo, lb+hi).
 // kSecond = false: count (returns Σ old, i.e. Σ C(count, 2)).
 // kSecond = true : read the final counts and attribute δ = count − 1.
-template <int MODE, int KIND, bool kSecond>
+//
+// The middles of x are taken a batch at a time (2048, or 1024 with 64-bit
+// positions).  For each middle, the run of ends in range is [s0, s1) of its
+// list (from the chunk-boundary table, or a binary search when there is
+// none).  Non-empty runs are compacted and their concatenation is cut into
+// windows of 32 wedges; each warp takes a contiguous range of windows.
+// Inside a window the run of every lane is found from a 32-bit mask of run
+// starts (reduce-or + popc), so no search is needed per wedge, and four
+// windows are in flight per iteration so their end loads overlap.
+template <int MODE, int KIND, bool kSecond, typename Pos, class SH>
 __device__ unsigned long long cta_walk(const CountParams &p, int32_t x, int32_t lb, int32_t lo,
                                        int32_t hi, int32_t R, uint32_t hmask, unsigned char *ctr,
-                                       SharedCTA &sh) {
+                                       SH &sh) {
+    constexpr int kPer = Batch<Pos>::kPer;
+    constexpr int kB = Batch<Pos>::kSize;
+    constexpr int kU = 4;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t e0 = p.off[x];
     const int32_t nmid = p.cut[x];
-    uint32_t *w32 = reinterpret_cast<uint32_t *>(ctr);
-    int32_t *hkeys = reinterpret_cast<int32_t *>(ctr);
-    uint32_t *hcnt = reinterpret_cast<uint32_t *>(ctr + (size_t)(hmask + 1) * 4);
     const int32_t span = hi - lo;
+    const uint32_t le_mask = 0xffffffffu >> (31 - lane);
     unsigned long long acc = 0;
-    for (int32_t mb = 0; mb < nmid; mb += kCountThreads) {
-        const int32_t j = mb + tid;
-        long long len = 0, src = 0;
-        int32_t v = 0;
-        int64_t e = 0;
-        if (j < nmid) {
-            e = e0 + j;
-            v = p.adj[e];
-            const int32_t pl = p.plen[e];
-            const int64_t b = p.off[v];
-            int32_t s0 = 0, s1 = pl;
-            if (KIND != kHash) {
-                if (lo > 0) s0 = lower_bound_g(p.adj + b, pl, lb + lo);
-                if (hi < R) s1 = lower_bound_g(p.adj + b, pl, lb + hi);
-            }
-            len = s1 - s0;
-            src = b + s0;
-        }
-        long long total;
-        const long long excl = block_excl_scan(len, sh, &total);
-        sh.excl[tid] = excl;
-        sh.src[tid] = src - excl;
-        if (kSecond) sh.msum[tid] = 0;
-        __syncthreads();
-        for (long long k0 = (long long)warp * 32; k0 < total; k0 += kCountThreads) {
-            const long long k = k0 + lane;
-            if (k < total) {
-                const int q = batch_entry(sh.excl, k);
-                const long long pos = sh.src[q] + k;
-#if BFC_CHECKED
-                if (pos < 0 || pos >= p.adj_len) { atomicOr(p.err, kErrBounds); continue; }
-#endif
-                const int32_t w = __ldg(p.adj + pos);
-                uint32_t c;
-                if (KIND == kHash) {
-                    const int slot = hash_find(hkeys, hmask, w - lb, !kSecond);
-                    if (slot < 0) { atomicOr(p.err, kErrHashFull); continue; }
-                    if (!kSecond) { acc += inc16(hcnt, slot); continue; }
-                    c = get16(hcnt, slot);
-                } else {
-                    const int idx = w - lb - lo;
-#if BFC_CHECKED
-                    if (idx < 0 || idx >= span) { atomicOr(p.err, kErrBounds); continue; }
-#endif
-                    if (!kSecond) {
-                        acc += (KIND == kDenseWide) ? atomicAdd(w32 + idx, 1u) : inc16(w32, idx);
-                        continue;
-                    }
-                    c = (KIND == kDenseWide) ? w32[idx] : get16(w32, idx);
-                }
-                if (kSecond) {
-                    const unsigned long long delta = (unsigned long long)c - 1ull;
-                    if (delta) {
-                        if (MODE == kModeEdges) atomicAdd(p.pe + __ldg(p.eid + pos), delta);
-                        atomicAdd(sh.msum + q, delta);
+    for (int32_t mb = 0; mb < nmid; mb += kB) {
+        int32_t len[kPer], v[kPer];
+        Pos src[kPer];
+        int64_t e[kPer];
+        long long packed_run = 0;
+        long long pk[kPer];
+#pragma unroll
+        for (int i = 0; i < kPer; ++i) {
+            const int32_t j = mb + i * kCountThreads + tid;
+            len[i] = 0; v[i] = 0; src[i] = 0; e[i] = 0;
+            if (j < nmid) {
+                e[i] = e0 + j;
+                v[i] = __ldg(p.adj + e[i]);
+                const int32_t pl = __ldg(p.plen + e[i]);
+                const int64_t b = __ldg(p.off + v[i]);
+                int32_t s0 = 0, s1 = pl;
+                if (KIND != kHash) {
+                    if (p.coff) {
+                        const int64_t tb = v[i] < p.l ? (int64_t)v[i] * p.coff_u1
+                                                      : (int64_t)p.l * p.coff_u1 + (int64_t)(v[i] - p.l) * p.coff_l1;
+                        if (lo > 0) s0 = __ldg(p.coff + tb + lo / kChunkUnit);
+                        if (hi < R) s1 = __ldg(p.coff + tb + hi / kChunkUnit);
+                    } else {
+                        if (lo > 0) s0 = lower_bound_g(p.adj + b, pl, lb + lo);
+                        if (hi < R) s1 = lower_bound_g(p.adj + b, pl, lb + hi);
                     }
                 }
+                len[i] = s1 - s0;
+                src[i] = (Pos)(b + s0);
+            }
+            // run length in the high bits, "non-empty" in the low 20 bits:
+            // one scan yields both the run offsets and the compacted slots
+            pk[i] = ((long long)len[i] << 20) | (len[i] > 0 ? 1 : 0);
+            packed_run += pk[i];
+        }
+        long long packed_total;
+        long long packed = block_excl_scan(packed_run, sh, &packed_total);
+        const int32_t total = (int32_t)(packed_total >> 20);
+        const int nnz = (int)(packed_total & 0xfffff);
+        int nzs[kPer];
+#pragma unroll
+        for (int i = 0; i < kPer; ++i) {
+            const int32_t excl = (int32_t)(packed >> 20);
+            nzs[i] = (int)(packed & 0xfffff);
+            if (len[i] > 0) {
+                sh.start[nzs[i]] = excl;
+                sh.src[nzs[i]] = src[i] - (Pos)excl;
+                if (kSecond) sh.msum[nzs[i]] = 0;
+            }
+            packed += pk[i];
+        }
+        if (tid == 0) sh.start[nnz] = total;
+        __syncthreads();
+        const int32_t nwin = (total + 31) >> 5;
+        int32_t wb = (int32_t)(((int64_t)warp * nwin) >> 5);
+        const int32_t wend = (int32_t)(((int64_t)(warp + 1) * nwin) >> 5);
+        if (wb < wend) {
+            int32_t k0 = wb << 5;
+            int q0 = last_le(sh.start, nnz, k0);
+            for (; wb < wend; wb += kU) {
+                int q[kU];
+                Pos pos[kU];
+                bool ok[kU];
+#pragma unroll
+                for (int u = 0; u < kU; ++u) {
+                    q[u] = 0;
+                    ok[u] = false;
+                    pos[u] = 0;
+                    if (wb + u < wend) {   // warp-uniform
+                        const int32_t kw = k0 + 32 * u;
+                        const int idx = q0 + 1 + lane;
+                        const int32_t d = (idx <= nnz ? sh.start[idx] : 0x7fffffff) - kw;
+                        const uint32_t m = __reduce_or_sync(0xffffffffu, d < 32 ? (1u << d) : 0u);
+                        q[u] = q0 + __popc(m & le_mask);
+                        q0 += __popc(__ballot_sync(0xffffffffu, d <= 32));
+                        ok[u] = kw + lane < total;
+                        if (ok[u]) pos[u] = sh.src[q[u]] + (Pos)(kw + lane);
+                    }
+                }
+                int32_t w[kU];
+#pragma unroll
+                for (int u = 0; u < kU; ++u) {
+#if BFC_CHECKED
+                    if (ok[u] && (unsigned long long)pos[u] >= (unsigned long long)p.adj_len) {
+                        atomicOr(p.err, kErrBounds);
+                        ok[u] = false;
+                    }
+#endif
+                    w[u] = ok[u] ? __ldg(p.adj + pos[u]) : 0;
+                }
+#pragma unroll
+                for (int u = 0; u < kU; ++u)
+                    if (ok[u]) acc += wedge_op<MODE, KIND, kSecond, Pos>(p, w[u], pos[u], q[u], lb, lo, span, hmask, ctr, sh.msum);
+                k0 += 32 * kU;
             }
         }
         __syncthreads();
-        if (kSecond && j < nmid) {
-            const unsigned long long d = sh.msum[tid];
-            if (d) {
-                if (MODE == kModeVertices) atomicAdd(p.pv + v, d);
-                if (MODE == kModeEdges) atomicAdd(p.pe + __ldg(p.eid + e), d);
+        if (kSecond) {
+#pragma unroll
+            for (int i = 0; i < kPer; ++i) {
+                if (len[i] > 0) {
+                    const unsigned long long dsum = sh.msum[nzs[i]];
+                    if (dsum) {
+                        if (MODE == kModeVertices) atomicAdd(p.pv + v[i], dsum);
+                        if (MODE == kModeEdges) atomicAdd(p.pe + __ldg(p.eid + e[i]), dsum);
+                    }
+                }
             }
         }
     }
-    (void)span;
     return acc;
 }
 
-template <int MODE, int KIND>
+template <int MODE, int KIND, typename Pos, class SH>
 __device__ unsigned long long cta_item_body(const CountParams &p, int32_t x, int32_t lb,
                                             int32_t lo, int32_t hi, int32_t R, uint32_t hmask,
-                                            unsigned char *ctr, SharedCTA &sh) {
-    unsigned long long acc = cta_walk<MODE, KIND, false>(p, x, lb, lo, hi, R, hmask, ctr, sh);
+                                            unsigned char *ctr, SH &sh) {
+    unsigned long long acc = cta_walk<MODE, KIND, false, Pos>(p, x, lb, lo, hi, R, hmask, ctr, sh);
     if (MODE != kModeTotal) {
         __syncthreads();
         if (MODE == kModeVertices) {
@@ -272,7 +371,7 @@ __device__ unsigned long long cta_item_body(const CountParams &p, int32_t x, int
                 }
             }
         }
-        cta_walk<MODE, KIND, true>(p, x, lb, lo, hi, R, hmask, ctr, sh);
+        cta_walk<MODE, KIND, true, Pos>(p, x, lb, lo, hi, R, hmask, ctr, sh);
         if (MODE == kModeVertices) {
             const unsigned long long t = block_sum(acc, sh);
             if (threadIdx.x == 0 && t) atomicAdd(p.pv + x, t);
@@ -288,9 +387,9 @@ __device__ __forceinline__ void zero_smem(unsigned char *p, int bytes, uint32_t 
     for (int i = threadIdx.x; i < n16; i += kCountThreads) q[i] = f;
 }
 
-template <int MODE>
+template <int MODE, typename Pos, class SH>
 __device__ unsigned long long cta_item(const CountParams &p, int2 item, unsigned char *ctr,
-                                       SharedCTA &sh) {
+                                       SH &sh) {
     const int32_t x = item.x;
     const int32_t lb = x >= p.l ? p.l : 0;
     const int32_t R = x - lb;
@@ -303,8 +402,8 @@ __device__ unsigned long long cta_item(const CountParams &p, int2 item, unsigned
         const int32_t span = hi - lo;
         zero_smem(ctr, wide ? span * 4 : ((span + 1) >> 1) * 4, 0u);
         __syncthreads();
-        acc = wide ? cta_item_body<MODE, kDenseWide>(p, x, lb, lo, hi, R, 0, ctr, sh)
-                   : cta_item_body<MODE, kDenseNarrow>(p, x, lb, lo, hi, R, 0, ctr, sh);
+        acc = wide ? cta_item_body<MODE, kDenseWide, Pos>(p, x, lb, lo, hi, R, 0, ctr, sh)
+                   : cta_item_body<MODE, kDenseNarrow, Pos>(p, x, lb, lo, hi, R, 0, ctr, sh);
     } else {
         const unsigned long long w = p.work[x];
         const unsigned long long bound = w < (unsigned long long)R ? w : (unsigned long long)R;
@@ -313,29 +412,35 @@ __device__ unsigned long long cta_item(const CountParams &p, int2 item, unsigned
         zero_smem(ctr, (int)cap * 4, 0xffffffffu);           // keys = -1
         zero_smem(ctr + (size_t)cap * 4, (int)cap * 2, 0u);  // packed 16-bit counts
         __syncthreads();
-        acc = cta_item_body<MODE, kHash>(p, x, lb, 0, R, R, cap - 1, ctr, sh);
+        acc = cta_item_body<MODE, kHash, Pos>(p, x, lb, 0, R, R, cap - 1, ctr, sh);
     }
     __syncthreads();
     return acc;
 }
 
 // ---- warp items -------------------------------------------------------------
+// The warp version of cta_walk for a light start: batches of 32 middles,
+// compacted runs and the same window masks, with a per-warp hash table.
 template <int MODE, bool kSecond>
 __device__ unsigned long long warp_walk(const CountParams &p, int32_t x, int32_t lb, uint32_t mask,
-                                        int32_t *keys, uint32_t *cnt, unsigned long long *msum) {
+                                        int32_t *keys, uint32_t *cnt, unsigned long long *msum,
+                                        int32_t *wstart, long long *wsrc) {
     const int lane = threadIdx.x & 31;
     const int64_t e0 = p.off[x];
     const int32_t nmid = p.cut[x];
+    const uint32_t le_mask = 0xffffffffu >> (31 - lane);
+    const uint32_t lt_mask = (1u << lane) - 1u;
     unsigned long long acc = 0;
     for (int32_t mb = 0; mb < nmid; mb += 32) {
         const int32_t j = mb + lane;
         int32_t len = 0, v = 0;
-        int64_t src = 0, e = 0;
+        long long src = 0;
+        int64_t e = 0;
         if (j < nmid) {
             e = e0 + j;
-            v = p.adj[e];
-            len = p.plen[e];
-            src = p.off[v];
+            v = __ldg(p.adj + e);
+            len = __ldg(p.plen + e);
+            src = __ldg(p.off + v);
         }
         int32_t incl = len;
 #pragma unroll
@@ -344,21 +449,26 @@ __device__ unsigned long long warp_walk(const CountParams &p, int32_t x, int32_t
             if (lane >= d) incl += o;
         }
         const int32_t total = __shfl_sync(0xffffffffu, incl, 31);
-        const int64_t base = src - (int64_t)(incl - len);
-        if (kSecond) msum[lane] = 0;
+        const int32_t excl = incl - len;
+        const uint32_t fm = __ballot_sync(0xffffffffu, len > 0);
+        const int nz = __popc(fm & lt_mask), nnz = __popc(fm);
+        if (len > 0) {
+            wstart[nz] = excl;
+            wsrc[nz] = src - excl;
+            if (kSecond) msum[nz] = 0;
+        }
+        if (lane == 0) wstart[nnz] = total;
         __syncwarp();
+        int q0 = 0;
         for (int32_t k0 = 0; k0 < total; k0 += 32) {
+            const int idx = q0 + 1 + lane;
+            const int32_t d = (idx <= nnz ? wstart[idx] : 0x7fffffff) - k0;
+            const uint32_t m = __reduce_or_sync(0xffffffffu, d < 32 ? (1u << d) : 0u);
+            const int q = q0 + __popc(m & le_mask);
+            q0 += __popc(__ballot_sync(0xffffffffu, d <= 32));
             const int32_t k = k0 + lane;
-            int q = 0;   // number of entries whose inclusive prefix is <= k
-#pragma unroll
-            for (int sft = 16; sft >= 1; sft >>= 1) {
-                const int32_t val = __shfl_sync(0xffffffffu, incl, q + sft - 1);
-                if (val <= k) q += sft;
-            }
-            q = min(q, 31);
-            const int64_t b = __shfl_sync(0xffffffffu, base, q);
             if (k < total) {
-                const int64_t pos = b + k;
+                const long long pos = wsrc[q] + k;
 #if BFC_CHECKED
                 if (pos < 0 || pos >= p.adj_len) { atomicOr(p.err, kErrBounds); continue; }
 #endif
@@ -377,17 +487,24 @@ __device__ unsigned long long warp_walk(const CountParams &p, int32_t x, int32_t
             }
         }
         __syncwarp();
-        if (kSecond && j < nmid) {
-            const unsigned long long d = msum[lane];
-            if (d) {
-                if (MODE == kModeVertices) atomicAdd(p.pv + v, d);
-                if (MODE == kModeEdges) atomicAdd(p.pe + __ldg(p.eid + e), d);
+        if (kSecond && len > 0) {
+            const unsigned long long dsum = msum[nz];
+            if (dsum) {
+                if (MODE == kModeVertices) atomicAdd(p.pv + v, dsum);
+                if (MODE == kModeEdges) atomicAdd(p.pe + __ldg(p.eid + e), dsum);
             }
         }
         __syncwarp();
     }
     return acc;
 }
+
+// per-warp region: keys[512] | counts[512] | msum[32] | src[32] | start[33]
+constexpr int kWarpCntOff = kWarpSlots * 4;
+constexpr int kWarpMsumOff = kWarpSlots * 8;
+constexpr int kWarpSrcOff = kWarpMsumOff + 32 * 8;
+constexpr int kWarpStartOff = kWarpSrcOff + 32 * 8;
+static_assert(kWarpStartOff + 33 * 4 <= kWarpRegion, "per-warp region overflow");
 
 template <int MODE>
 __device__ unsigned long long warp_item(const CountParams &p, int32_t x, unsigned char *region) {
@@ -399,11 +516,13 @@ __device__ unsigned long long warp_item(const CountParams &p, int32_t x, unsigne
     uint32_t cap = 32;
     while (cap < 2 * bound && cap < (uint32_t)kWarpSlots) cap <<= 1;
     int32_t *keys = reinterpret_cast<int32_t *>(region);
-    uint32_t *cnt = reinterpret_cast<uint32_t *>(region + kWarpSlots * 4);
-    unsigned long long *msum = reinterpret_cast<unsigned long long *>(region + kWarpSlots * 8);
+    uint32_t *cnt = reinterpret_cast<uint32_t *>(region + kWarpCntOff);
+    unsigned long long *msum = reinterpret_cast<unsigned long long *>(region + kWarpMsumOff);
+    long long *wsrc = reinterpret_cast<long long *>(region + kWarpSrcOff);
+    int32_t *wstart = reinterpret_cast<int32_t *>(region + kWarpStartOff);
     for (uint32_t s = lane; s < cap; s += 32) { keys[s] = -1; cnt[s] = 0; }
     __syncwarp();
-    unsigned long long acc = warp_walk<MODE, false>(p, x, lb, cap - 1, keys, cnt, msum);
+    unsigned long long acc = warp_walk<MODE, false>(p, x, lb, cap - 1, keys, cnt, msum, wstart, wsrc);
     if (MODE != kModeTotal) {
         __syncwarp();
         if (MODE == kModeVertices) {
@@ -412,7 +531,7 @@ __device__ unsigned long long warp_item(const CountParams &p, int32_t x, unsigne
                 if (k >= 0 && cnt[s] >= 2) atomicAdd(p.pv + lb + k, c2(cnt[s]));
             }
         }
-        warp_walk<MODE, true>(p, x, lb, cap - 1, keys, cnt, msum);
+        warp_walk<MODE, true>(p, x, lb, cap - 1, keys, cnt, msum, wstart, wsrc);
         if (MODE == kModeVertices) {
             unsigned long long t = acc;
 #pragma unroll
@@ -424,10 +543,10 @@ __device__ unsigned long long warp_item(const CountParams &p, int32_t x, unsigne
     return acc;
 }
 
-template <int MODE>
+template <int MODE, typename Pos>
 __global__ void __launch_bounds__(kCountThreads, 1) k_count(CountParams p) {
     extern __shared__ __align__(16) unsigned char ctr[];
-    __shared__ SharedCTA sh;
+    __shared__ SharedCTA<MODE, Pos> sh;
     unsigned long long acc = 0;
     // phase 1: CTA items, heaviest first
     for (;;) {
@@ -436,7 +555,7 @@ __global__ void __launch_bounds__(kCountThreads, 1) k_count(CountParams p) {
         const int64_t it = sh.item;
         __syncthreads();
         if (it >= p.n_cta) break;
-        acc += cta_item<MODE>(p, p.cta_items[it], ctr, sh);
+        acc += cta_item<MODE, Pos>(p, p.cta_items[it], ctr, sh);
     }
     // phase 2: warp items
     {
@@ -464,9 +583,9 @@ __global__ void k_gather_vertices(const unsigned long long *__restrict__ pv,
     if (i < l && per_l) per_l[i] = pv[rank_l[i]];
 }
 
-template <int MODE>
+template <int MODE, typename Pos>
 cudaError_t setup_one() {
-    return cudaFuncSetAttribute(k_count<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(k_count<MODE, Pos>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 kCounterBytes);
 }
 
@@ -476,9 +595,12 @@ int count_smem_setup(int device) {
     static bool done[64] = {false};
     if (device < 0 || device >= 64) return BFC_ERR_INVALID_ARGUMENT;
     if (done[device]) return BFC_OK;
-    BFC_CUDA(setup_one<kModeTotal>());
-    BFC_CUDA(setup_one<kModeVertices>());
-    BFC_CUDA(setup_one<kModeEdges>());
+    BFC_CUDA((setup_one<kModeTotal, int32_t>()));
+    BFC_CUDA((setup_one<kModeVertices, int32_t>()));
+    BFC_CUDA((setup_one<kModeEdges, int32_t>()));
+    BFC_CUDA((setup_one<kModeTotal, long long>()));
+    BFC_CUDA((setup_one<kModeVertices, long long>()));
+    BFC_CUDA((setup_one<kModeEdges, long long>()));
     done[device] = true;
     return BFC_OK;
 }
@@ -493,12 +615,20 @@ int launch_count(Graph *g, cudaStream_t s, int mode, unsigned long long *pv_proj
     p.n_cta = g->n_cta_items; p.n_warp = g->n_warp_items;
     p.cursors = g->cursors; p.acc = g->acc; p.pv = pv_proj; p.pe = pe;
     p.adj_len = 2 * g->m; p.l = g->l; p.err = g->err;
+    p.coff = g->coff; p.coff_u1 = g->coff_u1; p.coff_l1 = g->coff_l1;
     BFC_CUDA(cudaMemsetAsync(g->cursors, 0, 2 * sizeof(int), s));
     BFC_CUDA(cudaMemsetAsync(g->acc, 0, sizeof(unsigned long long), s));
     const int grid = g->grid;
-    if (mode == kModeTotal) k_count<kModeTotal><<<grid, kCountThreads, kCounterBytes, s>>>(p);
-    else if (mode == kModeVertices) k_count<kModeVertices><<<grid, kCountThreads, kCounterBytes, s>>>(p);
-    else k_count<kModeEdges><<<grid, kCountThreads, kCounterBytes, s>>>(p);
+    // 32-bit adjacency positions whenever G* has fewer than 2^31 slots
+    if (2 * g->m <= 0x7fffffffll && !g->opt.wide_positions) {
+        if (mode == kModeTotal) k_count<kModeTotal, int32_t><<<grid, kCountThreads, kCounterBytes, s>>>(p);
+        else if (mode == kModeVertices) k_count<kModeVertices, int32_t><<<grid, kCountThreads, kCounterBytes, s>>>(p);
+        else k_count<kModeEdges, int32_t><<<grid, kCountThreads, kCounterBytes, s>>>(p);
+    } else {
+        if (mode == kModeTotal) k_count<kModeTotal, long long><<<grid, kCountThreads, kCounterBytes, s>>>(p);
+        else if (mode == kModeVertices) k_count<kModeVertices, long long><<<grid, kCountThreads, kCounterBytes, s>>>(p);
+        else k_count<kModeEdges, long long><<<grid, kCountThreads, kCounterBytes, s>>>(p);
+    }
     note_launch();
     BFC_CUDA(cudaGetLastError());
     return BFC_OK;

@@ -265,6 +265,37 @@ __global__ void k_emit_items(const int32_t *__restrict__ order, int64_t n_dense,
     }
 }
 
+// ----- chunk-boundary table for the dense bin ----------------------------------
+__device__ __forceinline__ int64_t coff_base(int32_t v, int32_t l, int32_t u1, int32_t l1) {
+    return v < l ? (int64_t)v * u1 : (int64_t)l * u1 + (int64_t)(v - l) * l1;
+}
+
+__global__ void k_coff_fill(const int64_t *__restrict__ off, int32_t l, int32_t u1, int32_t l1,
+                            int64_t entries, int32_t *coff) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < entries;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t split = (int64_t)l * u1;
+        const int32_t v = i < split ? (int32_t)(i / u1) : l + (int32_t)((i - split) / l1);
+        coff[i] = (int32_t)(off[v + 1] - off[v]);
+    }
+}
+
+// entry c of v = first position in N(v) whose neighbour rank is >= c * unit
+__global__ void k_coff_slots(const int64_t *__restrict__ off, const int32_t *__restrict__ adj,
+                             const int32_t *__restrict__ rows, int64_t slots, int32_t l,
+                             int32_t u1, int32_t l1, int32_t *coff) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < slots;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t v = rows[p];
+        const int32_t lbe = v < l ? l : 0;
+        const int64_t b = off[v];
+        const int32_t cp = (adj[p] - lbe) / kChunkUnit;
+        const int32_t cprev = p == b ? -1 : (adj[p - 1] - lbe) / kChunkUnit;
+        const int64_t tb = coff_base(v, l, u1, l1);
+        for (int32_t c = cprev + 1; c <= cp; ++c) coff[tb + c] = (int32_t)(p - b);
+    }
+}
+
 unsigned grid_stride_blocks(int64_t n) {
     int64_t b = (n + kT - 1) / kT;
     if (b > 152 * 64) b = 152 * 64;
@@ -488,6 +519,19 @@ int prepare_graph(const bfc_csr *csr, const bfc_options *opt, cudaStream_t s, Gr
             BFC_CUDA(cudaGetLastError());
         }
         g->info.dense_items = h_dense_items;
+        // chunk boundaries of every list, so dense items read them instead of searching
+        const int32_t u1 = (int32_t)((r + kChunkUnit - 1) / kChunkUnit) + 1;
+        const int32_t l1 = (int32_t)((l + kChunkUnit - 1) / kChunkUnit) + 1;
+        const int64_t entries = (int64_t)l * u1 + (int64_t)r * l1;
+        if (h_dense_items > n_dense && entries <= kChunkTableMaxEntries) {
+            GET(g->mem, g->coff, entries);
+            g->coff_u1 = u1;
+            g->coff_l1 = l1;
+            k_coff_fill<<<grid_stride_blocks(entries), kT, 0, s>>>(g->off, l, u1, l1, entries, g->coff); note_launch();
+            BFC_CUDA(cudaGetLastError());
+            k_coff_slots<<<grid_stride_blocks(2 * m), kT, 0, s>>>(g->off, g->adj, rows_star, 2 * m, l, u1, l1, g->coff); note_launch();
+            BFC_CUDA(cudaGetLastError());
+        }
     } else {
         GET(g->mem, g->cta_items, 1);
         GET(g->mem, g->warp_items, 1);

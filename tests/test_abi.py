@@ -38,7 +38,8 @@ def test_version_and_strings(bfc):
 
 def test_options_defaults(bfc):
     o = bfc.bfc_options_init()
-    assert (o.validate, o.warp_max_work, o.hash_max_work, o.num_ctas) == (1, 256, 16384, 0)
+    assert (o.validate, o.warp_max_work, o.hash_max_work, o.num_ctas, o.wide_positions) == \
+        (1, 256, 16384, 0, 0)
 
 
 def test_struct_layouts_match_header(bfc, tmp_path):

@@ -38,6 +38,8 @@ BIN_SETTINGS = {
     "all_dense": dict(warp_max_work=0, hash_max_work=0),
     "hash_only": dict(warp_max_work=0, hash_max_work=16384),
     "warp_heavy": dict(warp_max_work=256, hash_max_work=256),
+    "wide_positions": dict(wide_positions=1),
+    "all_dense_wide_positions": dict(warp_max_work=0, hash_max_work=0, wide_positions=1),
 }
 
 
@@ -143,11 +145,12 @@ def test_powerlaw_all_outputs(bins, seed):
     _check_against_oracle(g, _opts(**BIN_SETTINGS[bins]))
 
 
-def test_multi_chunk_end_ranges():
+@pytest.mark.parametrize("wide", [0, 1])
+def test_multi_chunk_end_ranges(wide):
     # U layer larger than one dense chunk (98,304 counters) so heavy U starts
     # are split into several end-range chunks with a ragged last chunk
     g = G.chung_lu_bipartite(230_000, 20_000, 900_000, 2.1, 2.1, 43)
-    got, ref = _check_against_oracle(g, _opts(warp_max_work=0, hash_max_work=0))
+    got, ref = _check_against_oracle(g, _opts(warp_max_work=0, hash_max_work=0, wide_positions=wide))
     assert got["info"]["dense_items"] > got["info"]["dense_starts"]
 
 
