@@ -163,6 +163,37 @@ int bfc_count_host(int32_t num_u, int32_t num_l, int64_t num_edges, const int32_
                    const int32_t *adj_u_host, const bfc_options *opt, void *stream,
                    uint64_t *total_host, uint64_t *wedges_host);
 
+/* Allocation-free count for small graphs.  The paper has no counterpart: this
+ * exists for callers that may not allocate device memory where they count --
+ * code being recorded into a CUDA graph (allocation is illegal during stream
+ * capture), code whose device memory is reserved up front by its own
+ * allocator, or latency-bound loops that must not enter the driver's
+ * allocator.  bfc_prepare cannot serve them because it allocates the
+ * renumbered graph.
+ *
+ * Computes ⋈_G of the U-side CSR (off_u_dev, adj_u_dev: device memory, the
+ * graph contract above) into *total_dev (one uint64, device memory) and, if
+ * status_dev is not NULL, BFC_OK or BFC_ERR_INVALID_GRAPH (offsets not a CSR
+ * of num_edges entries, or an id out of range) into *status_dev (one int32,
+ * device memory); *total_dev is 0 for an invalid graph.  Duplicate edges are
+ * not detected.  Asynchronous on `stream`; one cooperative kernel launch.
+ *
+ * Limits: num_u <= 49,152, num_l <= 49,152, num_u + num_l <= 65,536,
+ * num_edges <= 1,048,576; larger graphs return BFC_ERR_INVALID_ARGUMENT
+ * before any GPU work.
+ *
+ * All working memory is one fixed array of about 4.8 MB that every GPU which
+ * loads the library holds until the process exits; no call allocates.  The
+ * first call on a device looks up that array's device address and sets the
+ * kernel's attributes, so make one call per device before any stream capture.
+ * Every call uses the same array, which keeps the previous call's contents
+ * (the kernel clears what must start at zero): calls whose kernels can overlap
+ * on the GPU (different streams, or several host threads) race and give wrong
+ * results; issue them on one stream. */
+int bfc_count_small_noalloc(int32_t num_u, int32_t num_l, int64_t num_edges,
+                            const int32_t *off_u_dev, const int32_t *adj_u_dev, void *stream,
+                            uint64_t *total_dev, int32_t *status_dev);
+
 /* Frees the graph's library memory (stream-ordered on the stream of its
  * last call).  NULL is ignored. */
 void bfc_release(bfc_graph *g);

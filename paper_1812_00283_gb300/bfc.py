@@ -76,6 +76,8 @@ _SIGS = {
     "bfc_last_error": (ctypes.c_char_p, []),
     "bfc_version": (c_int, []),
     "bfc_kernel_launches": (ctypes.c_longlong, []),
+    "bfc_count_small_noalloc": (c_int, [c_int32, c_int32, c_int64, c_void_p, c_void_p, c_void_p,
+                                        c_void_p, c_void_p]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -150,6 +152,14 @@ def bfc_count_host(num_u: int, num_l: int, num_edges: int, off_u_host: int, adj_
                                ctypes.byref(options) if options else None, stream,
                                ctypes.byref(t), ctypes.byref(w)), "bfc_count_host")
     return int(t.value), int(w.value)
+
+
+def bfc_count_small_noalloc(num_u: int, num_l: int, num_edges: int, off_u: int, adj_u: int,
+                            stream: int, total_dev: int, status_dev: int | None = None):
+    """Allocation-free count of a small graph (see include/bfc.h for the limits
+    and the rules on overlapping calls)."""
+    _check(_lib.bfc_count_small_noalloc(num_u, num_l, num_edges, off_u, adj_u, stream, total_dev,
+                                        status_dev), "bfc_count_small_noalloc")
 
 
 def bfc_release(g: int):
