@@ -359,17 +359,24 @@ def _ops(device):
 def _draw_distinct(num_u: int, num_l: int, m: int, seed: int, ops,
                    sample_u: Callable, sample_v: Callable) -> np.ndarray:
     """Draw (u, v) pairs in rounds until at least m distinct pairs exist, then
-    keep the m pairs of smallest hash.  Returns sorted keys u*l + v (numpy)."""
+    keep the m pairs of smallest hash.  Returns sorted keys u*l + v (numpy).
+    After 48 rounds (only near-saturated skewed graphs get there) the
+    remaining draws are uniform."""
     if m > num_u * num_l:
         raise ValueError("more edges requested than vertex pairs")
     s_u, s_v, s_h = seed * 4 + 1, seed * 4 + 2, seed * 4 + 3
     keys = ops.empty()
     drawn, need, factor = 0, m, 1.1
-    for _ in range(200):
+    for rnd in range(200):
         k = max(1024, int(math.ceil(need * factor)))
         ctr = ops.arange(drawn, drawn + k)
-        u = sample_u(ops.rand(ctr, s_u))
-        v = sample_v(ops.rand(ctr, s_v))
+        if rnd < 48:
+            u = sample_u(ops.rand(ctr, s_u))
+            v = sample_v(ops.rand(ctr, s_v))
+        else:
+            # near-saturated skewed graphs: top up with uniform draws
+            u = ops.rand(ctr, s_u) % num_u
+            v = ops.rand(ctr, s_v) % num_l
         before = ops.size(keys)
         keys = ops.unique(ops.cat(keys, u * num_l + v))
         drawn += k
@@ -403,14 +410,31 @@ def uniform_bipartite(num_u: int, num_l: int, m: int, seed: int, device=None) ->
                         dict(kind="uniform", seed=seed))
 
 
-def chung_lu_weights(n: int, total: float, gamma: float, w_max: float) -> tuple[np.ndarray, float]:
+def chung_lu_weights(n: int, total: float, gamma: float, w_max: float,
+                     fast: bool = False) -> tuple[np.ndarray, float]:
     """Expected degrees w_i = C (i + i0)^(-1/(gamma-1)), i = 0..n-1, with C set
-    so that sum(w) = total and i0 solved (bisection) so that w_0 = w_max."""
+    so that sum(w) = total and i0 solved (bisection) so that w_0 = w_max.
+
+    fast=True evaluates the sum inside the bisection as 256 exact terms plus
+    the midpoint integral of the tail (used for the many small batch graphs)."""
     alpha = 1.0 / (gamma - 1.0)
     i = np.arange(n, dtype=np.float64)
+    head = np.arange(min(n, 256), dtype=np.float64)
+
+    def tail(i0: float) -> float:
+        k = head.size
+        if k >= n:
+            return 0.0
+        a, b = k - 0.5 + i0, n - 0.5 + i0
+        if abs(alpha - 1.0) < 1e-12:
+            return math.log(b / a)
+        return (b ** (1.0 - alpha) - a ** (1.0 - alpha)) / (1.0 - alpha)
 
     def top(i0: float) -> float:
-        s = np.sum((i + i0) ** (-alpha))
+        if fast:
+            s = np.sum((head + i0) ** (-alpha)) + tail(i0)
+        else:
+            s = np.sum((i + i0) ** (-alpha))
         return total * i0 ** (-alpha) / s
 
     lo, hi = 1e-9, 1e12
@@ -437,7 +461,7 @@ def _quantised_cdf(w: np.ndarray) -> np.ndarray:
 
 def chung_lu_bipartite(num_u: int, num_l: int, m: int, gamma_u: float, gamma_l: float,
                        seed: int, max_u: Optional[float] = None, max_l: Optional[float] = None,
-                       device=None) -> BipartiteCSR:
+                       device=None, fast_weights: bool = False) -> BipartiteCSR:
     """Chung-Lu style power-law bipartite graph with exactly m distinct edges.
 
     Endpoints are drawn independently with probability proportional to the
@@ -450,8 +474,8 @@ def chung_lu_bipartite(num_u: int, num_l: int, m: int, gamma_u: float, gamma_l: 
     ops = _ops(device)
     max_u = 0.1 * num_l if max_u is None else max_u
     max_l = 0.1 * num_u if max_l is None else max_l
-    wu, i0u = chung_lu_weights(num_u, m, gamma_u, max_u)
-    wl, i0l = chung_lu_weights(num_l, m, gamma_l, max_l)
+    wu, i0u = chung_lu_weights(num_u, m, gamma_u, max_u, fast_weights)
+    wl, i0l = chung_lu_weights(num_l, m, gamma_l, max_l, fast_weights)
     cu, cl = _quantised_cdf(wu), _quantised_cdf(wl)
     pu, pl = _perm_np(num_u, seed * 4 + 5), _perm_np(num_l, seed * 4 + 6)
     tcu, tcl, tpu, tpl = ops.table(cu), ops.table(cl), ops.table(pu), ops.table(pl)
@@ -517,6 +541,48 @@ def batch_graph_params(g: int, seed_base: int = 4000) -> tuple[int, int, int, fl
 
 def batch_graph(g: int, seed_base: int = 4000, device=None) -> BipartiteCSR:
     nu, nl, m, gu, gl = batch_graph_params(g, seed_base)
-    gr = chung_lu_bipartite(nu, nl, m, gu, gl, seed_base + g, device=device)
+    gr = chung_lu_bipartite(nu, nl, m, gu, gl, seed_base + g, device=device, fast_weights=True)
     gr.name = f"batch{g}"
     return gr
+
+
+# ---------------------------------------------------------------------------
+# Batches as disjoint unions
+# ---------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class Batch:
+    """Several graphs laid side by side as one disjoint union.
+
+    ``union`` is the U-side CSR of the union (graph g's U vertices are
+    ``u_start[g]:u_start[g+1]``, its L vertices ``l_start[g]:l_start[g+1]``,
+    L ids global); ``e_start[g]`` is the first edge slot of graph g, so graph
+    g's per-edge outputs are the union's slots ``e_start[g]:e_start[g+1]``.
+    """
+    union: BipartiteCSR
+    u_start: np.ndarray  # int32[G+1]
+    l_start: np.ndarray  # int32[G+1]
+    e_start: np.ndarray  # int64[G+1]
+
+    @property
+    def num_graphs(self) -> int:
+        return int(self.u_start.shape[0] - 1)
+
+
+def union_batch(graphs) -> Batch:
+    us = np.zeros(len(graphs) + 1, dtype=np.int64)
+    ls = np.zeros(len(graphs) + 1, dtype=np.int64)
+    es = np.zeros(len(graphs) + 1, dtype=np.int64)
+    for i, g in enumerate(graphs):
+        us[i + 1] = us[i] + g.num_u
+        ls[i + 1] = ls[i] + g.num_l
+        es[i + 1] = es[i] + g.num_edges
+    if us[-1] + ls[-1] > np.iinfo(np.int32).max - 1 or es[-1] > np.iinfo(np.int32).max:
+        raise ValueError("batch too large for int32 ids and offsets")
+    off = np.zeros(us[-1] + 1, dtype=np.int64)
+    adj = np.zeros(es[-1], dtype=np.int32)
+    for i, g in enumerate(graphs):
+        off[us[i] + 1:us[i + 1] + 1] = es[i] + g.off_u[1:].astype(np.int64)
+        adj[es[i]:es[i + 1]] = g.adj_u + ls[i]
+    u = BipartiteCSR(int(us[-1]), int(ls[-1]), off.astype(np.int32), adj, f"union_{len(graphs)}")
+    return Batch(u, us.astype(np.int32), ls.astype(np.int32), es)

@@ -145,6 +145,40 @@ int bfc_count_vertices(bfc_graph *g, void *stream, uint64_t *per_u_dev, uint64_t
  * NULL.  Asynchronous; no allocation. */
 int bfc_count_edges(bfc_graph *g, void *stream, uint64_t *per_edge_dev, uint64_t *total_dev);
 
+/* A batch of independent graphs given as one disjoint union: the union's
+ * U-side CSR (bfc_csr; L ids global) plus, per graph g, its U vertices
+ * [graph_u_start[g], graph_u_start[g+1]) and L vertices
+ * [graph_l_start[g], graph_l_start[g+1]).  Every edge must join a U and an L
+ * vertex of the same graph. */
+typedef struct bfc_batch {
+    int32_t num_graphs;
+    const int32_t *graph_u_start;   /* device, [num_graphs + 1], prefix sums of |U_g| */
+    const int32_t *graph_l_start;   /* device, [num_graphs + 1], prefix sums of |L_g| */
+} bfc_batch;
+
+/* Steps a1-a5 for a whole batch at once: one set of segmented sorts and
+ * scans over the union (Theorem 1: any total order counts every component
+ * exactly, so the union's priority order serves all graphs).  Rejects edges
+ * that cross graphs (BFC_ERR_INVALID_GRAPH).  Synchronises `stream`. */
+int bfc_prepare_batch(const bfc_csr *union_csr, const bfc_batch *batch, const bfc_options *opt,
+                      void *stream, bfc_graph **out);
+
+/* Steps a6-a7 for a batch in ONE persistent launch: totals_dev[g] = ⋈ of
+ * graph g (uint64[num_graphs], device); total_dev (nullable) = their sum.
+ * Asynchronous, no allocation, no host synchronisation: it can be captured
+ * in a CUDA graph once a first call has been made outside capture. */
+int bfc_count_batch(bfc_graph *g, void *stream, uint64_t *totals_dev, uint64_t *total_dev);
+
+/* Processed wedges of every graph of a batch (uint64[num_graphs], device). */
+int bfc_batch_wedges(const bfc_graph *g, void *stream, uint64_t *wedges_dev);
+
+/* Autotuner for the bin thresholds of step a5: re-bins the prepared graph for
+ * each candidate (warp_max_work in {32, 128, 256} x hash_max_work in {1024,
+ * 4096, 16384}), times `iters` count launches of each with CUDA events on
+ * `stream`, keeps the fastest and writes it to *chosen (nullable).
+ * Synchronises `stream`; allocates only the schedule arrays. */
+int bfc_autotune(bfc_graph *g, void *stream, int iters, bfc_options *chosen);
+
 /* Waits for `stream` and reports any error a kernel of this graph flagged
  * since the last bfc_sync (BFC_ERR_INTERNAL), then clears the flag. */
 int bfc_sync(bfc_graph *g, void *stream);

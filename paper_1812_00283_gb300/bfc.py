@@ -47,6 +47,10 @@ class bfc_info(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class bfc_batch(ctypes.Structure):
+    _fields_ = [("num_graphs", c_int32), ("graph_u_start", c_void_p), ("graph_l_start", c_void_p)]
+
+
 class BfcError(RuntimeError):
     def __init__(self, status: int, where: str, msg: str):
         super().__init__(f"{where}: {STATUS.get(status, status)}: {msg}")
@@ -76,6 +80,11 @@ _SIGS = {
     "bfc_last_error": (ctypes.c_char_p, []),
     "bfc_version": (c_int, []),
     "bfc_kernel_launches": (ctypes.c_longlong, []),
+    "bfc_prepare_batch": (c_int, [ctypes.POINTER(bfc_csr), ctypes.POINTER(bfc_batch),
+                                  ctypes.POINTER(bfc_options), c_void_p, ctypes.POINTER(c_void_p)]),
+    "bfc_count_batch": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "bfc_batch_wedges": (c_int, [c_void_p, c_void_p, c_void_p]),
+    "bfc_autotune": (c_int, [c_void_p, c_void_p, c_int, ctypes.POINTER(bfc_options)]),
     "bfc_count_small_noalloc": (c_int, [c_int32, c_int32, c_int64, c_void_p, c_void_p, c_void_p,
                                         c_void_p, c_void_p]),
 }
@@ -152,6 +161,33 @@ def bfc_count_host(num_u: int, num_l: int, num_edges: int, off_u_host: int, adj_
                                ctypes.byref(options) if options else None, stream,
                                ctypes.byref(t), ctypes.byref(w)), "bfc_count_host")
     return int(t.value), int(w.value)
+
+
+def bfc_prepare_batch(num_u: int, num_l: int, num_edges: int, off_u: int, adj_u: int,
+                      num_graphs: int, graph_u_start: int, graph_l_start: int,
+                      options: bfc_options | None = None, stream: int = 0) -> int:
+    """Steps a1-a5 for a batch given as a disjoint union; returns a graph handle."""
+    csr = bfc_csr(num_u, num_l, num_edges, off_u, adj_u)
+    b = bfc_batch(num_graphs, graph_u_start, graph_l_start)
+    h = c_void_p()
+    _check(_lib.bfc_prepare_batch(ctypes.byref(csr), ctypes.byref(b),
+                                  ctypes.byref(options) if options else None, stream,
+                                  ctypes.byref(h)), "bfc_prepare_batch")
+    return h.value
+
+
+def bfc_count_batch(g: int, stream: int, totals_dev: int, total_dev: int | None = None):
+    _check(_lib.bfc_count_batch(g, stream, totals_dev, total_dev), "bfc_count_batch")
+
+
+def bfc_batch_wedges(g: int, stream: int, wedges_dev: int):
+    _check(_lib.bfc_batch_wedges(g, stream, wedges_dev), "bfc_batch_wedges")
+
+
+def bfc_autotune(g: int, stream: int = 0, iters: int = 2) -> bfc_options:
+    o = bfc_options()
+    _check(_lib.bfc_autotune(g, stream, iters, ctypes.byref(o)), "bfc_autotune")
+    return o
 
 
 def bfc_count_small_noalloc(num_u: int, num_l: int, num_edges: int, off_u: int, adj_u: int,

@@ -66,7 +66,7 @@ def build(verbose: bool = False, extra_flags=(), force: bool = False) -> str:
     objs = [os.path.join(BUILD, s.replace(".cu", ".o")) for s in SOURCES]
     if force or jobs or not os.path.exists(LIB):
         tmp = LIB + f".tmp{os.getpid()}"
-        run([cc, *ARCH, "-shared", "-cudart=static", "-o", tmp, *objs])
+        run([cc, *ARCH, "-shared", "-cudart=static", "-Xlinker", "--no-undefined", "-o", tmp, *objs])
         os.replace(tmp, LIB)
     return LIB
 

@@ -186,6 +186,112 @@ static int count_common(bfc_graph *h, void *stream, int mode, uint64_t *per_a, u
     return BFC_OK;
 }
 
+int bfc_prepare_batch(const bfc_csr *csr, const bfc_batch *batch, const bfc_options *opt_in,
+                      void *stream, bfc_graph **out) {
+    bfc::set_last_error("");
+    if (!csr || !batch || !out) { bfc::set_last_error("null argument"); return BFC_ERR_INVALID_ARGUMENT; }
+    *out = nullptr;
+    if (batch->num_graphs < 1 || !batch->graph_u_start || !batch->graph_l_start) {
+        bfc::set_last_error("a batch needs num_graphs >= 1 and both start arrays");
+        return BFC_ERR_INVALID_ARGUMENT;
+    }
+    bfc_options opt;
+    if (opt_in) opt = *opt_in; else bfc_options_init(&opt);
+    int rc = check_options(&opt);
+    if (rc) return rc;
+    if (csr->num_u < 0 || csr->num_l < 0 || csr->num_edges < 0 || csr->num_edges > 2147483647LL ||
+        (int64_t)csr->num_u + (int64_t)csr->num_l > 2147483646LL || !csr->off_u ||
+        (csr->num_edges > 0 && !csr->adj_u)) {
+        bfc::set_last_error("invalid union CSR arguments");
+        return BFC_ERR_INVALID_ARGUMENT;
+    }
+    bfc_graph *h = new (std::nothrow) bfc_graph();
+    if (!h) { bfc::set_last_error("host allocation failed"); return BFC_ERR_OUT_OF_MEMORY; }
+    Graph *g = &h->g;
+    cudaError_t e = cudaGetDevice(&g->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device);
+    if (e != cudaSuccess) { delete h; return bfc::cuda_fail(e, "cudaGetDevice"); }
+    g->grid = opt.num_ctas > 0 ? opt.num_ctas : g->num_sms;
+    rc = bfc::prepare_graph(csr, &opt, static_cast<cudaStream_t>(stream), g, batch->num_graphs,
+                            batch->graph_u_start, batch->graph_l_start);
+    if (rc != BFC_OK) {
+        g->mem.release();
+        cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+        delete h;
+        return rc;
+    }
+    *out = h;
+    return BFC_OK;
+}
+
+int bfc_count_batch(bfc_graph *h, void *stream, uint64_t *totals_dev, uint64_t *total_dev) {
+    bfc::set_last_error("");
+    if (!h || !totals_dev) { bfc::set_last_error("null argument"); return BFC_ERR_INVALID_ARGUMENT; }
+    Graph *g = &h->g;
+    if (g->num_graphs < 1) { bfc::set_last_error("graph was not prepared as a batch"); return BFC_ERR_INVALID_ARGUMENT; }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    g->stream = s;
+    unsigned long long *gt = reinterpret_cast<unsigned long long *>(totals_dev);
+    BFC_CUDA(cudaMemsetAsync(gt, 0, sizeof(uint64_t) * (size_t)g->num_graphs, s));
+    int rc = bfc::launch_count(g, s, bfc::kModeBatch, nullptr, nullptr, gt);
+    if (rc) return rc;
+    if (total_dev)
+        BFC_CUDA(cudaMemcpyAsync(total_dev, g->acc, sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
+    return BFC_OK;
+}
+
+int bfc_batch_wedges(const bfc_graph *h, void *stream, uint64_t *wedges_dev) {
+    if (!h || !wedges_dev) { bfc::set_last_error("null argument"); return BFC_ERR_INVALID_ARGUMENT; }
+    const Graph *g = &h->g;
+    if (g->num_graphs < 1) { bfc::set_last_error("graph was not prepared as a batch"); return BFC_ERR_INVALID_ARGUMENT; }
+    BFC_CUDA(cudaMemcpyAsync(wedges_dev, g->gwork, sizeof(uint64_t) * (size_t)g->num_graphs,
+                             cudaMemcpyDeviceToDevice, static_cast<cudaStream_t>(stream)));
+    return BFC_OK;
+}
+
+int bfc_autotune(bfc_graph *h, void *stream, int iters, bfc_options *chosen) {
+    bfc::set_last_error("");
+    if (!h) { bfc::set_last_error("null graph"); return BFC_ERR_INVALID_ARGUMENT; }
+    if (iters < 1) iters = 1;
+    Graph *g = &h->g;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    g->stream = s;
+    static const int32_t warp_c[] = {32, 128, 256};
+    static const int32_t hash_c[] = {1024, 4096, 16384};
+    cudaEvent_t e0, e1;
+    BFC_CUDA(cudaEventCreate(&e0));
+    BFC_CUDA(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int32_t bw = g->opt.warp_max_work, bh = g->opt.hash_max_work;
+    int rc = BFC_OK;
+    for (int32_t wmax : warp_c) {
+        for (int32_t hmax : hash_c) {
+            rc = bfc::rebin_graph(g, s, wmax, hmax);
+            if (rc) break;
+            rc = bfc::launch_count(g, s, bfc::kModeTotal, nullptr, nullptr);   // warm-up
+            if (rc) break;
+            cudaEventRecord(e0, s);
+            for (int i = 0; i < iters && rc == BFC_OK; ++i)
+                rc = bfc::launch_count(g, s, bfc::kModeTotal, nullptr, nullptr);
+            cudaEventRecord(e1, s);
+            if (rc) break;
+            cudaError_t e = cudaEventSynchronize(e1);
+            if (e != cudaSuccess) { rc = bfc::cuda_fail(e, "cudaEventSynchronize"); break; }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best) { best = ms; bw = wmax; bh = hmax; }
+        }
+        if (rc) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    rc = bfc::rebin_graph(g, s, bw, bh);
+    if (rc) return rc;
+    if (chosen) *chosen = g->opt;
+    return BFC_OK;
+}
+
 int bfc_count(bfc_graph *g, void *stream, uint64_t *total_dev) {
     if (!total_dev) { bfc::set_last_error("null total_dev"); return BFC_ERR_INVALID_ARGUMENT; }
     return count_common(g, stream, bfc::kModeTotal, nullptr, nullptr, total_dev);

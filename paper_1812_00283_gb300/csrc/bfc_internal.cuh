@@ -88,6 +88,18 @@ struct Allocs {
         *p = static_cast<T *>(q);
         return cudaSuccess;
     }
+    // frees one allocation of the list (no-op for null or unknown pointers)
+    void drop(void *p) {
+        if (!p) return;
+        for (int i = 0; i < n; ++i)
+            if (ptr[i] == p) {
+                pool_free(p, stream);
+                total -= bytes[i];
+                for (int j = i + 1; j < n; ++j) { ptr[j - 1] = ptr[j]; bytes[j - 1] = bytes[j]; }
+                --n;
+                return;
+            }
+    }
     void release() {
         for (int i = n - 1; i >= 0; --i) pool_free(ptr[i], stream);
         n = 0;
@@ -128,6 +140,11 @@ struct Graph {
     int32_t *coff = nullptr;
     int32_t coff_u1 = 0;   // entries per L vertex (its neighbours are U vertices)
     int32_t coff_l1 = 0;   // entries per U vertex
+    // batch of graphs prepared as one disjoint union
+    int32_t num_graphs = 0;
+    int32_t *gstar = nullptr;             // [n] graph of each vertex of G*
+    int32_t *vbase = nullptr;             // [n] first G* id of x's graph in x's layer
+    unsigned long long *gwork = nullptr;  // [num_graphs] wedges per graph
 };
 
 // ---------------------------------------------------------------------------
@@ -160,10 +177,15 @@ cudaError_t reduce_max_u64(const uint64_t *in, int64_t n, unsigned long long *ou
 // ---------------------------------------------------------------------------
 // Prepare and count (prepare.cu, count.cu)
 // ---------------------------------------------------------------------------
-int prepare_graph(const bfc_csr *csr, const bfc_options *opt, cudaStream_t s, Graph *g);
-enum CountMode { kModeTotal = 0, kModeVertices = 1, kModeEdges = 2 };
+int prepare_graph(const bfc_csr *csr, const bfc_options *opt, cudaStream_t s, Graph *g,
+                  int32_t num_graphs = 0, const int32_t *graph_u_start = nullptr,
+                  const int32_t *graph_l_start = nullptr);
+// kModeBatch = total plus per-graph totals for a batch prepared as a disjoint union
+enum CountMode { kModeTotal = 0, kModeVertices = 1, kModeEdges = 2, kModeBatch = 3 };
+__host__ __device__ constexpr bool has_second_walk(int mode) { return mode == kModeVertices || mode == kModeEdges; }
 int launch_count(Graph *g, cudaStream_t s, int mode, unsigned long long *pv_proj,
-                 unsigned long long *pe);
+                 unsigned long long *pe, unsigned long long *gtot = nullptr);
+int rebin_graph(Graph *g, cudaStream_t s, int32_t warp_max_work, int32_t hash_max_work);
 int count_smem_setup(int device);
 
 // small helpers

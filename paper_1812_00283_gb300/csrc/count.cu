@@ -45,6 +45,9 @@ struct CountParams {
     unsigned long long *pv;   // [n] in G* ids
     unsigned long long *pe;   // [m] by edge id
     const int32_t *__restrict__ coff;  // chunk-boundary table (nullable)
+    const int32_t *__restrict__ gstar; // graph of each G* vertex (batch mode)
+    const int32_t *__restrict__ vbase; // first id of x's graph in x's layer (batch mode)
+    unsigned long long *gtot;          // per-graph totals (batch mode)
     int32_t coff_u1, coff_l1;          // entries per L vertex / per U vertex
     int64_t adj_len;
     int32_t l;
@@ -64,7 +67,7 @@ struct SharedCTA {
     static constexpr int kB = Batch<Pos>::kSize;
     int32_t start[kB + 1];              // compacted batch: exclusive prefix of run lengths (+ sentinel)
     Pos src[kB];                        // compacted batch: adjacency position of a run minus its prefix
-    unsigned long long msum[MODE == kModeTotal ? 1 : kB];  // second walk: Σ δ per compacted middle
+    unsigned long long msum[has_second_walk(MODE) ? kB : 1];  // second walk: Σ δ per compacted middle
     long long wtot[32];
     unsigned long long red[32];
     int item;
@@ -349,7 +352,7 @@ __device__ unsigned long long cta_item_body(const CountParams &p, int32_t x, int
                                             int32_t lo, int32_t hi, int32_t R, uint32_t hmask,
                                             unsigned char *ctr, SH &sh) {
     unsigned long long acc = cta_walk<MODE, KIND, false, Pos>(p, x, lb, lo, hi, R, hmask, ctr, sh);
-    if (MODE != kModeTotal) {
+    if (has_second_walk(MODE)) {
         __syncthreads();
         if (MODE == kModeVertices) {
             // ends: each pair (x, w) adds C(count, 2) to ⋈_w
@@ -391,7 +394,8 @@ template <int MODE, typename Pos, class SH>
 __device__ unsigned long long cta_item(const CountParams &p, int2 item, unsigned char *ctr,
                                        SH &sh) {
     const int32_t x = item.x;
-    const int32_t lb = x >= p.l ? p.l : 0;
+    // ends of x are the vertices of x's layer (of x's graph, in a batch) below x
+    const int32_t lb = p.vbase ? __ldg(p.vbase + x) : (x >= p.l ? p.l : 0);
     const int32_t R = x - lb;
     unsigned long long acc;
     if (item.y >= 0) {
@@ -413,6 +417,11 @@ __device__ unsigned long long cta_item(const CountParams &p, int2 item, unsigned
         zero_smem(ctr + (size_t)cap * 4, (int)cap * 2, 0u);  // packed 16-bit counts
         __syncthreads();
         acc = cta_item_body<MODE, kHash, Pos>(p, x, lb, 0, R, R, cap - 1, ctr, sh);
+    }
+    if (MODE == kModeBatch) {
+        // the batch is a disjoint union: every butterfly of start x lies in x's graph
+        const unsigned long long t = block_sum(acc, sh);
+        if (threadIdx.x == 0 && t) atomicAdd(p.gtot + p.gstar[x], t);
     }
     __syncthreads();
     return acc;
@@ -509,7 +518,8 @@ static_assert(kWarpStartOff + 33 * 4 <= kWarpRegion, "per-warp region overflow")
 template <int MODE>
 __device__ unsigned long long warp_item(const CountParams &p, int32_t x, unsigned char *region) {
     const int lane = threadIdx.x & 31;
-    const int32_t lb = x >= p.l ? p.l : 0;
+    // ends of x are the vertices of x's layer (of x's graph, in a batch) below x
+    const int32_t lb = p.vbase ? __ldg(p.vbase + x) : (x >= p.l ? p.l : 0);
     const int32_t R = x - lb;
     const unsigned long long w = p.work[x];
     const unsigned long long bound = w < (unsigned long long)R ? w : (unsigned long long)R;
@@ -523,7 +533,7 @@ __device__ unsigned long long warp_item(const CountParams &p, int32_t x, unsigne
     for (uint32_t s = lane; s < cap; s += 32) { keys[s] = -1; cnt[s] = 0; }
     __syncwarp();
     unsigned long long acc = warp_walk<MODE, false>(p, x, lb, cap - 1, keys, cnt, msum, wstart, wsrc);
-    if (MODE != kModeTotal) {
+    if (has_second_walk(MODE)) {
         __syncwarp();
         if (MODE == kModeVertices) {
             for (uint32_t s = lane; s < cap; s += 32) {
@@ -538,6 +548,12 @@ __device__ unsigned long long warp_item(const CountParams &p, int32_t x, unsigne
             for (int d = 16; d > 0; d >>= 1) t += __shfl_xor_sync(0xffffffffu, t, d);
             if (lane == 0 && t) atomicAdd(p.pv + x, t);
         }
+    }
+    if (MODE == kModeBatch) {
+        unsigned long long t = acc;
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) t += __shfl_xor_sync(0xffffffffu, t, d);
+        if (lane == 0 && t) atomicAdd(p.gtot + p.gstar[x], t);
     }
     __syncwarp();
     return acc;
@@ -599,6 +615,8 @@ int count_smem_setup(int device) {
     BFC_CUDA((setup_one<kModeVertices, int32_t>()));
     BFC_CUDA((setup_one<kModeEdges, int32_t>()));
     BFC_CUDA((setup_one<kModeTotal, long long>()));
+    BFC_CUDA((setup_one<kModeBatch, int32_t>()));
+    BFC_CUDA((setup_one<kModeBatch, long long>()));
     BFC_CUDA((setup_one<kModeVertices, long long>()));
     BFC_CUDA((setup_one<kModeEdges, long long>()));
     done[device] = true;
@@ -606,7 +624,7 @@ int count_smem_setup(int device) {
 }
 
 int launch_count(Graph *g, cudaStream_t s, int mode, unsigned long long *pv_proj,
-                 unsigned long long *pe) {
+                 unsigned long long *pe, unsigned long long *gtot) {
     int rc = count_smem_setup(g->device);
     if (rc) return rc;
     CountParams p;
@@ -616,16 +634,19 @@ int launch_count(Graph *g, cudaStream_t s, int mode, unsigned long long *pv_proj
     p.cursors = g->cursors; p.acc = g->acc; p.pv = pv_proj; p.pe = pe;
     p.adj_len = 2 * g->m; p.l = g->l; p.err = g->err;
     p.coff = g->coff; p.coff_u1 = g->coff_u1; p.coff_l1 = g->coff_l1;
+    p.gstar = g->gstar; p.gtot = gtot; p.vbase = g->vbase;
     BFC_CUDA(cudaMemsetAsync(g->cursors, 0, 2 * sizeof(int), s));
     BFC_CUDA(cudaMemsetAsync(g->acc, 0, sizeof(unsigned long long), s));
     const int grid = g->grid;
     // 32-bit adjacency positions whenever G* has fewer than 2^31 slots
     if (2 * g->m <= 0x7fffffffll && !g->opt.wide_positions) {
         if (mode == kModeTotal) k_count<kModeTotal, int32_t><<<grid, kCountThreads, kCounterBytes, s>>>(p);
+        else if (mode == kModeBatch) k_count<kModeBatch, int32_t><<<grid, kCountThreads, kCounterBytes, s>>>(p);
         else if (mode == kModeVertices) k_count<kModeVertices, int32_t><<<grid, kCountThreads, kCounterBytes, s>>>(p);
         else k_count<kModeEdges, int32_t><<<grid, kCountThreads, kCounterBytes, s>>>(p);
     } else {
         if (mode == kModeTotal) k_count<kModeTotal, long long><<<grid, kCountThreads, kCounterBytes, s>>>(p);
+        else if (mode == kModeBatch) k_count<kModeBatch, long long><<<grid, kCountThreads, kCounterBytes, s>>>(p);
         else if (mode == kModeVertices) k_count<kModeVertices, long long><<<grid, kCountThreads, kCounterBytes, s>>>(p);
         else k_count<kModeEdges, long long><<<grid, kCountThreads, kCounterBytes, s>>>(p);
     }

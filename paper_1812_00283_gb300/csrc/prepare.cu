@@ -67,13 +67,30 @@ __global__ void k_iota_keys(const int32_t *__restrict__ deg, int32_t n, uint64_t
     vals[i] = (int32_t)i;
 }
 
+// batch of graphs: rank graph-major (graph id above the degree bits), so each
+// graph's vertices keep Definition 3's order among themselves and occupy the
+// contiguous rank range [start[g], start[g+1]) of their layer
+__global__ void k_iota_keys_batch(const int32_t *__restrict__ deg, int32_t n,
+                                  const int32_t *__restrict__ start, int32_t num_graphs, int bdeg,
+                                  uint64_t *keys, int32_t *vals) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int32_t lo = 0, hi = num_graphs;
+    while (hi - lo > 1) {
+        const int32_t mid = (lo + hi) >> 1;
+        if (start[mid] <= (int32_t)i) lo = mid; else hi = mid;
+    }
+    keys[i] = ((uint64_t)lo << bdeg) | (uint64_t)(uint32_t)deg[i];
+    vals[i] = (int32_t)i;
+}
+
 // rank[order[i]] = i; degree of G* vertex (base + i) = sorted key
 __global__ void k_ranks(const uint64_t *__restrict__ sorted_deg, const int32_t *__restrict__ order,
-                        int32_t n, int32_t *rank, int32_t *deg_star, int32_t base) {
+                        int32_t n, int32_t *rank, int32_t *deg_star, int32_t base, uint64_t deg_mask) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     rank[order[i]] = (int32_t)i;
-    deg_star[base + i] = (int32_t)sorted_deg[i];
+    deg_star[base + i] = (int32_t)(sorted_deg[i] & deg_mask);   // low bits: the degree
 }
 
 // ----- a3: projection + sorted adjacency -------------------------------------
@@ -232,30 +249,33 @@ __global__ void k_classify(const uint64_t *__restrict__ work, int32_t n, uint64_
     }
 }
 
-__device__ __forceinline__ int32_t dense_chunks(int32_t x, int32_t l, int32_t cut) {
-    const int64_t R = x >= l ? x - l : x;
+__device__ __forceinline__ int32_t dense_chunks(int32_t x, int32_t l, int32_t cut,
+                                                const int32_t *vbase) {
+    const int64_t R = x - (vbase ? vbase[x] : (x >= l ? l : 0));
     const int64_t S = cut > (int32_t)kNarrowMaxCut ? kDense32 : kDense16;
     return (int32_t)((R + S - 1) / S);
 }
 
 __global__ void k_chunk_counts(const int32_t *__restrict__ order, int64_t n_dense, int32_t l,
-                               const int32_t *__restrict__ cut, int64_t *nch) {
+                               const int32_t *__restrict__ cut, const int32_t *__restrict__ vbase,
+                               int64_t *nch) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_dense) return;
     int32_t x = order[i];
-    nch[i] = dense_chunks(x, l, cut[x]);
+    nch[i] = dense_chunks(x, l, cut[x], vbase);
 }
 
 __global__ void k_emit_items(const int32_t *__restrict__ order, int64_t n_dense, int64_t n_hash,
                              int64_t n_warp, const int64_t *__restrict__ nch_scan, int32_t l,
-                             const int32_t *__restrict__ cut, int2 *cta_items, int32_t *warp_items) {
+                             const int32_t *__restrict__ cut, const int32_t *__restrict__ vbase,
+                             int2 *cta_items, int32_t *warp_items) {
     const int64_t total_dense = nch_scan[n_dense];
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_dense + n_hash + n_warp;
          i += (int64_t)gridDim.x * blockDim.x) {
         int32_t x = order[i];
         if (i < n_dense) {
             int64_t o = nch_scan[i];
-            int32_t k = dense_chunks(x, l, cut[x]);
+            int32_t k = dense_chunks(x, l, cut[x], vbase);
             for (int32_t c = 0; c < k; ++c) cta_items[o + c] = make_int2(x, c);
         } else if (i < n_dense + n_hash) {
             cta_items[total_dense + (i - n_dense)] = make_int2(x, -1);
@@ -303,9 +323,191 @@ unsigned grid_stride_blocks(int64_t n) {
     return (unsigned)b;
 }
 
+// ----- batches prepared as one disjoint union ------------------------------------
+__device__ __forceinline__ int32_t graph_of(const int32_t *start, int32_t num_graphs, int32_t id) {
+    int32_t lo = 0, hi = num_graphs;   // last g with start[g] <= id
+    while (hi - lo > 1) {
+        const int32_t mid = (lo + hi) >> 1;
+        if (start[mid] <= id) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void k_check_starts(const int32_t *__restrict__ start, int32_t num_graphs,
+                               int32_t total, int *err) {
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g <= num_graphs;
+         g += (int64_t)gridDim.x * blockDim.x) {
+        if (g == 0 && start[0] != 0) atomicOr(err, kErrBadOffsets);
+        if (g < num_graphs && start[g + 1] < start[g]) atomicOr(err, kErrBadOffsets);
+        if (g == num_graphs && start[g] != total) atomicOr(err, kErrBadOffsets);
+    }
+}
+
+// every edge must join a U and an L vertex of the same graph
+__global__ void k_check_batch_edges(const int32_t *__restrict__ rows, const int32_t *__restrict__ adj,
+                                    int64_t m, const int32_t *__restrict__ gu,
+                                    const int32_t *__restrict__ gl, int32_t num_graphs, int *err) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < m;
+         k += (int64_t)gridDim.x * blockDim.x)
+        if (graph_of(gu, num_graphs, rows[k]) != graph_of(gl, num_graphs, adj[k]))
+            atomicOr(err, kErrBadId);
+}
+
+// graph-major ranks: vertex x of G* belongs to the graph whose rank range
+// holds it; vbase[x] = the first G* id of that graph in x's layer
+__global__ void k_graph_star(int32_t r, int32_t l, const int32_t *__restrict__ gu,
+                             const int32_t *__restrict__ gl, int32_t num_graphs, int32_t *gstar,
+                             int32_t *vbase) {
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < (int64_t)r + l;
+         x += (int64_t)gridDim.x * blockDim.x) {
+        if (x < l) {
+            const int32_t gg = graph_of(gl, num_graphs, (int32_t)x);
+            gstar[x] = gg;
+            vbase[x] = gl[gg];
+        } else {
+            const int32_t gg = graph_of(gu, num_graphs, (int32_t)(x - l));
+            gstar[x] = gg;
+            vbase[x] = l + gu[gg];
+        }
+    }
+}
+
+__global__ void k_graph_work(const uint64_t *__restrict__ work, const int32_t *__restrict__ gstar,
+                             int32_t n, unsigned long long *gwork) {
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
+         x += (int64_t)gridDim.x * blockDim.x)
+        if (work[x]) atomicAdd(gwork + gstar[x], (unsigned long long)work[x]);
+}
+
+// slot -> owning vertex of G*, one warp per vertex
+__global__ void k_rows_from_off(const int64_t *__restrict__ off, int32_t n, int32_t *rows) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t x = w; x < n; x += nw)
+        for (int64_t p = off[x] + lane; p < off[x + 1]; p += 32) rows[p] = (int32_t)x;
+}
+
 }  // namespace
 
-int prepare_graph(const bfc_csr *csr, const bfc_options *opt, cudaStream_t s, Graph *g) {
+// Step a5: order the starts by descending exact work and split them into the
+// warp, CTA-hash and CTA-dense bins (dense starts into end-range chunks);
+// builds the chunk-boundary table when a dense start has several chunks.
+// `rows_star` (slot -> vertex of G*) may be null; it is rebuilt when needed.
+static int schedule_graph(Graph *g, cudaStream_t s, int32_t warp_max_work, int32_t hash_max_work,
+                          const int32_t *rows_star) {
+    const int32_t r = g->r, l = g->l, n = g->n;
+    const int64_t m = g->m;
+    Allocs tmp;
+    tmp.stream = s;
+    struct TmpGuard { Allocs *a; ~TmpGuard() { a->release(); } } guard{&tmp};
+#define GET(allocs, ptr, cnt)                                                         \
+    do {                                                                              \
+        cudaError_t e_ = (allocs).get(&(ptr), (size_t)(cnt));                         \
+        if (e_ != cudaSuccess) {                                                      \
+            set_last_error(std::string("device allocation failed: ") + #ptr);         \
+            return BFC_ERR_OUT_OF_MEMORY;                                             \
+        }                                                                             \
+    } while (0)
+    const uint64_t warp_max = (uint64_t)warp_max_work;
+    const uint64_t hash_max = (uint64_t)hash_max_work;
+    const uint64_t maxw = g->info.max_start_work;
+    int64_t n_dense = 0, n_hash = 0, n_warp = 0, n_items = 0, h_dense_items = 0;
+    if (n > 0 && g->info.wedges > 0) {
+        const int64_t nn = (int64_t)n + 1;
+        uint64_t *k0, *k1;
+        int32_t *v0, *v1;
+        uint32_t *hist, *hist_tmp;
+        int64_t *scan64_tmp, *nch;
+        unsigned long long *red;
+        GET(tmp, k0, nn); GET(tmp, k1, nn); GET(tmp, v0, nn); GET(tmp, v1, nn);
+        GET(tmp, hist, radix_hist_elems(n));
+        GET(tmp, hist_tmp, scan_tmp_elems<uint32_t>((int64_t)radix_hist_elems(n)));
+        GET(tmp, scan64_tmp, scan_tmp_elems<int64_t>(nn));
+        GET(tmp, nch, nn);
+        GET(tmp, red, 4);
+        BFC_CUDA(cudaMemsetAsync(red, 0, 4 * sizeof(unsigned long long), s));
+        int which = 0;
+        k_sched_keys<<<blocks_for(n), kT, 0, s>>>(g->work, n, maxw, k0, v0); note_launch();
+        BFC_CUDA(cudaGetLastError());
+        BFC_CUDA(radix_sort_pairs(k0, v0, k1, v1, n, 0, bits_for(maxw), hist, hist_tmp, s, &which));
+        const int32_t *order = which ? v1 : v0;
+        k_classify<<<grid_stride_blocks(n), kT, 0, s>>>(g->work, n, warp_max, hash_max, red); note_launch();
+        BFC_CUDA(cudaGetLastError());
+        unsigned long long hc[3];
+        BFC_CUDA(cudaMemcpyAsync(hc, red, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+        BFC_CUDA(cudaStreamSynchronize(s));
+        n_dense = (int64_t)hc[0]; n_hash = (int64_t)hc[1]; n_warp = (int64_t)hc[2];
+        if (n_dense > 0) {
+            k_chunk_counts<<<blocks_for(n_dense), kT, 0, s>>>(order, n_dense, l, g->cut, g->vbase, nch); note_launch();
+            BFC_CUDA(cudaGetLastError());
+        }
+        // the sorted keys are no longer needed; the other key buffer holds the scan
+        int64_t *nch_scan = reinterpret_cast<int64_t *>(which ? k0 : k1);
+        BFC_CUDA(scan_exclusive<int64_t>(nch, nch_scan, n_dense, scan64_tmp, s));
+        BFC_CUDA(cudaMemcpyAsync(&h_dense_items, nch_scan + n_dense, sizeof(int64_t),
+                                 cudaMemcpyDeviceToHost, s));
+        BFC_CUDA(cudaStreamSynchronize(s));
+        n_items = h_dense_items + n_hash;
+        GET(g->mem, g->cta_items, std::max<int64_t>(n_items, 1));
+        GET(g->mem, g->warp_items, std::max<int64_t>(n_warp, 1));
+        if (n_dense + n_hash + n_warp > 0) {
+            k_emit_items<<<grid_stride_blocks(n_dense + n_hash + n_warp), kT, 0, s>>>(
+                order, n_dense, n_hash, n_warp, nch_scan, l, g->cut, g->vbase, g->cta_items, g->warp_items); note_launch();
+            BFC_CUDA(cudaGetLastError());
+        }
+        // chunk boundaries of every list, so dense items read them instead of searching
+        const int32_t u1 = (int32_t)((r + kChunkUnit - 1) / kChunkUnit) + 1;
+        const int32_t l1 = (int32_t)((l + kChunkUnit - 1) / kChunkUnit) + 1;
+        const int64_t entries = (int64_t)l * u1 + (int64_t)r * l1;
+        // (not for batches: their chunks are relative to each graph's rank range)
+        if (!g->coff && g->num_graphs == 0 && h_dense_items > n_dense && entries <= kChunkTableMaxEntries) {
+            if (!rows_star) {
+                int32_t *rs;
+                GET(tmp, rs, 2 * m);
+                k_rows_from_off<<<grid_stride_blocks((int64_t)n * 32), kT, 0, s>>>(g->off, n, rs); note_launch();
+                BFC_CUDA(cudaGetLastError());
+                rows_star = rs;
+            }
+            GET(g->mem, g->coff, entries);
+            g->coff_u1 = u1;
+            g->coff_l1 = l1;
+            k_coff_fill<<<grid_stride_blocks(entries), kT, 0, s>>>(g->off, l, u1, l1, entries, g->coff); note_launch();
+            BFC_CUDA(cudaGetLastError());
+            k_coff_slots<<<grid_stride_blocks(2 * m), kT, 0, s>>>(g->off, g->adj, rows_star, 2 * m, l, u1, l1, g->coff); note_launch();
+            BFC_CUDA(cudaGetLastError());
+        }
+    } else {
+        GET(g->mem, g->cta_items, 1);
+        GET(g->mem, g->warp_items, 1);
+    }
+    g->n_cta_items = n_items;
+    g->n_warp_items = n_warp;
+    g->info.dense_items = h_dense_items;
+    g->info.starts_with_work = n_dense + n_hash + n_warp;
+    g->info.dense_starts = n_dense;
+    g->info.hash_starts = n_hash;
+    g->info.warp_starts = n_warp;
+    g->opt.warp_max_work = warp_max_work;
+    g->opt.hash_max_work = hash_max_work;
+    BFC_CUDA(cudaStreamSynchronize(s));
+#undef GET
+    return BFC_OK;
+}
+
+int rebin_graph(Graph *g, cudaStream_t s, int32_t warp_max_work, int32_t hash_max_work) {
+    g->mem.stream = s;
+    g->mem.drop(g->cta_items);
+    g->mem.drop(g->warp_items);
+    g->cta_items = nullptr;
+    g->warp_items = nullptr;
+    int rc = schedule_graph(g, s, warp_max_work, hash_max_work, nullptr);
+    g->info.device_bytes = (int64_t)g->mem.total;
+    return rc;
+}
+
+int prepare_graph(const bfc_csr *csr, const bfc_options *opt, cudaStream_t s, Graph *g,
+                  int32_t num_graphs, const int32_t *graph_u_start, const int32_t *graph_l_start) {
     const int32_t r = csr->num_u, l = csr->num_l;
     const int64_t m = csr->num_edges;
     const int32_t n = r + l;
@@ -357,6 +559,20 @@ int prepare_graph(const bfc_csr *csr, const bfc_options *opt, cudaStream_t s, Gr
         if (herr) { set_last_error("adj_u holds an id outside [0, num_l)"); return BFC_ERR_INVALID_GRAPH; }
     }
 
+    if (num_graphs > 0) {
+        k_check_starts<<<blocks_for((int64_t)num_graphs + 1), kT, 0, s>>>(graph_u_start, num_graphs, r, g->err); note_launch();
+        k_check_starts<<<blocks_for((int64_t)num_graphs + 1), kT, 0, s>>>(graph_l_start, num_graphs, l, g->err); note_launch();
+        BFC_CUDA(cudaGetLastError());
+        BFC_CUDA(cudaMemcpyAsync(&herr, g->err, sizeof(int), cudaMemcpyDeviceToHost, s));
+        BFC_CUDA(cudaStreamSynchronize(s));
+        if (herr) { set_last_error("graph start arrays are not prefix sums of the layer sizes"); return BFC_ERR_INVALID_GRAPH; }
+        g->num_graphs = num_graphs;
+        GET(g->mem, g->gstar, std::max<int64_t>(n, 1));
+        GET(g->mem, g->vbase, std::max<int64_t>(n, 1));
+        GET(g->mem, g->gwork, num_graphs);
+        BFC_CUDA(cudaMemsetAsync(g->gwork, 0, sizeof(unsigned long long) * num_graphs, s));
+    }
+
     // ---- temporaries
     const int64_t nsort = std::max<int64_t>({(int64_t)r, (int64_t)l, m, (int64_t)n, 1});
     uint64_t *k0, *k1;
@@ -395,25 +611,43 @@ int prepare_graph(const bfc_csr *csr, const bfc_options *opt, cudaStream_t s, Gr
     // ---- a2: per-layer priority ranks by a stable sort on degree
     int which = 0;
     if (r > 0) {
-        k_iota_keys<<<blocks_for(r), kT, 0, s>>>(deg_u, r, k0, v0); note_launch();
+        int bkey = bits_for((uint64_t)hmax[0]);
+        if (num_graphs > 0) {
+            k_iota_keys_batch<<<blocks_for(r), kT, 0, s>>>(deg_u, r, graph_u_start, num_graphs, bkey, k0, v0); note_launch();
+            bkey += bits_for((uint64_t)(num_graphs - 1));
+        } else {
+            k_iota_keys<<<blocks_for(r), kT, 0, s>>>(deg_u, r, k0, v0); note_launch();
+        }
         BFC_CUDA(cudaGetLastError());
-        BFC_CUDA(radix_sort_pairs(k0, v0, k1, v1, r, 0, bits_for((uint64_t)hmax[0]), hist,
+        BFC_CUDA(radix_sort_pairs(k0, v0, k1, v1, r, 0, bkey, hist,
                                   hist_tmp, s, &which));
         const uint64_t *ks = which ? k1 : k0;
         const int32_t *vs = which ? v1 : v0;
         BFC_CUDA(cudaMemcpyAsync(order_u, vs, sizeof(int32_t) * r, cudaMemcpyDeviceToDevice, s));
-        k_ranks<<<blocks_for(r), kT, 0, s>>>(ks, vs, r, g->rank_u, deg_star, l); note_launch();
+        k_ranks<<<blocks_for(r), kT, 0, s>>>(ks, vs, r, g->rank_u, deg_star, l, (1ull << bits_for((uint64_t)hmax[0])) - 1); note_launch();
         BFC_CUDA(cudaGetLastError());
     }
     if (l > 0) {
-        k_iota_keys<<<blocks_for(l), kT, 0, s>>>(deg_l, l, k0, v0); note_launch();
+        int bkey = bits_for((uint64_t)hmax[1]);
+        if (num_graphs > 0) {
+            k_iota_keys_batch<<<blocks_for(l), kT, 0, s>>>(deg_l, l, graph_l_start, num_graphs, bkey, k0, v0); note_launch();
+            bkey += bits_for((uint64_t)(num_graphs - 1));
+        } else {
+            k_iota_keys<<<blocks_for(l), kT, 0, s>>>(deg_l, l, k0, v0); note_launch();
+        }
         BFC_CUDA(cudaGetLastError());
-        BFC_CUDA(radix_sort_pairs(k0, v0, k1, v1, l, 0, bits_for((uint64_t)hmax[1]), hist,
+        BFC_CUDA(radix_sort_pairs(k0, v0, k1, v1, l, 0, bkey, hist,
                                   hist_tmp, s, &which));
         const uint64_t *ks = which ? k1 : k0;
         const int32_t *vs = which ? v1 : v0;
         BFC_CUDA(cudaMemcpyAsync(order_l, vs, sizeof(int32_t) * l, cudaMemcpyDeviceToDevice, s));
-        k_ranks<<<blocks_for(l), kT, 0, s>>>(ks, vs, l, g->rank_l, deg_star, 0); note_launch();
+        k_ranks<<<blocks_for(l), kT, 0, s>>>(ks, vs, l, g->rank_l, deg_star, 0, (1ull << bits_for((uint64_t)hmax[1])) - 1); note_launch();
+        BFC_CUDA(cudaGetLastError());
+    }
+
+    if (num_graphs > 0 && n > 0) {
+        k_graph_star<<<grid_stride_blocks(n), kT, 0, s>>>(r, l, graph_u_start, graph_l_start,
+                                                         num_graphs, g->gstar, g->vbase); note_launch();
         BFC_CUDA(cudaGetLastError());
     }
 
@@ -427,6 +661,14 @@ int prepare_graph(const bfc_csr *csr, const bfc_options *opt, cudaStream_t s, Gr
     const int bl = bits_for(l > 0 ? (uint64_t)(l - 1) : 0);
     if (m > 0) {
         BFC_CUDA(max_scan_inclusive(heads, rows, m, (int32_t *)scan64_tmp, s));
+        if (num_graphs > 0) {
+            k_check_batch_edges<<<grid_stride_blocks(m), kT, 0, s>>>(rows, csr->adj_u, m, graph_u_start,
+                                                                     graph_l_start, num_graphs, g->err); note_launch();
+            BFC_CUDA(cudaGetLastError());
+            BFC_CUDA(cudaMemcpyAsync(&herr, g->err, sizeof(int), cudaMemcpyDeviceToHost, s));
+            BFC_CUDA(cudaStreamSynchronize(s));
+            if (herr) { set_last_error("an edge joins vertices of two different graphs of the batch"); return BFC_ERR_INVALID_GRAPH; }
+        }
         k_edge_keys<<<grid_stride_blocks(m), kT, 0, s>>>(rows, csr->adj_u, g->rank_u, g->rank_l, m,
                                                           bl, k0, v0); note_launch();
         BFC_CUDA(cudaGetLastError());
@@ -475,6 +717,10 @@ int prepare_graph(const bfc_csr *csr, const bfc_options *opt, cudaStream_t s, Gr
         BFC_CUDA(cudaGetLastError());
         BFC_CUDA(reduce_max_u64(g->work, n, red + 1, s));
     }
+    if (num_graphs > 0 && n > 0) {
+        k_graph_work<<<grid_stride_blocks(n), kT, 0, s>>>(g->work, g->gstar, n, g->gwork); note_launch();
+        BFC_CUDA(cudaGetLastError());
+    }
     unsigned long long hred[2] = {0, 0};
     BFC_CUDA(cudaMemcpyAsync(hred, red, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
     BFC_CUDA(cudaStreamSynchronize(s));
@@ -482,67 +728,11 @@ int prepare_graph(const bfc_csr *csr, const bfc_options *opt, cudaStream_t s, Gr
     g->info.max_start_work = hred[1];
 
     // ---- a5: heaviest-first order and bins
-    const uint64_t warp_max = (uint64_t)opt->warp_max_work;
-    const uint64_t hash_max = (uint64_t)opt->hash_max_work;
-    int64_t n_dense = 0, n_hash = 0, n_warp = 0, n_items = 0;
-    if (n > 0 && hred[0] > 0) {
-        k_sched_keys<<<blocks_for(n), kT, 0, s>>>(g->work, n, hred[1], k0, v0); note_launch();
-        BFC_CUDA(cudaGetLastError());
-        BFC_CUDA(radix_sort_pairs(k0, v0, k1, v1, n, 0, bits_for(hred[1]), hist, hist_tmp, s,
-                                  &which));
-        const int32_t *order = which ? v1 : v0;
-        k_classify<<<grid_stride_blocks(n), kT, 0, s>>>(g->work, n, warp_max, hash_max, red + 2); note_launch();
-        BFC_CUDA(cudaGetLastError());
-        unsigned long long hc[3];
-        BFC_CUDA(cudaMemcpyAsync(hc, red + 2, 3 * sizeof(unsigned long long),
-                                 cudaMemcpyDeviceToHost, s));
-        BFC_CUDA(cudaStreamSynchronize(s));
-        n_dense = (int64_t)hc[0]; n_hash = (int64_t)hc[1]; n_warp = (int64_t)hc[2];
-        int64_t *nch = deg64;   // reuse: n_dense + 1 <= n + 1 entries
-        if (n_dense > 0) {
-            k_chunk_counts<<<blocks_for(n_dense), kT, 0, s>>>(order, n_dense, l, g->cut, nch); note_launch();
-            BFC_CUDA(cudaGetLastError());
-        }
-        // the sorted keys are no longer needed; the other key buffer holds the scan
-        int64_t *nch_scan = reinterpret_cast<int64_t *>(which ? k0 : k1);
-        BFC_CUDA(scan_exclusive<int64_t>(nch, nch_scan, n_dense, scan64_tmp, s));
-        int64_t h_dense_items = 0;
-        BFC_CUDA(cudaMemcpyAsync(&h_dense_items, nch_scan + n_dense, sizeof(int64_t),
-                                 cudaMemcpyDeviceToHost, s));
-        BFC_CUDA(cudaStreamSynchronize(s));
-        n_items = h_dense_items + n_hash;
-        GET(g->mem, g->cta_items, std::max<int64_t>(n_items, 1));
-        GET(g->mem, g->warp_items, std::max<int64_t>(n_warp, 1));
-        if (n_dense + n_hash + n_warp > 0) {
-            k_emit_items<<<grid_stride_blocks(n_dense + n_hash + n_warp), kT, 0, s>>>(
-                order, n_dense, n_hash, n_warp, nch_scan, l, g->cut, g->cta_items, g->warp_items); note_launch();
-            BFC_CUDA(cudaGetLastError());
-        }
-        g->info.dense_items = h_dense_items;
-        // chunk boundaries of every list, so dense items read them instead of searching
-        const int32_t u1 = (int32_t)((r + kChunkUnit - 1) / kChunkUnit) + 1;
-        const int32_t l1 = (int32_t)((l + kChunkUnit - 1) / kChunkUnit) + 1;
-        const int64_t entries = (int64_t)l * u1 + (int64_t)r * l1;
-        if (h_dense_items > n_dense && entries <= kChunkTableMaxEntries) {
-            GET(g->mem, g->coff, entries);
-            g->coff_u1 = u1;
-            g->coff_l1 = l1;
-            k_coff_fill<<<grid_stride_blocks(entries), kT, 0, s>>>(g->off, l, u1, l1, entries, g->coff); note_launch();
-            BFC_CUDA(cudaGetLastError());
-            k_coff_slots<<<grid_stride_blocks(2 * m), kT, 0, s>>>(g->off, g->adj, rows_star, 2 * m, l, u1, l1, g->coff); note_launch();
-            BFC_CUDA(cudaGetLastError());
-        }
-    } else {
-        GET(g->mem, g->cta_items, 1);
-        GET(g->mem, g->warp_items, 1);
+    {
+        int rc = schedule_graph(g, s, opt->warp_max_work, opt->hash_max_work, rows_star);
+        if (rc) return rc;
     }
-    g->n_cta_items = n_items;
-    g->n_warp_items = n_warp;
     g->info.num_u = r; g->info.num_l = l; g->info.num_edges = m;
-    g->info.starts_with_work = n_dense + n_hash + n_warp;
-    g->info.dense_starts = n_dense;
-    g->info.hash_starts = n_hash;
-    g->info.warp_starts = n_warp;
     g->info.device_bytes = (int64_t)g->mem.total;
     BFC_CUDA(cudaStreamSynchronize(s));
 #undef GET
