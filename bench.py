@@ -35,6 +35,7 @@ WORKLOADS = {
     "powerlaw_20m": "chunglu_u1m_l500k_m20m_g2.1 (|U|=1M, |L|=500k, 20M edges, exponent 2.1 both layers, seed 2001+rank)",
     "shopping_300m": "shopping_u10m_l100k_m300m (users exponent 2.5, items exponent 1.8, top item ~1M, seed 3001+rank)",
     "uniform_small": "uniform_u2k_l3k_m20k (seed 1001+rank)",
+    "serve_poisson": "Poisson request stream: graphs drawn as the batched workload (pool of 256, seeds 5001+i) plus 2% large graphs (5M edges, exponent 2.0, |U|=1M, |L|=500k); 120 GB admission budget",
     "batch_4096": "4,096 Chung-Lu graphs, |U|,|L| log-uniform [100, 50k], m log-uniform [1k, 2M] clamped to 0.5|U||L|, exponents uniform [1.8, 2.6], seeds 4000+g (+rank*4096)",
 }
 
@@ -177,6 +178,109 @@ def run_batch(args, rank, world):
         per_graph=dict(graphs_per_s=num / per_graph_s, latency_ms_p50=pct(50), latency_ms_p99=pct(99),
                        note="bfc_prepare + bfc_count + host read of the total, one graph at a time"),
         gpu_launches=launches, clocks=clocks)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    return 0
+
+
+def run_serve(args, rank, world):
+    """Serving: a Poisson stream of counting requests at swept arrival rates,
+    through the continuous-batching server and through plain per-graph
+    launches (a server with one worker and one graph per batch)."""
+    import random
+
+    import numpy as np
+    import torch
+
+    from bfc_inputs import generators as G
+    from paper_1812_00283_gb300 import bfc
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    t0 = time.perf_counter()
+    pool = [G.batch_graph(i, 5001 + rank * 1000, device=dev) for i in range(args.serve_pool)]
+    large = [G.chung_lu_bipartite(1_000_000, 500_000, 5_000_000, 2.0, 2.0, 5900 + rank * 10 + i,
+                                  device=dev) for i in range(max(1, args.serve_pool // 50))]
+    gen_s = time.perf_counter() - t0
+    arrays = [(np.ascontiguousarray(g.off_u), np.ascontiguousarray(g.adj_u)) for g in pool + large]
+    rng = random.Random(5001 + rank)
+    nreq = args.serve_requests
+    # 2% of the requests are large graphs
+    choice = [(len(pool) + rng.randrange(len(large))) if rng.random() < 0.02 else rng.randrange(len(pool))
+              for _ in range(nreq)]
+    gs = pool + large
+
+    def serve(cfg, rate):
+        """Submit the stream at `rate` requests/s (inf = all at once); returns
+        (graphs/s over the makespan, latencies in ms, totals, stats)."""
+        sv = bfc.bfc_server_create(cfg)
+        ids = [0] * nreq
+        arr = np.cumsum([rng2.expovariate(rate) for _ in range(nreq)]) if rate != float("inf") else np.zeros(nreq)
+        try:
+            tstart = time.perf_counter()
+
+            def submit():
+                for j, gi in enumerate(choice):
+                    wait = tstart + arr[j] - time.perf_counter()
+                    if wait > 0:
+                        time.sleep(wait)
+                    g = gs[gi]
+                    off, adj = arrays[gi]
+                    ids[j] = bfc.bfc_server_submit(sv, g.num_u, g.num_l, g.num_edges,
+                                                   off.ctypes.data, adj.ctypes.data)
+            th = threading.Thread(target=submit)
+            th.start()
+            th.join()
+            res = [bfc.bfc_server_poll(sv, rid, True) for rid in ids]
+            makespan = time.perf_counter() - tstart
+            stats = bfc.bfc_server_get_stats(sv)
+        finally:
+            bfc.bfc_server_destroy(sv)
+        if any(st != 0 for st, _, _ in res):
+            raise SystemExit("a served request failed")
+        lat = sorted(1e3 * x for _, _, x in res)
+        return nreq / makespan, lat, [t for _, t, _ in res], stats
+
+    def pct(lat, p):
+        return lat[min(len(lat) - 1, int(round(p / 100 * (len(lat) - 1))))]
+
+    rng2 = random.Random(17)
+    batched_cfg = bfc.bfc_server_config_init(memory_budget_bytes=120 << 30, workers=2)
+    plain_cfg = bfc.bfc_server_config_init(memory_budget_bytes=120 << 30, workers=1, max_batch_graphs=1)
+    # warm-up: pool + kernels
+    serve(batched_cfg, float("inf"))
+    sat_b, lat_b, tot_b, st_b = serve(batched_cfg, float("inf"))
+    sat_p, lat_p, tot_p, st_p = serve(plain_cfg, float("inf"))
+    if tot_b != tot_p:
+        raise SystemExit("served totals differ between batched and plain serving")
+    rates = []
+    for frac in args.serve_rates:
+        lam = frac * sat_b
+        gb, lb, tb, sb = serve(batched_cfg, lam)
+        gp, lp, tp, sp_ = serve(plain_cfg, lam) if lam <= 1.5 * sat_p else (None, None, None, None)
+        if tb != tot_b:
+            raise SystemExit("a served total changed with the arrival rate")
+        row = dict(rate_per_s=lam, frac_of_batched_saturation=frac,
+                   batched=dict(graphs_per_s=gb, p50_ms=pct(lb, 50), p99_ms=pct(lb, 99),
+                                batches=sb["batches"], max_batch=sb["max_batch_graphs"]))
+        if gp is not None:
+            row["per_graph"] = dict(graphs_per_s=gp, p50_ms=pct(lp, 50), p99_ms=pct(lp, 99))
+        else:
+            row["per_graph"] = "not run: arrival rate above 1.5x its saturation (queue grows without bound)"
+        rates.append(row)
+    out = dict(
+        metric=METRIC, value=sat_b, unit="graphs/s", n_gpus=world, steps=nreq, warmup=nreq,
+        ms_per_step=1e3 / sat_b, higher_is_better=True, scaling="weak", vs_baseline=None,
+        dtype="u64", data="synthetic",
+        config=dict(workload=WORKLOADS["serve_poisson"], requests_per_rate=nreq, pool=len(pool),
+                    large_graphs=len(large), generation_s=gen_s,
+                    step="one request: H2D of its CSR, prepare + count in a batch, D2H of its total"),
+        saturation=dict(batched=dict(graphs_per_s=sat_b, p50_ms=pct(lat_b, 50), p99_ms=pct(lat_b, 99),
+                                     batches=st_b["batches"], max_batch=st_b["max_batch_graphs"],
+                                     peak_bytes=st_b["peak_bytes_in_use"]),
+                        per_graph=dict(graphs_per_s=sat_p, p50_ms=pct(lat_p, 50), p99_ms=pct(lat_p, 99))),
+        rates=rates)
     if rank == 0:
         print(json.dumps(out), flush=True)
     return 0
@@ -329,6 +433,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--batch-graphs", type=int, default=4096)
+    ap.add_argument("--serve-pool", type=int, default=256)
+    ap.add_argument("--serve-requests", type=int, default=10000)
+    ap.add_argument("--serve-rates", type=float, nargs="*", default=[0.25, 0.5, 1.0, 1.5])
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -337,6 +444,8 @@ def main():
         return run_reference(args, rank, world)
     if args.workload == "batch_4096":
         return run_batch(args, rank, world)
+    if args.workload == "serve_poisson":
+        return run_serve(args, rank, world)
 
     import torch
     import torch.distributed as dist

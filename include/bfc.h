@@ -179,6 +179,58 @@ int bfc_batch_wedges(const bfc_graph *g, void *stream, uint64_t *wedges_dev);
  * Synchronises `stream`; allocates only the schedule arrays. */
 int bfc_autotune(bfc_graph *g, void *stream, int iters, bfc_options *chosen);
 
+/* ---- Serving: continuous batching of counting requests -------------------
+ * Requests (one graph each, U-side CSR in HOST memory) may arrive at any time
+ * from any thread.  Worker threads (one CUDA stream each) take the oldest
+ * waiting requests that fit the device-memory budget, count them as one
+ * batch (bfc_prepare_batch + bfc_count_batch), and complete them; requests
+ * that arrive while other batches are on the GPU are admitted as soon as a
+ * worker and memory are free, so batches overlap on the device.  A request's
+ * total is exactly its graph's count alone (no butterfly spans two graphs of
+ * a batch).  The paper has no serving layer; this wraps steps a1-a9 only. */
+typedef struct bfc_server bfc_server;
+
+typedef struct bfc_server_config {
+    int64_t memory_budget_bytes; /* device bytes admitted batches may hold at once (default 120 GiB) */
+    int32_t workers;             /* worker threads / streams (default 2, range [1, 16]) */
+    int32_t max_batch_graphs;    /* requests per batch at most (default 1024; 1 = one graph per launch) */
+    int64_t max_batch_edges;     /* edges per batch at most, unless one request alone is larger (default 2^26) */
+    int32_t warp_max_work;       /* bin thresholds passed to every batch (0 = library default) */
+    int32_t hash_max_work;
+    int32_t reserved[8];
+} bfc_server_config;
+
+typedef struct bfc_server_stats {
+    int64_t submitted, completed, failed, batches;
+    int64_t max_batch_graphs;    /* largest batch formed */
+    int64_t peak_bytes_in_use;   /* largest admitted footprint (estimate) */
+    int64_t bytes_in_use;        /* admitted footprint now */
+    int64_t waiting;             /* requests not yet admitted */
+} bfc_server_stats;
+
+void bfc_server_config_init(bfc_server_config *cfg);
+
+/* Starts the workers on the current device. */
+int bfc_server_create(const bfc_server_config *cfg, bfc_server **out);
+
+/* Queues one request.  off_u_host[num_u + 1] / adj_u_host[num_edges] must stay
+ * valid until bfc_server_poll reports the request complete.  A request whose
+ * footprint alone exceeds the budget returns BFC_ERR_OUT_OF_MEMORY. */
+int bfc_server_submit(bfc_server *sv, int32_t num_u, int32_t num_l, int64_t num_edges,
+                      const int32_t *off_u_host, const int32_t *adj_u_host, uint64_t *request_id);
+
+/* *status = -1 while pending, else the request's bfc_status; when complete,
+ * *total = ⋈ of its graph, *latency_s = seconds from submit to completion,
+ * and the request id is retired.  wait != 0 blocks until completion. */
+int bfc_server_poll(bfc_server *sv, uint64_t request_id, int wait, uint64_t *total, int *status,
+                    double *latency_s);
+
+int bfc_server_get_stats(bfc_server *sv, bfc_server_stats *out);
+
+/* Stops the workers after the batches in flight; requests never admitted
+ * complete with BFC_ERR_INTERNAL.  No thread may be inside bfc_server_poll. */
+void bfc_server_destroy(bfc_server *sv);
+
 /* Waits for `stream` and reports any error a kernel of this graph flagged
  * since the last bfc_sync (BFC_ERR_INTERNAL), then clears the flag. */
 int bfc_sync(bfc_graph *g, void *stream);

@@ -51,6 +51,21 @@ class bfc_batch(ctypes.Structure):
     _fields_ = [("num_graphs", c_int32), ("graph_u_start", c_void_p), ("graph_l_start", c_void_p)]
 
 
+class bfc_server_config(ctypes.Structure):
+    _fields_ = [("memory_budget_bytes", c_int64), ("workers", c_int32), ("max_batch_graphs", c_int32),
+                ("max_batch_edges", c_int64), ("warp_max_work", c_int32), ("hash_max_work", c_int32),
+                ("reserved", c_int32 * 8)]
+
+
+class bfc_server_stats(ctypes.Structure):
+    _fields_ = [(k, c_int64) for k in ("submitted", "completed", "failed", "batches",
+                                       "max_batch_graphs", "peak_bytes_in_use", "bytes_in_use",
+                                       "waiting")]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class BfcError(RuntimeError):
     def __init__(self, status: int, where: str, msg: str):
         super().__init__(f"{where}: {STATUS.get(status, status)}: {msg}")
@@ -85,6 +100,14 @@ _SIGS = {
     "bfc_count_batch": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "bfc_batch_wedges": (c_int, [c_void_p, c_void_p, c_void_p]),
     "bfc_autotune": (c_int, [c_void_p, c_void_p, c_int, ctypes.POINTER(bfc_options)]),
+    "bfc_server_config_init": (None, [ctypes.POINTER(bfc_server_config)]),
+    "bfc_server_create": (c_int, [ctypes.POINTER(bfc_server_config), ctypes.POINTER(c_void_p)]),
+    "bfc_server_submit": (c_int, [c_void_p, c_int32, c_int32, c_int64, c_void_p, c_void_p,
+                                  ctypes.POINTER(c_uint64)]),
+    "bfc_server_poll": (c_int, [c_void_p, c_uint64, c_int, ctypes.POINTER(c_uint64),
+                                ctypes.POINTER(c_int), ctypes.POINTER(ctypes.c_double)]),
+    "bfc_server_get_stats": (c_int, [c_void_p, ctypes.POINTER(bfc_server_stats)]),
+    "bfc_server_destroy": (None, [c_void_p]),
     "bfc_count_small_noalloc": (c_int, [c_int32, c_int32, c_int64, c_void_p, c_void_p, c_void_p,
                                         c_void_p, c_void_p]),
 }
@@ -188,6 +211,49 @@ def bfc_autotune(g: int, stream: int = 0, iters: int = 2) -> bfc_options:
     o = bfc_options()
     _check(_lib.bfc_autotune(g, stream, iters, ctypes.byref(o)), "bfc_autotune")
     return o
+
+
+def bfc_server_config_init(**overrides) -> bfc_server_config:
+    c = bfc_server_config()
+    _lib.bfc_server_config_init(ctypes.byref(c))
+    for k, v in overrides.items():
+        setattr(c, k, v)
+    return c
+
+
+def bfc_server_create(cfg: bfc_server_config | None = None) -> int:
+    h = c_void_p()
+    _check(_lib.bfc_server_create(ctypes.byref(cfg) if cfg else None, ctypes.byref(h)),
+           "bfc_server_create")
+    return h.value
+
+
+def bfc_server_submit(sv: int, num_u: int, num_l: int, num_edges: int, off_u_host: int,
+                      adj_u_host: int) -> int:
+    rid = c_uint64(0)
+    _check(_lib.bfc_server_submit(sv, num_u, num_l, num_edges, off_u_host, adj_u_host,
+                                  ctypes.byref(rid)), "bfc_server_submit")
+    return int(rid.value)
+
+
+def bfc_server_poll(sv: int, request_id: int, wait: bool = True):
+    """Returns (status, total, latency_s); status -1 = still pending."""
+    t = c_uint64(0)
+    st = c_int(-1)
+    lat = ctypes.c_double(0.0)
+    _check(_lib.bfc_server_poll(sv, request_id, 1 if wait else 0, ctypes.byref(t), ctypes.byref(st),
+                                ctypes.byref(lat)), "bfc_server_poll")
+    return int(st.value), int(t.value), float(lat.value)
+
+
+def bfc_server_get_stats(sv: int) -> dict:
+    o = bfc_server_stats()
+    _check(_lib.bfc_server_get_stats(sv, ctypes.byref(o)), "bfc_server_get_stats")
+    return o.as_dict()
+
+
+def bfc_server_destroy(sv: int):
+    _lib.bfc_server_destroy(sv)
 
 
 def bfc_count_small_noalloc(num_u: int, num_l: int, num_edges: int, off_u: int, adj_u: int,

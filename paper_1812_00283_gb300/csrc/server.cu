@@ -1,0 +1,324 @@
+// A continuous-batching request server for butterfly counts.
+//
+// Requests (one graph each, U-side CSR in host memory) arrive at any time.
+// Worker threads, each with its own CUDA stream, repeatedly take the oldest
+// waiting requests that fit the device-memory budget, copy them into one
+// disjoint-union batch on the device, prepare the batch and count it in one
+// persistent launch (bfc_prepare_batch / bfc_count_batch), and complete the
+// requests with their per-graph totals.  While one worker's batch is on the
+// GPU, the next worker admits the requests that arrived meanwhile, so batches
+// overlap on the device and memory freed by a finished batch is reused at
+// once.  The method itself is untouched: the totals are exactly the counts of
+// each graph alone (butterflies never span graphs of a disjoint union).
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "bfc_internal.cuh"
+
+namespace bfc {
+namespace {
+
+// device footprint estimate of a batch (arena, prepare temporaries, union CSR)
+int64_t batch_bytes(int64_t r, int64_t l, int64_t m) {
+    return 96 * m + 64 * (r + l) + (4 << 20);
+}
+
+// offsets and ids of each graph shifted into the union's id space
+__global__ void k_union_fixup(int32_t *off, int32_t *adj, const int64_t *__restrict__ e_start,
+                              const int32_t *__restrict__ u_start,
+                              const int32_t *__restrict__ l_start, int32_t num_graphs,
+                              int64_t total_u, int64_t total_m) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total_m; i += stride) {
+        int32_t lo = 0, hi = num_graphs;
+        while (hi - lo > 1) {
+            const int32_t mid = (lo + hi) >> 1;
+            if (e_start[mid] <= i) lo = mid; else hi = mid;
+        }
+        adj[i] += l_start[lo];
+    }
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total_u; i += stride) {
+        int32_t lo = 0, hi = num_graphs;
+        while (hi - lo > 1) {
+            const int32_t mid = (lo + hi) >> 1;
+            if (u_start[mid] <= i) lo = mid; else hi = mid;
+        }
+        off[i] += (int32_t)e_start[lo];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) off[total_u] = (int32_t)total_m;
+}
+
+struct Request {
+    uint64_t id;
+    int32_t r, l;
+    int64_t m;
+    const int32_t *off;
+    const int32_t *adj;
+    int64_t bytes;
+    std::chrono::steady_clock::time_point t_submit, t_done;
+    int status = -1;        // -1 pending, else a bfc_status
+    uint64_t total = 0;
+};
+
+}  // namespace
+}  // namespace bfc
+
+struct bfc_server {
+    bfc_server_config cfg{};
+    int device = 0;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<bfc::Request *> waiting;
+    std::unordered_map<uint64_t, bfc::Request *> all;
+    std::vector<std::thread> workers;
+    uint64_t next_id = 1;
+    int64_t bytes_in_use = 0;
+    bool stop = false;
+    bfc_server_stats stats{};
+};
+
+namespace bfc {
+namespace {
+
+void complete(bfc_server *sv, std::vector<Request *> &batch, int status, const uint64_t *totals) {
+    const auto now = std::chrono::steady_clock::now();
+    std::lock_guard<std::mutex> lk(sv->mu);
+    for (size_t i = 0; i < batch.size(); ++i) {
+        batch[i]->status = status;
+        batch[i]->total = (status == BFC_OK && totals) ? totals[i] : 0;
+        batch[i]->t_done = now;
+        if (status == BFC_OK) sv->stats.completed += 1; else sv->stats.failed += 1;
+    }
+    sv->cv_done.notify_all();
+}
+
+// Counts one batch on stream s; returns a bfc_status.
+int run_batch(bfc_server *sv, std::vector<Request *> &batch, cudaStream_t s,
+              std::vector<uint64_t> &totals) {
+    const int32_t G = (int32_t)batch.size();
+    std::vector<int32_t> us(G + 1, 0), ls(G + 1, 0);
+    std::vector<int64_t> es(G + 1, 0);
+    for (int32_t g = 0; g < G; ++g) {
+        us[g + 1] = us[g] + batch[g]->r;
+        ls[g + 1] = ls[g] + batch[g]->l;
+        es[g + 1] = es[g] + batch[g]->m;
+    }
+    Allocs in;
+    in.stream = s;
+    struct Guard { Allocs *a; ~Guard() { a->release(); } } guard{&in};
+    int32_t *off = nullptr, *adj = nullptr, *dus = nullptr, *dls = nullptr;
+    int64_t *des = nullptr;
+    unsigned long long *dtot = nullptr;
+    if (in.get(&off, (size_t)us[G] + 1) || in.get(&adj, (size_t)std::max<int64_t>(es[G], 1)) ||
+        in.get(&dus, (size_t)G + 1) || in.get(&dls, (size_t)G + 1) || in.get(&des, (size_t)G + 1) ||
+        in.get(&dtot, (size_t)G))
+        return BFC_ERR_OUT_OF_MEMORY;
+    for (int32_t g = 0; g < G; ++g) {
+        BFC_CUDA(cudaMemcpyAsync(off + us[g], batch[g]->off, sizeof(int32_t) * batch[g]->r,
+                                 cudaMemcpyHostToDevice, s));
+        if (batch[g]->m > 0)
+            BFC_CUDA(cudaMemcpyAsync(adj + es[g], batch[g]->adj, sizeof(int32_t) * batch[g]->m,
+                                     cudaMemcpyHostToDevice, s));
+    }
+    BFC_CUDA(cudaMemcpyAsync(dus, us.data(), sizeof(int32_t) * (G + 1), cudaMemcpyHostToDevice, s));
+    BFC_CUDA(cudaMemcpyAsync(dls, ls.data(), sizeof(int32_t) * (G + 1), cudaMemcpyHostToDevice, s));
+    BFC_CUDA(cudaMemcpyAsync(des, es.data(), sizeof(int64_t) * (G + 1), cudaMemcpyHostToDevice, s));
+    {
+        int64_t work = std::max<int64_t>(es[G], us[G]);
+        int blocks = (int)std::min<int64_t>((work + 255) / 256, 152 * 32);
+        if (blocks < 1) blocks = 1;
+        k_union_fixup<<<blocks, 256, 0, s>>>(off, adj, des, dus, dls, G, us[G], es[G]);
+        note_launch();
+        BFC_CUDA(cudaGetLastError());
+    }
+    bfc_csr csr{us[G], ls[G], es[G], off, adj};
+    bfc_batch b{G, dus, dls};
+    bfc_options opt;
+    bfc_options_init(&opt);
+    opt.warp_max_work = sv->cfg.warp_max_work > 0 ? sv->cfg.warp_max_work : opt.warp_max_work;
+    opt.hash_max_work = sv->cfg.hash_max_work > 0 ? sv->cfg.hash_max_work : opt.hash_max_work;
+    bfc_graph *h = nullptr;
+    int rc = bfc_prepare_batch(&csr, &b, &opt, s, &h);
+    if (rc) return rc;
+    rc = bfc_count_batch(h, s, reinterpret_cast<uint64_t *>(dtot), nullptr);
+    if (rc == BFC_OK) {
+        totals.assign(G, 0);
+        cudaError_t e = cudaMemcpyAsync(totals.data(), dtot, sizeof(uint64_t) * G,
+                                        cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) rc = cuda_fail(e, "cudaMemcpyAsync(D2H totals)");
+    }
+    if (rc == BFC_OK) rc = bfc_sync(h, s);
+    bfc_release(h);
+    cudaStreamSynchronize(s);
+    return rc;
+}
+
+void worker_main(bfc_server *sv) {
+    cudaSetDevice(sv->device);
+    cudaStream_t s;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return;
+    std::vector<uint64_t> totals;
+    for (;;) {
+        std::vector<Request *> batch;
+        int64_t bytes = 0;
+        {
+            std::unique_lock<std::mutex> lk(sv->mu);
+            // admit the oldest waiting requests that fit the budget and the batch limits
+            for (;;) {
+                if (sv->stop) break;
+                if (!sv->waiting.empty() &&
+                    sv->bytes_in_use + sv->waiting.front()->bytes <= sv->cfg.memory_budget_bytes)
+                    break;
+                sv->cv_work.wait(lk);
+            }
+            if (sv->stop && sv->waiting.empty()) break;
+            if (sv->stop && sv->bytes_in_use + sv->waiting.front()->bytes > sv->cfg.memory_budget_bytes) break;
+            int64_t edges = 0;
+            while (!sv->waiting.empty() && (int32_t)batch.size() < sv->cfg.max_batch_graphs) {
+                Request *q = sv->waiting.front();
+                if (sv->bytes_in_use + bytes + q->bytes > sv->cfg.memory_budget_bytes) break;
+                if (!batch.empty() && edges + q->m > sv->cfg.max_batch_edges) break;
+                sv->waiting.pop_front();
+                batch.push_back(q);
+                bytes += q->bytes;
+                edges += q->m;
+            }
+            sv->bytes_in_use += bytes;
+            if (sv->bytes_in_use > sv->stats.peak_bytes_in_use) sv->stats.peak_bytes_in_use = sv->bytes_in_use;
+            sv->stats.batches += 1;
+            if ((int64_t)batch.size() > sv->stats.max_batch_graphs) sv->stats.max_batch_graphs = (int64_t)batch.size();
+        }
+        int rc = run_batch(sv, batch, s, totals);
+        {
+            std::lock_guard<std::mutex> lk(sv->mu);
+            sv->bytes_in_use -= bytes;
+        }
+        sv->cv_work.notify_all();
+        complete(sv, batch, rc, rc == BFC_OK ? totals.data() : nullptr);
+    }
+    cudaStreamDestroy(s);
+}
+
+}  // namespace
+}  // namespace bfc
+
+extern "C" {
+
+void bfc_server_config_init(bfc_server_config *c) {
+    if (!c) return;
+    memset(c, 0, sizeof(*c));
+    c->memory_budget_bytes = 120ll << 30;
+    c->workers = 2;
+    c->max_batch_graphs = 1024;
+    c->max_batch_edges = 64ll << 20;
+}
+
+int bfc_server_create(const bfc_server_config *cfg, bfc_server **out) {
+    bfc::set_last_error("");
+    if (!out) { bfc::set_last_error("null argument"); return BFC_ERR_INVALID_ARGUMENT; }
+    *out = nullptr;
+    bfc_server_config c;
+    if (cfg) c = *cfg; else bfc_server_config_init(&c);
+    if (c.workers < 1 || c.workers > 16 || c.max_batch_graphs < 1 || c.memory_budget_bytes <= 0 ||
+        c.max_batch_edges < 1) {
+        bfc::set_last_error("invalid server configuration");
+        return BFC_ERR_INVALID_ARGUMENT;
+    }
+    bfc_server *sv = new (std::nothrow) bfc_server();
+    if (!sv) { bfc::set_last_error("host allocation failed"); return BFC_ERR_OUT_OF_MEMORY; }
+    sv->cfg = c;
+    cudaError_t e = cudaGetDevice(&sv->device);
+    if (e != cudaSuccess) { delete sv; return bfc::cuda_fail(e, "cudaGetDevice"); }
+    int rc = bfc::count_smem_setup(sv->device);   // before any worker launches
+    if (rc) { delete sv; return rc; }
+    for (int i = 0; i < c.workers; ++i) sv->workers.emplace_back(bfc::worker_main, sv);
+    *out = sv;
+    return BFC_OK;
+}
+
+int bfc_server_submit(bfc_server *sv, int32_t num_u, int32_t num_l, int64_t num_edges,
+                      const int32_t *off_u_host, const int32_t *adj_u_host, uint64_t *request_id) {
+    bfc::set_last_error("");
+    if (!sv || !off_u_host || (num_edges > 0 && !adj_u_host) || !request_id || num_u < 0 ||
+        num_l < 0 || num_edges < 0 || num_edges > 2147483647LL) {
+        bfc::set_last_error("invalid request");
+        return BFC_ERR_INVALID_ARGUMENT;
+    }
+    bfc::Request *q = new (std::nothrow) bfc::Request();
+    if (!q) { bfc::set_last_error("host allocation failed"); return BFC_ERR_OUT_OF_MEMORY; }
+    q->r = num_u; q->l = num_l; q->m = num_edges; q->off = off_u_host; q->adj = adj_u_host;
+    q->bytes = bfc::batch_bytes(num_u, num_l, num_edges);
+    q->t_submit = std::chrono::steady_clock::now();
+    std::lock_guard<std::mutex> lk(sv->mu);
+    if (q->bytes > sv->cfg.memory_budget_bytes) {
+        delete q;
+        bfc::set_last_error("request exceeds the server's memory budget on its own");
+        return BFC_ERR_OUT_OF_MEMORY;
+    }
+    q->id = sv->next_id++;
+    sv->all[q->id] = q;
+    sv->waiting.push_back(q);
+    sv->stats.submitted += 1;
+    *request_id = q->id;
+    sv->cv_work.notify_one();
+    return BFC_OK;
+}
+
+int bfc_server_poll(bfc_server *sv, uint64_t request_id, int wait, uint64_t *total, int *status,
+                    double *latency_s) {
+    if (!sv || !status) { bfc::set_last_error("null argument"); return BFC_ERR_INVALID_ARGUMENT; }
+    std::unique_lock<std::mutex> lk(sv->mu);
+    auto it = sv->all.find(request_id);
+    if (it == sv->all.end()) { bfc::set_last_error("unknown request id"); return BFC_ERR_INVALID_ARGUMENT; }
+    bfc::Request *q = it->second;
+    if (wait) sv->cv_done.wait(lk, [q] { return q->status >= 0; });
+    *status = q->status;
+    if (q->status >= 0) {
+        if (total) *total = q->total;
+        if (latency_s)
+            *latency_s = std::chrono::duration<double>(q->t_done - q->t_submit).count();
+        sv->all.erase(it);
+        delete q;
+    }
+    return BFC_OK;
+}
+
+int bfc_server_get_stats(bfc_server *sv, bfc_server_stats *out) {
+    if (!sv || !out) { bfc::set_last_error("null argument"); return BFC_ERR_INVALID_ARGUMENT; }
+    std::lock_guard<std::mutex> lk(sv->mu);
+    *out = sv->stats;
+    out->bytes_in_use = sv->bytes_in_use;
+    out->waiting = (int64_t)sv->waiting.size();
+    return BFC_OK;
+}
+
+void bfc_server_destroy(bfc_server *sv) {
+    if (!sv) return;
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        sv->stop = true;
+    }
+    sv->cv_work.notify_all();
+    for (auto &t : sv->workers) t.join();
+    {
+        // requests never admitted are cancelled
+        std::lock_guard<std::mutex> lk(sv->mu);
+        for (bfc::Request *q : sv->waiting) {
+            q->status = BFC_ERR_INTERNAL;
+            sv->stats.failed += 1;
+        }
+        sv->waiting.clear();
+        sv->cv_done.notify_all();
+    }
+    for (auto &kv : sv->all) delete kv.second;
+    delete sv;
+}
+
+}  // extern "C"
