@@ -431,6 +431,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="powerlaw_20m", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--orientation", type=int, default=0, choices=[0, 1],
+                    help="0 = Algorithm 2 (start highest), 1 = Algorithm 3 (end highest)")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--batch-graphs", type=int, default=4096)
     ap.add_argument("--serve-pool", type=int, default=256)
@@ -467,10 +469,12 @@ def main():
     total = torch.zeros(1, dtype=torch.int64, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
+    step_opts = bfc.bfc_options_init(orientation=args.orientation)
+
     def one_step(ev=None):
         if ev:
             ev[0].record(stream)
-        h = bfc.bfc_prepare(r, l, m, off.data_ptr(), adj.data_ptr(), None, sp)
+        h = bfc.bfc_prepare(r, l, m, off.data_ptr(), adj.data_ptr(), step_opts, sp)
         if ev:
             ev[1].record(stream)
         bfc.bfc_count(h, sp, total.data_ptr())
@@ -544,7 +548,7 @@ def main():
         for i in range(args.e2e_steps + 1):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            tot, wd = bfc.bfc_count_host(r, l, m, off_h.data_ptr(), adj_h.data_ptr(), None, sp)
+            tot, wd = bfc.bfc_count_host(r, l, m, off_h.data_ptr(), adj_h.data_ptr(), step_opts, sp)
             ts.append(time.perf_counter() - t0)
             if tot != expect or wd != W:
                 raise SystemExit("end-to-end count disagrees with the device-resident count")
@@ -578,6 +582,7 @@ def main():
                         step="prepare (a1-a5) + count (a6-a7), CSR resident in HBM",
                         l2="flushed between steps (512 MB write outside the timed events)",
                         parallelism=f"replicas x{world} (independent graphs, no collective)",
+                        orientation=["Algorithm 2 (BFC-VP)", "Algorithm 3 (BFC-VP++)"][args.orientation],
                         prepare_ms_median=statistics.median(prep_ms),
                         count_ms_median=statistics.median(count_ms),
                         count_only_wedges_per_s=W / cnt_s,

@@ -88,7 +88,16 @@ typedef struct bfc_options {
     int32_t wide_positions; /* 1: count with 64-bit adjacency positions even when
                                32 bits suffice (they are used automatically when
                                the graph has 2^30 edges or more); default 0 */
-    int32_t reserved[11];   /* must be zero */
+    int32_t orientation;    /* which wedges are enumerated (same W by Lemma 4):
+                               0 (default) = Algorithm 2: start u highest,
+                               p(v) < p(u), p(w) < p(u);
+                               1 = Algorithm 3 (BFC-VP++): end w highest,
+                               p(w) > p(u), p(w) > p(v).  With 1, every start
+                               beyond the warp bin gets a CTA hash table and a
+                               start whose table fills up is counted again by a
+                               chunked dense pass; hash_max_work is then ignored
+                               except that 0 sends all of them to that pass. */
+    int32_t reserved[10];   /* must be zero */
 } bfc_options;
 
 /* Figures of a prepared graph (host values). */

@@ -79,7 +79,8 @@ static int check_options(const bfc_options *o) {
         bfc::set_last_error("warp_max_work must lie in [0, 256]");
         return BFC_ERR_INVALID_ARGUMENT;
     }
-    if (o->hash_max_work < o->warp_max_work || o->hash_max_work > bfc::kHashMaxWork) {
+    if ((o->hash_max_work < o->warp_max_work && !(o->orientation == 1 && o->hash_max_work == 0)) ||
+        o->hash_max_work > bfc::kHashMaxWork || o->hash_max_work < 0) {
         bfc::set_last_error("hash_max_work must lie in [warp_max_work, 16384]");
         return BFC_ERR_INVALID_ARGUMENT;
     }
@@ -91,7 +92,11 @@ static int check_options(const bfc_options *o) {
         bfc::set_last_error("wide_positions must be 0 or 1");
         return BFC_ERR_INVALID_ARGUMENT;
     }
-    for (int i = 0; i < 11; ++i)
+    if (o->orientation != 0 && o->orientation != 1) {
+        bfc::set_last_error("orientation must be 0 (Algorithm 2) or 1 (Algorithm 3)");
+        return BFC_ERR_INVALID_ARGUMENT;
+    }
+    for (int i = 0; i < 10; ++i)
         if (o->reserved[i] != 0) {
             bfc::set_last_error("reserved option fields must be zero");
             return BFC_ERR_INVALID_ARGUMENT;

@@ -144,6 +144,13 @@ struct Graph {
     int32_t num_graphs = 0;
     int32_t *gstar = nullptr;             // [n] graph of each vertex of G*
     int32_t *vbase = nullptr;             // [n] first G* id of x's graph in x's layer
+    int32_t *vend = nullptr;              // [n] one past the last G* id of x's graph in x's layer
+    // Algorithm 3 orientation: per slot e = (x, v), the run of N(v) holding
+    // the ends above both x and v starts at sbeg[e] and has plen[e] entries
+    int64_t *sbeg = nullptr;
+    int32_t *retry = nullptr;             // starts counted by the chunked retry pass
+    int64_t retry_static = 0;             // of which assigned there by prepare
+    int64_t retry_cap = 0;
     unsigned long long *gwork = nullptr;  // [num_graphs] wedges per graph
 };
 

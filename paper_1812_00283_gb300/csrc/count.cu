@@ -47,6 +47,13 @@ struct CountParams {
     const int32_t *__restrict__ coff;  // chunk-boundary table (nullable)
     const int32_t *__restrict__ gstar; // graph of each G* vertex (batch mode)
     const int32_t *__restrict__ vbase; // first id of x's graph in x's layer (batch mode)
+    const int32_t *__restrict__ vend;  // one past the last id of x's graph in x's layer (batch mode)
+    const int64_t *__restrict__ sbeg;  // Algorithm 3: start of each slot's run of ends
+    int32_t *retry;                    // Algorithm 3: starts left to the chunked retry pass
+    int64_t retry_cap;
+    int64_t retry_static;              // retry[0, retry_static) were assigned by prepare
+    int32_t orient;                    // 0 = Algorithm 2, 1 = Algorithm 3
+    int32_t n;
     unsigned long long *gtot;          // per-graph totals (batch mode)
     int32_t coff_u1, coff_l1;          // entries per L vertex / per U vertex
     int64_t adj_len;
@@ -71,6 +78,8 @@ struct SharedCTA {
     long long wtot[32];
     unsigned long long red[32];
     int item;
+    int overflow;   // Algorithm 3: this item's hash table filled up
+    int inserts;    // Algorithm 3: distinct ends inserted so far
 };
 
 __device__ __forceinline__ unsigned long long c2(unsigned long long c) {
@@ -146,7 +155,8 @@ __device__ __forceinline__ uint32_t hash_slot(int32_t key, uint32_t mask) {
 
 // Finds (inserting if absent) the slot of `key`.  Returns -1 if the table is
 // full, which the slot sizing rules out.
-__device__ __forceinline__ int hash_find(int32_t *keys, uint32_t mask, int32_t key, bool insert) {
+__device__ __forceinline__ int hash_find(int32_t *keys, uint32_t mask, int32_t key, bool insert,
+                                         int *inserted = nullptr) {
     uint32_t h = hash_slot(key, mask);
     for (uint32_t probe = 0; probe <= mask; ++probe) {
         int32_t k = *((volatile int32_t *)(keys + h));
@@ -154,7 +164,11 @@ __device__ __forceinline__ int hash_find(int32_t *keys, uint32_t mask, int32_t k
         if (k == -1) {
             if (!insert) return -1;
             int32_t prev = atomicCAS(keys + h, -1, key);
-            if (prev == -1 || prev == key) return (int)h;
+            if (prev == -1) {
+                if (inserted) *inserted = 1;
+                return (int)h;
+            }
+            if (prev == key) return (int)h;
         }
         h = (h + 1) & mask;
     }
@@ -183,15 +197,25 @@ __device__ __forceinline__ unsigned long long wedge_op(const CountParams &p, int
                                                        Pos pos, int q, int32_t lb, int32_t lo,
                                                        int32_t span, uint32_t hmask,
                                                        unsigned char *ctr,
-                                                       unsigned long long *msum) {
+                                                       unsigned long long *msum, int *ovf,
+                                                       int *ins) {
     uint32_t *w32 = reinterpret_cast<uint32_t *>(ctr);
     uint32_t c;
     if (KIND == kHash) {
         int32_t *hkeys = reinterpret_cast<int32_t *>(ctr);
         uint32_t *hcnt = reinterpret_cast<uint32_t *>(ctr + (size_t)(hmask + 1) * 4);
-        const int slot = hash_find(hkeys, hmask, w - lb, !kSecond);
-        if (slot < 0) { atomicOr(p.err, kErrHashFull); return 0; }
-        if (!kSecond) return inc16(hcnt, slot);
+        int inserted = 0;
+        const int slot = hash_find(hkeys, hmask, w - lb, !kSecond, &inserted);
+        if (slot < 0) {
+            // Algorithm 3 sizes tables by a guess: a full table sends the start
+            // to the retry pass; Algorithm 2's sizing rules it out
+            if (p.orient && !kSecond) *ovf = 1; else atomicOr(p.err, kErrHashFull);
+            return 0;
+        }
+        if (!kSecond) {
+            if (inserted && p.orient && atomicAdd(ins, 1) >= (int)((hmask + 1) / 4 * 3)) *ovf = 1;
+            return inc16(hcnt, slot);
+        }
         c = get16(hcnt, slot);
     } else {
         const int idx = w - lb - lo;
@@ -223,14 +247,16 @@ __device__ __forceinline__ unsigned long long wedge_op(const CountParams &p, int
 // windows are in flight per iteration so their end loads overlap.
 template <int MODE, int KIND, bool kSecond, typename Pos, class SH>
 __device__ unsigned long long cta_walk(const CountParams &p, int32_t x, int32_t lb, int32_t lo,
-                                       int32_t hi, int32_t R, uint32_t hmask, unsigned char *ctr,
+                                       int32_t hi, int flags, uint32_t hmask, unsigned char *ctr,
                                        SH &sh) {
     constexpr int kPer = Batch<Pos>::kPer;
     constexpr int kB = Batch<Pos>::kSize;
     constexpr int kU = 4;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t e0 = p.off[x];
-    const int32_t nmid = p.cut[x];
+    // Algorithm 2: the middles are the cut[x] lower-priority neighbours;
+    // Algorithm 3: every neighbour is a middle
+    const int32_t nmid = p.orient ? (int32_t)(p.off[x + 1] - e0) : p.cut[x];
     const int32_t span = hi - lo;
     const uint32_t le_mask = 0xffffffffu >> (31 - lane);
     unsigned long long acc = 0;
@@ -248,17 +274,19 @@ __device__ unsigned long long cta_walk(const CountParams &p, int32_t x, int32_t 
                 e[i] = e0 + j;
                 v[i] = __ldg(p.adj + e[i]);
                 const int32_t pl = __ldg(p.plen + e[i]);
-                const int64_t b = __ldg(p.off + v[i]);
+                // run of ends: prefix of N(v) below x (Algorithm 2) or the
+                // suffix above both x and v (Algorithm 3)
+                const int64_t b = p.orient ? __ldg(p.sbeg + e[i]) : __ldg(p.off + v[i]);
                 int32_t s0 = 0, s1 = pl;
                 if (KIND != kHash) {
                     if (p.coff) {
                         const int64_t tb = v[i] < p.l ? (int64_t)v[i] * p.coff_u1
                                                       : (int64_t)p.l * p.coff_u1 + (int64_t)(v[i] - p.l) * p.coff_l1;
-                        if (lo > 0) s0 = __ldg(p.coff + tb + lo / kChunkUnit);
-                        if (hi < R) s1 = __ldg(p.coff + tb + hi / kChunkUnit);
+                        if (flags & 1) s0 = __ldg(p.coff + tb + lo / kChunkUnit);
+                        if (flags & 2) s1 = __ldg(p.coff + tb + hi / kChunkUnit);
                     } else {
-                        if (lo > 0) s0 = lower_bound_g(p.adj + b, pl, lb + lo);
-                        if (hi < R) s1 = lower_bound_g(p.adj + b, pl, lb + hi);
+                        if (flags & 1) s0 = lower_bound_g(p.adj + b, pl, lb + lo);
+                        if (flags & 2) s1 = lower_bound_g(p.adj + b, pl, lb + hi);
                     }
                 }
                 len[i] = s1 - s0;
@@ -326,11 +354,12 @@ __device__ unsigned long long cta_walk(const CountParams &p, int32_t x, int32_t 
                 }
 #pragma unroll
                 for (int u = 0; u < kU; ++u)
-                    if (ok[u]) acc += wedge_op<MODE, KIND, kSecond, Pos>(p, w[u], pos[u], q[u], lb, lo, span, hmask, ctr, sh.msum);
+                    if (ok[u]) acc += wedge_op<MODE, KIND, kSecond, Pos>(p, w[u], pos[u], q[u], lb, lo, span, hmask, ctr, sh.msum, &sh.overflow, &sh.inserts);
                 k0 += 32 * kU;
             }
         }
         __syncthreads();
+        if (KIND == kHash && !kSecond && sh.overflow) break;   // uniform: read after the barrier
         if (kSecond) {
 #pragma unroll
             for (int i = 0; i < kPer; ++i) {
@@ -349,9 +378,13 @@ __device__ unsigned long long cta_walk(const CountParams &p, int32_t x, int32_t 
 
 template <int MODE, int KIND, typename Pos, class SH>
 __device__ unsigned long long cta_item_body(const CountParams &p, int32_t x, int32_t lb,
-                                            int32_t lo, int32_t hi, int32_t R, uint32_t hmask,
+                                            int32_t lo, int32_t hi, int flags, uint32_t hmask,
                                             unsigned char *ctr, SH &sh) {
-    unsigned long long acc = cta_walk<MODE, KIND, false, Pos>(p, x, lb, lo, hi, R, hmask, ctr, sh);
+    unsigned long long acc = cta_walk<MODE, KIND, false, Pos>(p, x, lb, lo, hi, flags, hmask, ctr, sh);
+    if (KIND == kHash && p.orient) {
+        __syncthreads();
+        if (sh.overflow) return 0;   // the caller re-queues x
+    }
     if (has_second_walk(MODE)) {
         __syncthreads();
         if (MODE == kModeVertices) {
@@ -374,7 +407,7 @@ __device__ unsigned long long cta_item_body(const CountParams &p, int32_t x, int
                 }
             }
         }
-        cta_walk<MODE, KIND, true, Pos>(p, x, lb, lo, hi, R, hmask, ctr, sh);
+        cta_walk<MODE, KIND, true, Pos>(p, x, lb, lo, hi, flags, hmask, ctr, sh);
         if (MODE == kModeVertices) {
             const unsigned long long t = block_sum(acc, sh);
             if (threadIdx.x == 0 && t) atomicAdd(p.pv + x, t);
@@ -394,29 +427,49 @@ template <int MODE, typename Pos, class SH>
 __device__ unsigned long long cta_item(const CountParams &p, int2 item, unsigned char *ctr,
                                        SH &sh) {
     const int32_t x = item.x;
-    // ends of x are the vertices of x's layer (of x's graph, in a batch) below x
+    // ends lie in x's layer (in a batch: x's graph's part of it) from lb on
     const int32_t lb = p.vbase ? __ldg(p.vbase + x) : (x >= p.l ? p.l : 0);
-    const int32_t R = x - lb;
+    const int32_t R = x - lb;   // Algorithm 2: the ends are the R vertices below x
     unsigned long long acc;
-    if (item.y >= 0) {
+    if (item.y >= 0) {          // dense items exist only for Algorithm 2
         const bool wide = (uint32_t)p.cut[x] > kNarrowMaxCut;
         const int32_t S = wide ? kDense32 : kDense16;
         const int32_t lo = item.y * S;
         const int32_t hi = min(R, lo + S);
         const int32_t span = hi - lo;
+        const int flags = (lo > 0 ? 1 : 0) | (hi < R ? 2 : 0);
         zero_smem(ctr, wide ? span * 4 : ((span + 1) >> 1) * 4, 0u);
         __syncthreads();
-        acc = wide ? cta_item_body<MODE, kDenseWide, Pos>(p, x, lb, lo, hi, R, 0, ctr, sh)
-                   : cta_item_body<MODE, kDenseNarrow, Pos>(p, x, lb, lo, hi, R, 0, ctr, sh);
+        acc = wide ? cta_item_body<MODE, kDenseWide, Pos>(p, x, lb, lo, hi, flags, 0, ctr, sh)
+                   : cta_item_body<MODE, kDenseNarrow, Pos>(p, x, lb, lo, hi, flags, 0, ctr, sh);
     } else {
+        // how many distinct ends x can have: the vertices below it (Algorithm 2)
+        // or above it (Algorithm 3), and at most one per wedge
+        unsigned long long range = (unsigned long long)R;
+        if (p.orient) {
+            const int32_t hiend = p.vend ? __ldg(p.vend + x) : (x >= p.l ? p.n : p.l);
+            range = (unsigned long long)(hiend - x - 1);
+        }
         const unsigned long long w = p.work[x];
-        const unsigned long long bound = w < (unsigned long long)R ? w : (unsigned long long)R;
+        const unsigned long long bound = w < range ? w : range;
         uint32_t cap = 64;
         while (cap < 2 * bound && cap < (uint32_t)kHashMaxSlots) cap <<= 1;
+        // Algorithm 3: counts are bounded by deg(x), which must fit 16 bits here
+        const bool too_wide = p.orient && (p.off[x + 1] - p.off[x]) > (int64_t)kNarrowMaxCut;
+        if (threadIdx.x == 0) { sh.overflow = too_wide ? 1 : 0; sh.inserts = 0; }
         zero_smem(ctr, (int)cap * 4, 0xffffffffu);           // keys = -1
         zero_smem(ctr + (size_t)cap * 4, (int)cap * 2, 0u);  // packed 16-bit counts
         __syncthreads();
-        acc = cta_item_body<MODE, kHash, Pos>(p, x, lb, 0, R, R, cap - 1, ctr, sh);
+        acc = sh.overflow ? 0ull : cta_item_body<MODE, kHash, Pos>(p, x, lb, 0, 0, 0, cap - 1, ctr, sh);
+        if (p.orient && sh.overflow) {
+            // discard this attempt: the retry pass counts x with dense chunks
+            if (threadIdx.x == 0) {
+                const int64_t k = p.retry_static + atomicAdd(p.cursors + 2, 1);
+                if (k < p.retry_cap) p.retry[k] = x; else atomicOr(p.err, kErrBounds);
+            }
+            __syncthreads();
+            return 0;
+        }
     }
     if (MODE == kModeBatch) {
         // the batch is a disjoint union: every butterfly of start x lies in x's graph
@@ -436,7 +489,7 @@ __device__ unsigned long long warp_walk(const CountParams &p, int32_t x, int32_t
                                         int32_t *wstart, long long *wsrc) {
     const int lane = threadIdx.x & 31;
     const int64_t e0 = p.off[x];
-    const int32_t nmid = p.cut[x];
+    const int32_t nmid = p.orient ? (int32_t)(p.off[x + 1] - e0) : p.cut[x];
     const uint32_t le_mask = 0xffffffffu >> (31 - lane);
     const uint32_t lt_mask = (1u << lane) - 1u;
     unsigned long long acc = 0;
@@ -449,7 +502,7 @@ __device__ unsigned long long warp_walk(const CountParams &p, int32_t x, int32_t
             e = e0 + j;
             v = __ldg(p.adj + e);
             len = __ldg(p.plen + e);
-            src = __ldg(p.off + v);
+            src = p.orient ? __ldg(p.sbeg + e) : __ldg(p.off + v);
         }
         int32_t incl = len;
 #pragma unroll
@@ -518,11 +571,15 @@ static_assert(kWarpStartOff + 33 * 4 <= kWarpRegion, "per-warp region overflow")
 template <int MODE>
 __device__ unsigned long long warp_item(const CountParams &p, int32_t x, unsigned char *region) {
     const int lane = threadIdx.x & 31;
-    // ends of x are the vertices of x's layer (of x's graph, in a batch) below x
+    // ends lie in x's layer (in a batch: x's graph's part of it) from lb on
     const int32_t lb = p.vbase ? __ldg(p.vbase + x) : (x >= p.l ? p.l : 0);
-    const int32_t R = x - lb;
+    unsigned long long range = (unsigned long long)(x - lb);
+    if (p.orient) {
+        const int32_t hiend = p.vend ? __ldg(p.vend + x) : (x >= p.l ? p.n : p.l);
+        range = (unsigned long long)(hiend - x - 1);
+    }
     const unsigned long long w = p.work[x];
-    const unsigned long long bound = w < (unsigned long long)R ? w : (unsigned long long)R;
+    const unsigned long long bound = w < range ? w : range;
     uint32_t cap = 32;
     while (cap < 2 * bound && cap < (uint32_t)kWarpSlots) cap <<= 1;
     int32_t *keys = reinterpret_cast<int32_t *>(region);
@@ -590,6 +647,49 @@ __global__ void __launch_bounds__(kCountThreads, 1) k_count(CountParams p) {
     if (threadIdx.x == 0 && t) atomicAdd(p.acc, t);
 }
 
+// Algorithm 3's retry pass: the starts whose hash table filled up (or whose
+// counts could pass 16 bits) are counted with dense counters, one CTA per
+// start, chunk after chunk of the end range (x, end of x's layer).
+template <int MODE, typename Pos>
+__global__ void __launch_bounds__(kCountThreads, 1) k_count_retry(CountParams p) {
+    extern __shared__ __align__(16) unsigned char ctr[];
+    __shared__ SharedCTA<MODE, Pos> sh;
+    unsigned long long acc = 0;
+    const int nretry = (int)min(p.retry_static + *((volatile int *)(p.cursors + 2)), p.retry_cap);
+    for (;;) {
+        if (threadIdx.x == 0) sh.item = atomicAdd(p.cursors + 3, 1);
+        __syncthreads();
+        const int it = sh.item;
+        __syncthreads();
+        if (it >= nretry) break;
+        const int32_t x = p.retry[it];
+        const int32_t lb = p.vbase ? __ldg(p.vbase + x) : (x >= p.l ? p.l : 0);
+        const int32_t hiend = p.vend ? __ldg(p.vend + x) : (x >= p.l ? p.n : p.l);
+        const bool wide = (p.off[x + 1] - p.off[x]) > (int64_t)kNarrowMaxCut;
+        const int32_t S = wide ? kDense32 : kDense16;
+        const int32_t first = x + 1 - lb, last = hiend - lb;   // ends in [lb + first, lb + last)
+        unsigned long long item_acc = 0;
+        for (int32_t c = first / S; c * S < last; ++c) {
+            const int32_t lo = max(c * S, first), hi = min((c + 1) * S, last);
+            const int32_t span = hi - lo;
+            const int flags = (lo > first ? 1 : 0) | (hi < last ? 2 : 0);
+            zero_smem(ctr, wide ? span * 4 : ((span + 1) >> 1) * 4, 0u);
+            __syncthreads();
+            item_acc += wide ? cta_item_body<MODE, kDenseWide, Pos>(p, x, lb, lo, hi, flags, 0, ctr, sh)
+                             : cta_item_body<MODE, kDenseNarrow, Pos>(p, x, lb, lo, hi, flags, 0, ctr, sh);
+            __syncthreads();
+        }
+        if (MODE == kModeBatch) {
+            const unsigned long long t = block_sum(item_acc, sh);
+            if (threadIdx.x == 0 && t) atomicAdd(p.gtot + p.gstar[x], t);
+            __syncthreads();
+        }
+        acc += item_acc;
+    }
+    const unsigned long long t = block_sum(acc, sh);
+    if (threadIdx.x == 0 && t) atomicAdd(p.acc, t);
+}
+
 __global__ void k_gather_vertices(const unsigned long long *__restrict__ pv,
                                   const int32_t *__restrict__ rank_u,
                                   const int32_t *__restrict__ rank_l, int32_t r, int32_t l,
@@ -601,8 +701,11 @@ __global__ void k_gather_vertices(const unsigned long long *__restrict__ pv,
 
 template <int MODE, typename Pos>
 cudaError_t setup_one() {
-    return cudaFuncSetAttribute(k_count<MODE, Pos>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                kCounterBytes);
+    cudaError_t e = cudaFuncSetAttribute(k_count<MODE, Pos>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kCounterBytes);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_count_retry<MODE, Pos>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, kCounterBytes);
 }
 
 }  // namespace
@@ -635,7 +738,10 @@ int launch_count(Graph *g, cudaStream_t s, int mode, unsigned long long *pv_proj
     p.adj_len = 2 * g->m; p.l = g->l; p.err = g->err;
     p.coff = g->coff; p.coff_u1 = g->coff_u1; p.coff_l1 = g->coff_l1;
     p.gstar = g->gstar; p.gtot = gtot; p.vbase = g->vbase;
-    BFC_CUDA(cudaMemsetAsync(g->cursors, 0, 2 * sizeof(int), s));
+    p.vend = g->vend; p.sbeg = g->sbeg; p.retry = g->retry; p.retry_cap = g->retry_cap;
+    p.retry_static = g->retry_static;
+    p.orient = g->opt.orientation; p.n = g->n;
+    BFC_CUDA(cudaMemsetAsync(g->cursors, 0, 4 * sizeof(int), s));
     BFC_CUDA(cudaMemsetAsync(g->acc, 0, sizeof(unsigned long long), s));
     const int grid = g->grid;
     // 32-bit adjacency positions whenever G* has fewer than 2^31 slots
@@ -652,6 +758,22 @@ int launch_count(Graph *g, cudaStream_t s, int mode, unsigned long long *pv_proj
     }
     note_launch();
     BFC_CUDA(cudaGetLastError());
+    if (g->opt.orientation == 1) {
+        // the retry pass reads how many starts the first launch re-queued
+        if (2 * g->m <= 0x7fffffffll && !g->opt.wide_positions) {
+            if (mode == kModeTotal) k_count_retry<kModeTotal, int32_t><<<grid, kCountThreads, kCounterBytes, s>>>(p);
+            else if (mode == kModeBatch) k_count_retry<kModeBatch, int32_t><<<grid, kCountThreads, kCounterBytes, s>>>(p);
+            else if (mode == kModeVertices) k_count_retry<kModeVertices, int32_t><<<grid, kCountThreads, kCounterBytes, s>>>(p);
+            else k_count_retry<kModeEdges, int32_t><<<grid, kCountThreads, kCounterBytes, s>>>(p);
+        } else {
+            if (mode == kModeTotal) k_count_retry<kModeTotal, long long><<<grid, kCountThreads, kCounterBytes, s>>>(p);
+            else if (mode == kModeBatch) k_count_retry<kModeBatch, long long><<<grid, kCountThreads, kCounterBytes, s>>>(p);
+            else if (mode == kModeVertices) k_count_retry<kModeVertices, long long><<<grid, kCountThreads, kCounterBytes, s>>>(p);
+            else k_count_retry<kModeEdges, long long><<<grid, kCountThreads, kCounterBytes, s>>>(p);
+        }
+        note_launch();
+        BFC_CUDA(cudaGetLastError());
+    }
     return BFC_OK;
 }
 

@@ -195,9 +195,32 @@ __global__ void k_plen(const int64_t *__restrict__ off, const int32_t *__restric
     }
 }
 
-// work[x] = Σ plen over x's middle slots; one warp per start.
+// Algorithm 3: for slot e = (x, v) the ends are the w in N(v) with
+// p(w) > p(x) and p(w) > p(v).  N(v) ascends in priority, so they form the
+// suffix that starts after both x (x is in N(v)) and v's cut.
+__global__ void k_slen(const int64_t *__restrict__ off, const int32_t *__restrict__ adj,
+                       const int32_t *__restrict__ rows, const int32_t *__restrict__ cut,
+                       int64_t slots, int32_t *slen, int64_t *sbeg) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < slots;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t x = rows[e];
+        const int32_t v = adj[e];
+        const int64_t b = off[v], d = off[v + 1] - b;
+        int64_t lo = 0, hi = d;
+        while (lo < hi) {
+            int64_t mid = (lo + hi) >> 1;
+            if (adj[b + mid] <= x) lo = mid + 1; else hi = mid;
+        }
+        const int64_t a = lo > cut[v] ? lo : (int64_t)cut[v];
+        slen[e] = (int32_t)(d - a);
+        sbeg[e] = b + a;
+    }
+}
+
+// work[x] = Σ plen over x's middle slots (the first cut[x] slots for
+// Algorithm 2, every slot for Algorithm 3); one warp per start.
 __global__ void k_work(const int64_t *__restrict__ off, const int32_t *__restrict__ cut,
-                       const int32_t *__restrict__ plen, int32_t n, uint64_t *work,
+                       const int32_t *__restrict__ plen, int32_t n, int all_slots, uint64_t *work,
                        unsigned long long *total) {
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -205,9 +228,9 @@ __global__ void k_work(const int64_t *__restrict__ off, const int32_t *__restric
     unsigned long long tot = 0;
     for (int64_t x = warp; x < n; x += nwarps) {
         const int64_t b = off[x];
-        const int32_t c = cut[x];
+        const int64_t c = all_slots ? off[x + 1] - b : (int64_t)cut[x];
         unsigned long long s = 0;
-        for (int32_t j = lane; j < c; j += 32) s += (unsigned)plen[b + j];
+        for (int64_t j = lane; j < c; j += 32) s += (unsigned)plen[b + j];
 #pragma unroll
         for (int d = 16; d > 0; d >>= 1) s += __shfl_xor_sync(0xffffffffu, s, d);
         if (lane == 0) work[x] = s;
@@ -285,6 +308,11 @@ __global__ void k_emit_items(const int32_t *__restrict__ order, int64_t n_dense,
     }
 }
 
+__global__ void k_items_to_starts(const int2 *__restrict__ items, int64_t n, int32_t *starts) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) starts[i] = items[i].x;
+}
+
 // ----- chunk-boundary table for the dense bin ----------------------------------
 __device__ __forceinline__ int64_t coff_base(int32_t v, int32_t l, int32_t u1, int32_t l1) {
     return v < l ? (int64_t)v * u1 : (int64_t)l * u1 + (int64_t)(v - l) * l1;
@@ -357,17 +385,19 @@ __global__ void k_check_batch_edges(const int32_t *__restrict__ rows, const int3
 // holds it; vbase[x] = the first G* id of that graph in x's layer
 __global__ void k_graph_star(int32_t r, int32_t l, const int32_t *__restrict__ gu,
                              const int32_t *__restrict__ gl, int32_t num_graphs, int32_t *gstar,
-                             int32_t *vbase) {
+                             int32_t *vbase, int32_t *vend) {
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < (int64_t)r + l;
          x += (int64_t)gridDim.x * blockDim.x) {
         if (x < l) {
             const int32_t gg = graph_of(gl, num_graphs, (int32_t)x);
             gstar[x] = gg;
             vbase[x] = gl[gg];
+            vend[x] = gl[gg + 1];
         } else {
             const int32_t gg = graph_of(gu, num_graphs, (int32_t)(x - l));
             gstar[x] = gg;
             vbase[x] = l + gu[gg];
+            vend[x] = l + gu[gg + 1];
         }
     }
 }
@@ -410,7 +440,10 @@ static int schedule_graph(Graph *g, cudaStream_t s, int32_t warp_max_work, int32
         }                                                                             \
     } while (0)
     const uint64_t warp_max = (uint64_t)warp_max_work;
-    const uint64_t hash_max = (uint64_t)hash_max_work;
+    // Algorithm 3: ends concentrate on few high-priority vertices, so every
+    // start beyond the warp bin gets a CTA hash table; a start whose table
+    // fills up is counted again by the chunked retry pass
+    const uint64_t hash_max = g->opt.orientation == 1 ? ~0ull : (uint64_t)hash_max_work;
     const uint64_t maxw = g->info.max_start_work;
     int64_t n_dense = 0, n_hash = 0, n_warp = 0, n_items = 0, h_dense_items = 0;
     if (n > 0 && g->info.wedges > 0) {
@@ -483,6 +516,20 @@ static int schedule_graph(Graph *g, cudaStream_t s, int32_t warp_max_work, int32
     }
     g->n_cta_items = n_items;
     g->n_warp_items = n_warp;
+    if (g->opt.orientation == 1) {
+        g->mem.drop(g->retry);
+        g->retry = nullptr;
+        g->retry_static = 0;
+        g->retry_cap = std::max<int64_t>(n_hash, 1);
+        GET(g->mem, g->retry, g->retry_cap);
+        if (hash_max_work == 0 && n_hash > 0) {
+            // every start beyond the warp bin goes to the dense pass directly
+            k_items_to_starts<<<blocks_for(n_hash), kT, 0, s>>>(g->cta_items, n_hash, g->retry); note_launch();
+            BFC_CUDA(cudaGetLastError());
+            g->retry_static = n_hash;
+            g->n_cta_items = 0;
+        }
+    }
     g->info.dense_items = h_dense_items;
     g->info.starts_with_work = n_dense + n_hash + n_warp;
     g->info.dense_starts = n_dense;
@@ -569,6 +616,7 @@ int prepare_graph(const bfc_csr *csr, const bfc_options *opt, cudaStream_t s, Gr
         g->num_graphs = num_graphs;
         GET(g->mem, g->gstar, std::max<int64_t>(n, 1));
         GET(g->mem, g->vbase, std::max<int64_t>(n, 1));
+        GET(g->mem, g->vend, std::max<int64_t>(n, 1));
         GET(g->mem, g->gwork, num_graphs);
         BFC_CUDA(cudaMemsetAsync(g->gwork, 0, sizeof(unsigned long long) * num_graphs, s));
     }
@@ -647,7 +695,7 @@ int prepare_graph(const bfc_csr *csr, const bfc_options *opt, cudaStream_t s, Gr
 
     if (num_graphs > 0 && n > 0) {
         k_graph_star<<<grid_stride_blocks(n), kT, 0, s>>>(r, l, graph_u_start, graph_l_start,
-                                                         num_graphs, g->gstar, g->vbase); note_launch();
+                                                         num_graphs, g->gstar, g->vbase, g->vend); note_launch();
         BFC_CUDA(cudaGetLastError());
     }
 
@@ -706,14 +754,20 @@ int prepare_graph(const bfc_csr *csr, const bfc_options *opt, cudaStream_t s, Gr
         k_cut<<<blocks_for(n), kT, 0, s>>>(g->off, g->adj, deg_star, n, l, g->cut); note_launch();
         BFC_CUDA(cudaGetLastError());
     }
-    if (m > 0) {
+    if (m > 0 && opt->orientation == 0) {
         k_plen<<<grid_stride_blocks(2 * m), kT, 0, s>>>(g->off, g->adj, rows_star, g->cut, 2 * m,
                                                          g->plen); note_launch();
         BFC_CUDA(cudaGetLastError());
     }
+    if (m > 0 && opt->orientation == 1) {
+        GET(g->mem, g->sbeg, 2 * m);
+        k_slen<<<grid_stride_blocks(2 * m), kT, 0, s>>>(g->off, g->adj, rows_star, g->cut, 2 * m,
+                                                         g->plen, g->sbeg); note_launch();
+        BFC_CUDA(cudaGetLastError());
+    }
     if (n > 0) {
         k_work<<<grid_stride_blocks((int64_t)n * 32), kT, 0, s>>>(g->off, g->cut, g->plen, n,
-                                                                   g->work, red); note_launch();
+                                                                   opt->orientation, g->work, red); note_launch();
         BFC_CUDA(cudaGetLastError());
         BFC_CUDA(reduce_max_u64(g->work, n, red + 1, s));
     }

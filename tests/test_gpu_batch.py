@@ -49,7 +49,8 @@ def _count(h, nG):
     return tot.cpu().numpy().view(np.uint64), int(one.item())
 
 
-@pytest.mark.parametrize("opts", [{}, dict(warp_max_work=0, hash_max_work=0), dict(hash_max_work=256)])
+@pytest.mark.parametrize("opts", [{}, dict(warp_max_work=0, hash_max_work=0), dict(hash_max_work=256),
+                                  dict(orientation=1), dict(orientation=1, warp_max_work=0, hash_max_work=0)])
 def test_batch_totals_match_oracle(opts):
     from paper_1812_00283_gb300 import bfc
     graphs = _batch_graphs()

@@ -40,6 +40,12 @@ BIN_SETTINGS = {
     "warp_heavy": dict(warp_max_work=256, hash_max_work=256),
     "wide_positions": dict(wide_positions=1),
     "all_dense_wide_positions": dict(warp_max_work=0, hash_max_work=0, wide_positions=1),
+    # Algorithm 3's orientation: hash tables with the chunked retry pass
+    "vpp": dict(orientation=1),
+    "vpp_retry_all": dict(orientation=1, warp_max_work=0, hash_max_work=0),
+    "vpp_retry_beyond_warp": dict(orientation=1, warp_max_work=256, hash_max_work=0),
+    "vpp_no_warp": dict(orientation=1, warp_max_work=0),
+    "vpp_wide_positions": dict(orientation=1, wide_positions=1),
 }
 
 
@@ -73,13 +79,14 @@ def test_complete_bipartite(a, b):
     assert got["info"]["wedges"] == y * c2(x)
 
 
+@pytest.mark.parametrize("orientation", [0, 1])
 @pytest.mark.parametrize("a", [2, 3])
-def test_wide_counters(a):
-    # one start with more than 65,535 lower-priority middles: count_wedge
-    # reaches 70,000 and must not wrap in 16 bits
+def test_wide_counters(a, orientation):
+    # one start with more than 65,535 middles: count_wedge reaches 70,000 and
+    # must not wrap in 16 bits
     b = 70_000
     g = G.complete_bipartite(a, b)
-    got = run_gpu(g, vertices=True, edges=True)
+    got = run_gpu(g, vertices=True, edges=True, options=_opts(orientation=orientation))
     assert got["total"] == c2(a) * c2(b)
     assert np.all(got["pv_u"] == (a - 1) * c2(b))
     assert np.all(got["pv_l"] == (b - 1) * c2(a))
@@ -154,9 +161,27 @@ def test_multi_chunk_end_ranges(wide):
     assert got["info"]["dense_items"] > got["info"]["dense_starts"]
 
 
-def test_shopping_shape_small():
+@pytest.mark.parametrize("wide", [0, 1])
+def test_multi_chunk_retry_pass(wide):
+    # Algorithm 3 with every start sent to the chunked dense pass: low starts
+    # of the 230k-vertex U layer span several chunks above them
+    g = G.chung_lu_bipartite(230_000, 20_000, 900_000, 2.1, 2.1, 43)
+    _check_against_oracle(g, _opts(orientation=1, warp_max_work=0, hash_max_work=0,
+                                   wide_positions=wide))
+
+
+def test_orientations_agree_on_wedges_and_work():
+    # Lemma 4: both orientations process the same number of wedges
+    g = G.chung_lu_bipartite(20000, 8000, 150000, 2.1, 2.0, 47)
+    a = run_gpu(g, options=_opts(orientation=0))
+    b = run_gpu(g, options=_opts(orientation=1))
+    assert a["total"] == b["total"] and a["info"]["wedges"] == b["info"]["wedges"]
+
+
+@pytest.mark.parametrize("orientation", [0, 1])
+def test_shopping_shape_small(orientation):
     g = G.shopping_300m(scale=0.01)   # 100k users, 1k items, 3M edges
-    _check_against_oracle(g)
+    _check_against_oracle(g, _opts(orientation=orientation))
 
 
 def test_list_order_and_relabel_invariance():
