@@ -257,6 +257,23 @@ def paper_fig3() -> BipartiteCSR:
     return from_edges(1002, 1002, us, vs, "paper_fig3")
 
 
+def shifted_sidon_circulant(p: int, c: int, n: int) -> BipartiteCSR:
+    """A regular circulant: U vertex u is joined to L vertex (u + s) mod n for
+    every distinct shift s mod n in T and in T + c, where T = {2pk + (k^2 mod
+    p)} (p prime) is the Erdős-Turán Sidon set (its differences are pairwise
+    distinct).
+    Every vertex has degree 2p, so priorities tie on degree and every U vertex
+    lies above every L vertex.  The two-hop neighbourhood of a U vertex has
+    about 3p^2 distinct vertices, most reached once and the differences of T
+    twice: a start near either end of the U order has that many distinct
+    ends (hash-table stress), with butterflies from the doubled differences."""
+    t = np.array([2 * p * k + (k * k) % p for k in range(p)], dtype=np.int64)
+    shifts = np.unique(np.concatenate([t, t + c]) % n)
+    u = np.repeat(np.arange(n, dtype=np.int64), shifts.size)
+    v = (u + np.tile(shifts, n)) % n
+    return from_edges(n, n, u, v, f"sidon_{p}_{c}_{n}")
+
+
 def random_tiny(num_u: int, num_l: int, p_num: int, p_den: int, seed: int) -> BipartiteCSR:
     """Each of the r*l pairs is an edge with probability p_num/p_den."""
     k = np.arange(num_u * num_l, dtype=np.uint64)

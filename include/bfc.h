@@ -76,14 +76,16 @@ typedef struct bfc_options {
     int32_t validate;       /* 1 (default): reject duplicate edges.  Offsets and
                                id ranges are always checked. */
     int32_t warp_max_work;  /* starts with at most this many wedges are counted
-                               by one warp with a shared-memory hash table
-                               (default 256, range [0, 256]) */
-    int32_t hash_max_work;  /* starts with at most this many wedges (and more
-                               than warp_max_work) are counted by one CTA with
-                               a shared-memory hash table (default 16384,
-                               range [warp_max_work, 16384]); heavier starts
-                               get dense shared-memory counters over chunks of
-                               their end range */
+                               by one warp with a 512-slot shared-memory hash
+                               table (default 256, range [0, 256]) */
+    int32_t hash_max_work;  /* Algorithm 2: starts with at most this many
+                               wedges (and more than team_max_work) are counted
+                               by one CTA with a shared-memory hash table of up
+                               to 32,768 slots (default 16384, range
+                               [warp_max_work, 16384]); heavier starts get dense
+                               shared-memory counters over chunks of their end
+                               range.  Algorithm 3: ignored, except that 0 sends
+                               every start beyond the warp bin to the dense pass */
     int32_t num_ctas;       /* persistent grid size; 0 (default) = one CTA per SM */
     int32_t wide_positions; /* 1: count with 64-bit adjacency positions even when
                                32 bits suffice (they are used automatically when
@@ -93,11 +95,20 @@ typedef struct bfc_options {
                                p(v) < p(u), p(w) < p(u);
                                1 = Algorithm 3 (BFC-VP++): end w highest,
                                p(w) > p(u), p(w) > p(v).  With 1, every start
-                               beyond the warp bin gets a CTA hash table and a
-                               start whose table fills up is counted again by a
-                               chunked dense pass; hash_max_work is then ignored
-                               except that 0 sends all of them to that pass. */
-    int32_t reserved[10];   /* must be zero */
+                               beyond the warp bin gets a team or CTA hash table
+                               and a start whose table fills up is counted again
+                               by a retry pass (a CTA table, then dense chunks). */
+    int32_t team_max_work;  /* starts with more than warp_max_work and at most
+                               this many wedges are counted by a 256-thread team
+                               (four per CTA) with a 4,096-slot hash table.
+                               -1 (default) = 2048 for Algorithm 2 (its tables
+                               then always fit) and 16384 for Algorithm 3;
+                               otherwise in [0, 16384], and a value <=
+                               warp_max_work leaves the team bin empty.
+                               Algorithm 2 caps it at hash_max_work; above 2048
+                               a start whose team table fills up goes to the
+                               retry pass. */
+    int32_t reserved[9];    /* must be zero */
 } bfc_options;
 
 /* Figures of a prepared graph (host values). */
@@ -108,11 +119,13 @@ typedef struct bfc_info {
     uint64_t max_start_work;  /* largest per-start wedge count */
     int64_t starts_with_work; /* starts u with at least one wedge */
     int64_t warp_starts;      /* starts in the warp/hash bin */
-    int64_t hash_starts;      /* starts in the CTA/hash bin */
+    int64_t hash_starts;      /* starts in the CTA/hash bin (Algorithm 3 with
+                                 hash_max_work 0: starts sent to the dense pass) */
     int64_t dense_starts;     /* starts in the CTA/dense bin */
     int64_t dense_items;      /* (start, end-range chunk) work items of the dense bin */
     int64_t device_bytes;     /* library-owned device memory held by the graph */
     int32_t max_deg_u, max_deg_l;
+    int64_t team_starts;      /* starts in the team/hash bin */
 } bfc_info;
 
 /* What bfc_export() can copy out (for parity tests; layouts as stated). */
@@ -124,7 +137,9 @@ typedef enum bfc_array {
     BFC_PROJ_ADJ = 3, /* int32[2m]: neighbour ids in G*, each list ascending */
     BFC_PROJ_EID = 4, /* int32[2m]: edge id (U-side slot) of each entry */
     BFC_CUT = 5,      /* int32[n]: |{y in N(x) : p(y) < p(x)}| per vertex of G* */
-    BFC_WORK = 6      /* uint64[n]: wedges Algorithm 2 processes from each start x of G* */
+    BFC_WORK = 6,     /* uint64[n]: wedges Algorithm 2 processes from each start x of G* */
+    BFC_RETRIES = 7   /* int32[1]: starts whose hash table filled up in the last
+                         count's first launch and went to the retry pass */
 } bfc_array;
 
 void bfc_options_init(bfc_options *opt);
@@ -182,10 +197,12 @@ int bfc_count_batch(bfc_graph *g, void *stream, uint64_t *totals_dev, uint64_t *
 int bfc_batch_wedges(const bfc_graph *g, void *stream, uint64_t *wedges_dev);
 
 /* Autotuner for the bin thresholds of step a5: re-bins the prepared graph for
- * each candidate (warp_max_work in {32, 128, 256} x hash_max_work in {1024,
- * 4096, 16384}), times `iters` count launches of each with CUDA events on
- * `stream`, keeps the fastest and writes it to *chosen (nullable).
- * Synchronises `stream`; allocates only the schedule arrays. */
+ * each candidate (Algorithm 2: warp_max_work in {32, 128, 256} x
+ * team_max_work in {512, 2048} x hash_max_work in {4096, 16384}; Algorithm 3:
+ * warp_max_work in {32, 128, 256} x team_max_work in {2048, 16384}), times
+ * `iters` count launches of each with CUDA events on `stream`, keeps the
+ * fastest and writes it to *chosen (nullable).  Synchronises `stream`;
+ * allocates only the schedule arrays. */
 int bfc_autotune(bfc_graph *g, void *stream, int iters, bfc_options *chosen);
 
 /* ---- Serving: continuous batching of counting requests -------------------
@@ -206,7 +223,8 @@ typedef struct bfc_server_config {
     int64_t max_batch_edges;     /* edges per batch at most, unless one request alone is larger (default 2^26) */
     int32_t warp_max_work;       /* bin thresholds passed to every batch (0 = library default) */
     int32_t hash_max_work;
-    int32_t reserved[8];
+    int32_t team_max_work;
+    int32_t reserved[7];
 } bfc_server_config;
 
 typedef struct bfc_server_stats {

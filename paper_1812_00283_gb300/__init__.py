@@ -106,7 +106,7 @@ class ButterflyGraph:
         spec = {bfc.BFC_RANK_U: (self.num_u, torch.int32), bfc.BFC_RANK_L: (self.num_l, torch.int32),
                 bfc.BFC_PROJ_OFF: (n + 1, torch.int64), bfc.BFC_PROJ_ADJ: (2 * m, torch.int32),
                 bfc.BFC_PROJ_EID: (2 * m, torch.int32), bfc.BFC_CUT: (n, torch.int32),
-                bfc.BFC_WORK: (n, torch.int64)}[which]
+                bfc.BFC_WORK: (n, torch.int64), bfc.BFC_RETRIES: (1, torch.int32)}[which]
         t = torch.empty(max(spec[0], 1), dtype=spec[1], device=self.device)
         sp, _ = _stream(stream)
         bfc.bfc_export(self._h, which, t.data_ptr(), sp)

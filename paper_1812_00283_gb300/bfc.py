@@ -23,7 +23,7 @@ BFC_OK = 0
 STATUS = {0: "BFC_OK", 1: "BFC_ERR_INVALID_ARGUMENT", 2: "BFC_ERR_INVALID_GRAPH",
           3: "BFC_ERR_OUT_OF_MEMORY", 4: "BFC_ERR_CUDA", 5: "BFC_ERR_TIMEOUT",
           6: "BFC_ERR_INTERNAL"}
-BFC_RANK_U, BFC_RANK_L, BFC_PROJ_OFF, BFC_PROJ_ADJ, BFC_PROJ_EID, BFC_CUT, BFC_WORK = range(7)
+BFC_RANK_U, BFC_RANK_L, BFC_PROJ_OFF, BFC_PROJ_ADJ, BFC_PROJ_EID, BFC_CUT, BFC_WORK, BFC_RETRIES = range(8)
 
 
 class bfc_csr(ctypes.Structure):
@@ -34,7 +34,7 @@ class bfc_csr(ctypes.Structure):
 class bfc_options(ctypes.Structure):
     _fields_ = [("validate", c_int32), ("warp_max_work", c_int32), ("hash_max_work", c_int32),
                 ("num_ctas", c_int32), ("wide_positions", c_int32), ("orientation", c_int32),
-                ("reserved", c_int32 * 10)]
+                ("team_max_work", c_int32), ("reserved", c_int32 * 9)]
 
 
 class bfc_info(ctypes.Structure):
@@ -42,7 +42,7 @@ class bfc_info(ctypes.Structure):
                 ("wedges", c_uint64), ("max_start_work", c_uint64),
                 ("starts_with_work", c_int64), ("warp_starts", c_int64), ("hash_starts", c_int64),
                 ("dense_starts", c_int64), ("dense_items", c_int64), ("device_bytes", c_int64),
-                ("max_deg_u", c_int32), ("max_deg_l", c_int32)]
+                ("max_deg_u", c_int32), ("max_deg_l", c_int32), ("team_starts", c_int64)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -55,7 +55,7 @@ class bfc_batch(ctypes.Structure):
 class bfc_server_config(ctypes.Structure):
     _fields_ = [("memory_budget_bytes", c_int64), ("workers", c_int32), ("max_batch_graphs", c_int32),
                 ("max_batch_edges", c_int64), ("warp_max_work", c_int32), ("hash_max_work", c_int32),
-                ("reserved", c_int32 * 8)]
+                ("team_max_work", c_int32), ("reserved", c_int32 * 7)]
 
 
 class bfc_server_stats(ctypes.Structure):

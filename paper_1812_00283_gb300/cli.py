@@ -39,6 +39,7 @@ def main(argv=None):
     ap.add_argument("--mode", default="total", choices=["total", "vertices", "edges"])
     ap.add_argument("--warp-max-work", type=int, default=None)
     ap.add_argument("--hash-max-work", type=int, default=None)
+    ap.add_argument("--team-max-work", type=int, default=None)
     ap.add_argument("--orientation", type=int, default=0, choices=[0, 1])
     args = ap.parse_args(argv)
 
@@ -55,6 +56,8 @@ def main(argv=None):
         opts.warp_max_work = args.warp_max_work
     if args.hash_max_work is not None:
         opts.hash_max_work = args.hash_max_work
+    if args.team_max_work is not None:
+        opts.team_max_work = args.team_max_work
     opts.orientation = args.orientation
     s = torch.cuda.current_stream()
     sp = s.cuda_stream

@@ -84,6 +84,10 @@ static int check_options(const bfc_options *o) {
         bfc::set_last_error("hash_max_work must lie in [warp_max_work, 16384]");
         return BFC_ERR_INVALID_ARGUMENT;
     }
+    if (o->team_max_work < -1 || o->team_max_work > bfc::kTeamMaxWork) {
+        bfc::set_last_error("team_max_work must be -1 (default) or lie in [0, 16384]");
+        return BFC_ERR_INVALID_ARGUMENT;
+    }
     if (o->num_ctas < 0) {
         bfc::set_last_error("num_ctas must be >= 0");
         return BFC_ERR_INVALID_ARGUMENT;
@@ -96,7 +100,7 @@ static int check_options(const bfc_options *o) {
         bfc::set_last_error("orientation must be 0 (Algorithm 2) or 1 (Algorithm 3)");
         return BFC_ERR_INVALID_ARGUMENT;
     }
-    for (int i = 0; i < 10; ++i)
+    for (int i = 0; i < 9; ++i)
         if (o->reserved[i] != 0) {
             bfc::set_last_error("reserved option fields must be zero");
             return BFC_ERR_INVALID_ARGUMENT;
@@ -112,6 +116,7 @@ void bfc_options_init(bfc_options *opt) {
     opt->validate = 1;
     opt->warp_max_work = bfc::kWarpMaxWork;
     opt->hash_max_work = bfc::kHashMaxWork;
+    opt->team_max_work = -1;
     opt->num_ctas = 0;
 }
 
@@ -261,37 +266,44 @@ int bfc_autotune(bfc_graph *h, void *stream, int iters, bfc_options *chosen) {
     Graph *g = &h->g;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     g->stream = s;
-    static const int32_t warp_c[] = {32, 128, 256};
-    static const int32_t hash_c[] = {1024, 4096, 16384};
+    // candidate (warp, team, hash) bounds; Algorithm 3 ignores the hash bound
+    struct Cand { int32_t w, t, h; };
+    Cand cands[12];
+    int nc = 0;
+    for (int32_t wmax : {32, 128, 256}) {
+        if (g->opt.orientation == 1) {
+            for (int32_t tmax : {2048, 16384}) cands[nc++] = {wmax, tmax, bfc::kHashMaxWork};
+        } else {
+            for (int32_t tmax : {512, 2048})
+                for (int32_t hmax : {4096, 16384}) cands[nc++] = {wmax, tmax, hmax};
+        }
+    }
     cudaEvent_t e0, e1;
     BFC_CUDA(cudaEventCreate(&e0));
     BFC_CUDA(cudaEventCreate(&e1));
     float best = 1e30f;
-    int32_t bw = g->opt.warp_max_work, bh = g->opt.hash_max_work;
+    int32_t bw = g->opt.warp_max_work, bt = g->opt.team_max_work, bh = g->opt.hash_max_work;
     int rc = BFC_OK;
-    for (int32_t wmax : warp_c) {
-        for (int32_t hmax : hash_c) {
-            rc = bfc::rebin_graph(g, s, wmax, hmax);
-            if (rc) break;
-            rc = bfc::launch_count(g, s, bfc::kModeTotal, nullptr, nullptr);   // warm-up
-            if (rc) break;
-            cudaEventRecord(e0, s);
-            for (int i = 0; i < iters && rc == BFC_OK; ++i)
-                rc = bfc::launch_count(g, s, bfc::kModeTotal, nullptr, nullptr);
-            cudaEventRecord(e1, s);
-            if (rc) break;
-            cudaError_t e = cudaEventSynchronize(e1);
-            if (e != cudaSuccess) { rc = bfc::cuda_fail(e, "cudaEventSynchronize"); break; }
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            if (ms < best) { best = ms; bw = wmax; bh = hmax; }
-        }
+    for (int c = 0; c < nc; ++c) {
+        rc = bfc::rebin_graph(g, s, cands[c].w, cands[c].t, cands[c].h);
         if (rc) break;
+        rc = bfc::launch_count(g, s, bfc::kModeTotal, nullptr, nullptr);   // warm-up
+        if (rc) break;
+        cudaEventRecord(e0, s);
+        for (int i = 0; i < iters && rc == BFC_OK; ++i)
+            rc = bfc::launch_count(g, s, bfc::kModeTotal, nullptr, nullptr);
+        cudaEventRecord(e1, s);
+        if (rc) break;
+        cudaError_t e = cudaEventSynchronize(e1);
+        if (e != cudaSuccess) { rc = bfc::cuda_fail(e, "cudaEventSynchronize"); break; }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) { best = ms; bw = cands[c].w; bt = cands[c].t; bh = cands[c].h; }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc) return rc;
-    rc = bfc::rebin_graph(g, s, bw, bh);
+    rc = bfc::rebin_graph(g, s, bw, bt, bh);
     if (rc) return rc;
     if (chosen) *chosen = g->opt;
     return BFC_OK;
@@ -354,6 +366,7 @@ int bfc_export(const bfc_graph *h, int which, void *dst, void *stream) {
         case BFC_PROJ_EID: src = g->eid; bytes = 4 * (size_t)(2 * g->m); break;
         case BFC_CUT: src = g->cut; bytes = 4 * (size_t)g->n; break;
         case BFC_WORK: src = g->work; bytes = 8 * (size_t)g->n; break;
+        case BFC_RETRIES: src = g->cursors + 2; bytes = 4; break;
         default: bfc::set_last_error("unknown array"); return BFC_ERR_INVALID_ARGUMENT;
     }
     if (bytes) BFC_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, s));

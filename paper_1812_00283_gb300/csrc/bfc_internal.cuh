@@ -32,6 +32,12 @@ constexpr int kHashMaxWork = kHashMaxSlots / 2;           // 16,384 wedges
 constexpr int kWarpRegion = kCounterBytes / kCountWarps;  // 6 KB of counters per warp
 constexpr int kWarpSlots = 512;                           // warp hash: 2 KB keys + 2 KB counts
 constexpr int kWarpMaxWork = kWarpSlots / 2;              // 256 wedges
+constexpr int kTeamThreads = 256;                         // a team: 8 warps with a named barrier
+constexpr int kTeams = kCountThreads / kTeamThreads;      // 4 teams per CTA
+constexpr int kTeamRegion = kCounterBytes / kTeams;       // 48 KB of shared memory per team
+constexpr int kTeamSlots = 4096;                          // team hash: 16 KB keys + 8 KB counts
+constexpr int kTeamFitWork = kTeamSlots / 2;              // a start this light always fits a team table
+constexpr int kTeamMaxWork = kHashMaxWork;                // upper limit of team_max_work
 constexpr uint32_t kNarrowMaxCut = 65535;                 // counts fit 16 bits when cut <= this
 constexpr int kChunkUnit = kDense32;                      // end-range chunk unit of the boundary table
 static_assert(kDense16 % kChunkUnit == 0, "narrow chunks must be whole table units");
@@ -129,9 +135,12 @@ struct Graph {
     int32_t *cut = nullptr;   // [n]
     uint64_t *work = nullptr; // [n]
     int2 *cta_items = nullptr;    // (start, chunk) / (start, -1 = hash)
+    int32_t *team_items = nullptr;
     int32_t *warp_items = nullptr;
-    int64_t n_cta_items = 0, n_warp_items = 0;
-    int *cursors = nullptr;        // [2] work-queue cursors of the count kernel
+    int64_t n_cta_items = 0, n_team_items = 0, n_warp_items = 0;
+    int32_t team_max = 0;          // effective team bound of the current schedule
+    bool may_retry = false;        // the schedule can re-queue starts (retry pass launched)
+    int *cursors = nullptr;        // [8] work-queue cursors of the count kernels
     unsigned long long *acc = nullptr;  // [1] device accumulator for ⋈_G
     unsigned long long *pv = nullptr;   // [n] per-vertex scratch in G* ids (allocated on demand? no: in prepare)
     int *err = nullptr;            // device error word
@@ -148,7 +157,9 @@ struct Graph {
     // Algorithm 3 orientation: per slot e = (x, v), the run of N(v) holding
     // the ends above both x and v starts at sbeg[e] and has plen[e] entries
     int64_t *sbeg = nullptr;
-    int32_t *retry = nullptr;             // starts counted by the chunked retry pass
+    // starts re-queued for the retry pass: x (its team table filled up: try a
+    // CTA table) or -(x+1) (count with dense chunks)
+    int32_t *retry = nullptr;
     int64_t retry_static = 0;             // of which assigned there by prepare
     int64_t retry_cap = 0;
     unsigned long long *gwork = nullptr;  // [num_graphs] wedges per graph
@@ -192,7 +203,8 @@ enum CountMode { kModeTotal = 0, kModeVertices = 1, kModeEdges = 2, kModeBatch =
 __host__ __device__ constexpr bool has_second_walk(int mode) { return mode == kModeVertices || mode == kModeEdges; }
 int launch_count(Graph *g, cudaStream_t s, int mode, unsigned long long *pv_proj,
                  unsigned long long *pe, unsigned long long *gtot = nullptr);
-int rebin_graph(Graph *g, cudaStream_t s, int32_t warp_max_work, int32_t hash_max_work);
+int rebin_graph(Graph *g, cudaStream_t s, int32_t warp_max_work, int32_t team_max_work,
+                int32_t hash_max_work);
 int count_smem_setup(int device);
 
 // small helpers

@@ -1,24 +1,33 @@
-// Steps a6-a9: wedge enumeration with per-start aggregation (Algorithm 2),
-// the reduction to ⋈_G, and the per-vertex / per-edge second walk
-// (Algorithm 4 in the orientation of Algorithm 2).
+// Steps a6-a9: wedge enumeration with per-start aggregation, the reduction
+// to ⋈_G, and the per-vertex / per-edge second walk (Algorithm 4).
 //
-// One persistent launch, one CTA of 1024 threads per SM.  Each CTA first
-// takes CTA work items from a global queue (heaviest first, Section 6.2's
-// dynamic scheduling with the exact per-start workload), then its 32 warps
-// take single light starts from a second queue.
+// Two orientations of the same wedge set (Lemma 4):
+//   Algorithm 2 (orient 0): start u highest; the middles v with p(v) < p(u)
+//     are the first cut[u] entries of N(u); the ends w with p(w) < p(u) are
+//     the prefix of N(v) below u.
+//   Algorithm 3 (orient 1): end w highest; every neighbour v of the start u
+//     is a middle; the ends are the suffix of N(v) above both u and v.
+// Either way count_wedge(w) for the pair (u, w) is aggregated in one place and
+// Lemma 1 gives C(count, 2) butterflies.  Adding old = count_wedge(w) before
+// each increment gives Σ_w C(count_wedge(w), 2) exactly.
 //
-//   dense item (x, c): the wedges of start x whose end lies in the c-th
-//       chunk of x's end range [0, rank(x)); count_wedge is a dense array in
-//       shared memory (16-bit counts when cut[x] <= 65535, else 32-bit).
-//       Chunks split the END range, so every pair (x, w) is aggregated by
-//       exactly one item and C(count, 2) is never split.
-//   hash item (x): a start with at most 16,384 wedges; count_wedge is an
-//       open-addressing hash table in shared memory.
-//   warp item (x): a start with at most 256 wedges, one warp, a per-warp
-//       hash table.
-//
-// Aggregation uses the running form of Lemma 1: adding old = count_wedge(w)
-// before each increment gives Σ_w C(count_wedge(w), 2) exactly.
+// One persistent launch, one CTA of 1024 threads per SM, 192 KB of dynamic
+// shared memory.  Three phases, each fed by its own queue, heaviest first
+// (Section 6.2's dynamic scheduling with the exact per-start work):
+//   A. CTA items, the whole CTA on one item:
+//      dense (u, c)  count_wedge is a dense array over the c-th chunk of u's
+//                    end range (16-bit counts when at most 65,535 middles,
+//                    else 32-bit).  Chunks split the END range, so every pair
+//                    is aggregated by exactly one item and C(count, 2) is
+//                    never split;
+//      hash (u)      an open-addressing table of up to 32,768 slots.
+//   B. team items: four teams of 256 threads, each with a 48 KB region (a
+//      4,096-slot table and its batch arrays), one start per team.
+//   C. warp items: 32 warps, each with a 512-slot table, one light start each.
+// A table sized from a bound that can be exceeded (Algorithm 3's ends, or a
+// team bound above 2,048 wedges) detects when it fills up; the start is then
+// re-queued and counted by k_count_retry, first with a CTA table, then if
+// needed with dense chunks of its end range.
 #include "bfc_internal.cuh"
 
 #ifndef BFC_CHECKED
@@ -29,6 +38,10 @@ namespace bfc {
 
 namespace {
 
+constexpr int kTeamTableBytes = kTeamSlots * 6;   // 32-bit keys + 16-bit counts
+static_assert(kTeamRegion == (kCountWarps / kTeams) * kWarpRegion,
+              "a team's region is exactly the regions of its warps");
+
 struct CountParams {
     const int64_t *__restrict__ off;
     const int32_t *__restrict__ adj;
@@ -37,49 +50,63 @@ struct CountParams {
     const int32_t *__restrict__ cut;
     const uint64_t *__restrict__ work;
     const int2 *__restrict__ cta_items;
+    const int32_t *__restrict__ team_items;
     const int32_t *__restrict__ warp_items;
     int64_t n_cta;
+    int64_t n_team;
     int64_t n_warp;
-    int *cursors;
+    int *cursors;                      // [0] CTA, [1] warp, [2] retry pushes, [3] retry, [4] team
     unsigned long long *acc;
-    unsigned long long *pv;   // [n] in G* ids
-    unsigned long long *pe;   // [m] by edge id
-    const int32_t *__restrict__ coff;  // chunk-boundary table (nullable)
+    unsigned long long *pv;            // [n] in G* ids
+    unsigned long long *pe;            // [m] by edge id
+    const int32_t *__restrict__ coff;  // chunk-boundary table (nullable; Algorithm 2 only)
     const int32_t *__restrict__ gstar; // graph of each G* vertex (batch mode)
     const int32_t *__restrict__ vbase; // first id of x's graph in x's layer (batch mode)
     const int32_t *__restrict__ vend;  // one past the last id of x's graph in x's layer (batch mode)
     const int64_t *__restrict__ sbeg;  // Algorithm 3: start of each slot's run of ends
-    int32_t *retry;                    // Algorithm 3: starts left to the chunked retry pass
+    unsigned long long *gtot;          // per-graph totals (batch mode)
+    int32_t *retry;                    // re-queued starts: x (CTA table next) or -(x+1) (dense)
     int64_t retry_cap;
     int64_t retry_static;              // retry[0, retry_static) were assigned by prepare
+    int32_t retry_on;                  // the retry pass runs after this launch
+    int32_t coff_u1, coff_l1;          // entries per L vertex / per U vertex
     int32_t orient;                    // 0 = Algorithm 2, 1 = Algorithm 3
     int32_t n;
-    unsigned long long *gtot;          // per-graph totals (batch mode)
-    int32_t coff_u1, coff_l1;          // entries per L vertex / per U vertex
     int64_t adj_len;
     int32_t l;
     int *err;
 };
 
-// Middles per batch: two per thread when adjacency positions fit 32 bits,
-// one otherwise (shared memory holds the compacted batch).
-template <typename Pos>
-struct Batch {
-    static constexpr int kSize = sizeof(Pos) == 4 ? 2 * kCountThreads : kCountThreads;
-    static constexpr int kPer = kSize / kCountThreads;
+// The threads that walk one start together: the whole CTA (barrier 0) or one
+// of its four 256-thread teams (hardware barriers 1..4).
+template <int kThreads>
+struct Team {
+    int tid;
+    int bar;
+    __device__ __forceinline__ void sync() const {
+        if (kThreads == kCountThreads) __syncthreads();
+        else asm volatile("bar.sync %0, %1;" ::"r"(bar), "n"(kThreads) : "memory");
+    }
 };
 
-template <int MODE, typename Pos>
-struct SharedCTA {
-    static constexpr int kB = Batch<Pos>::kSize;
+// Middles per batch: two per thread when adjacency positions fit 32 bits.
+template <typename Pos, int kThreads>
+struct Batch {
+    static constexpr int kPer = sizeof(Pos) == 4 ? 2 : 1;
+    static constexpr int kSize = kPer * kThreads;
+};
+
+template <int MODE, typename Pos, int kThreads>
+struct SharedTeam {
+    static constexpr int kB = Batch<Pos, kThreads>::kSize;
     int32_t start[kB + 1];              // compacted batch: exclusive prefix of run lengths (+ sentinel)
     Pos src[kB];                        // compacted batch: adjacency position of a run minus its prefix
     unsigned long long msum[has_second_walk(MODE) ? kB : 1];  // second walk: Σ δ per compacted middle
-    long long wtot[32];
-    unsigned long long red[32];
+    long long wtot[kThreads / 32];
+    unsigned long long red[kThreads / 32];
     int item;
-    int overflow;   // Algorithm 3: this item's hash table filled up
-    int inserts;    // Algorithm 3: distinct ends inserted so far
+    int overflow;   // this item's table filled up
+    int inserts;    // distinct ends inserted so far
 };
 
 __device__ __forceinline__ unsigned long long c2(unsigned long long c) {
@@ -95,10 +122,12 @@ __device__ __forceinline__ int lower_bound_g(const int32_t *a, int len, int32_t 
     return lo;
 }
 
-// Exclusive block scan of one int64 per thread (1024 threads).
-template <class SH>
-__device__ __forceinline__ long long block_excl_scan(long long v, SH &sh, long long *total) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+// Exclusive scan of one int64 per thread across the team.
+template <int kThreads, class SH>
+__device__ __forceinline__ long long team_excl_scan(long long v, SH &sh, const Team<kThreads> &t,
+                                                    long long *total) {
+    constexpr int kWarps = kThreads / 32;
+    const int lane = t.tid & 31, warp = t.tid >> 5;
     long long x = v;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
@@ -106,37 +135,49 @@ __device__ __forceinline__ long long block_excl_scan(long long v, SH &sh, long l
         if (lane >= d) x += o;
     }
     if (lane == 31) sh.wtot[warp] = x;
-    __syncthreads();
+    t.sync();
     if (warp == 0) {
-        long long w = sh.wtot[lane];
+        long long w = lane < kWarps ? sh.wtot[lane] : 0;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
             long long o = __shfl_up_sync(0xffffffffu, w, d);
             if (lane >= d) w += o;
         }
-        sh.wtot[lane] = w;
+        if (lane < kWarps) sh.wtot[lane] = w;
     }
-    __syncthreads();
+    t.sync();
     long long before = warp > 0 ? sh.wtot[warp - 1] : 0;
-    *total = sh.wtot[31];
+    *total = sh.wtot[kWarps - 1];
     return before + x - v;
 }
 
-template <class SH>
-__device__ __forceinline__ unsigned long long block_sum(unsigned long long v, SH &sh) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+// Sum over the team; the result is valid in the team's first warp.
+template <int kThreads, class SH>
+__device__ __forceinline__ unsigned long long team_sum(unsigned long long v, SH &sh,
+                                                       const Team<kThreads> &t) {
+    constexpr int kWarps = kThreads / 32;
+    const int lane = t.tid & 31, warp = t.tid >> 5;
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
-    __syncthreads();
+    t.sync();
     if (lane == 0) sh.red[warp] = v;
-    __syncthreads();
-    unsigned long long t = 0;
+    t.sync();
+    unsigned long long r = 0;
     if (warp == 0) {
-        t = sh.red[lane];
+        r = lane < kWarps ? sh.red[lane] : 0;
 #pragma unroll
-        for (int d = 16; d > 0; d >>= 1) t += __shfl_xor_sync(0xffffffffu, t, d);
+        for (int d = 16; d > 0; d >>= 1) r += __shfl_xor_sync(0xffffffffu, r, d);
     }
-    return t;   // valid in warp 0
+    return r;
+}
+
+template <int kThreads>
+__device__ __forceinline__ void team_fill(unsigned char *p, int bytes, uint32_t fill,
+                                          const Team<kThreads> &t) {
+    uint4 *q = reinterpret_cast<uint4 *>(p);
+    const int n16 = (bytes + 15) >> 4;
+    const uint4 f = make_uint4(fill, fill, fill, fill);
+    for (int i = t.tid; i < n16; i += kThreads) q[i] = f;
 }
 
 // largest j in [0, n) with a[j] <= k, given a[0] <= k and a ascending
@@ -154,7 +195,7 @@ __device__ __forceinline__ uint32_t hash_slot(int32_t key, uint32_t mask) {
 }
 
 // Finds (inserting if absent) the slot of `key`.  Returns -1 if the table is
-// full, which the slot sizing rules out.
+// full.  *inserted is set when this call claimed an empty slot.
 __device__ __forceinline__ int hash_find(int32_t *keys, uint32_t mask, int32_t key, bool insert,
                                          int *inserted = nullptr) {
     uint32_t h = hash_slot(key, mask);
@@ -188,15 +229,14 @@ __device__ __forceinline__ uint32_t get16(const uint32_t *w32, int idx) {
 
 enum CounterKind { kDenseNarrow = 0, kDenseWide = 1, kHash = 2 };
 
-// The counter operation for one wedge (x, middle, w) whose end id is w and
-// whose end sits at adjacency slot pos.  First walk: increment count_wedge(w)
-// and return the old value.  Second walk: read the final count and attribute
-// δ = count − 1 to the edge (middle, w) and to the middle's batch sum.
+// The counter operation for one wedge whose end id is w and whose end sits at
+// adjacency slot pos.  First walk: increment count_wedge(w), return the old
+// value.  Second walk: read the final count and attribute δ = count − 1 to the
+// edge (middle, w) and to the middle's batch sum.
 template <int MODE, int KIND, bool kSecond, typename Pos>
-__device__ __forceinline__ unsigned long long wedge_op(const CountParams &p, int32_t w,
-                                                       Pos pos, int q, int32_t lb, int32_t lo,
-                                                       int32_t span, uint32_t hmask,
-                                                       unsigned char *ctr,
+__device__ __forceinline__ unsigned long long wedge_op(const CountParams &p, int32_t w, Pos pos,
+                                                       int q, int32_t lb, int32_t lo, int32_t span,
+                                                       uint32_t hmask, unsigned char *ctr,
                                                        unsigned long long *msum, int *ovf,
                                                        int *ins) {
     uint32_t *w32 = reinterpret_cast<uint32_t *>(ctr);
@@ -207,13 +247,14 @@ __device__ __forceinline__ unsigned long long wedge_op(const CountParams &p, int
         int inserted = 0;
         const int slot = hash_find(hkeys, hmask, w - lb, !kSecond, &inserted);
         if (slot < 0) {
-            // Algorithm 3 sizes tables by a guess: a full table sends the start
-            // to the retry pass; Algorithm 2's sizing rules it out
-            if (p.orient && !kSecond) *ovf = 1; else atomicOr(p.err, kErrHashFull);
+            // the first walk re-queues a start whose table filled up; the
+            // second walk only looks up ends the first walk inserted
+            if (!kSecond) *ovf = 1; else atomicOr(p.err, kErrHashFull);
             return 0;
         }
         if (!kSecond) {
-            if (inserted && p.orient && atomicAdd(ins, 1) >= (int)((hmask + 1) / 4 * 3)) *ovf = 1;
+            // keep the load factor at most 3/4 so probes stay short
+            if (inserted && atomicAdd(ins, 1) >= (int)((hmask + 1) / 4 * 3)) *ovf = 1;
             return inc16(hcnt, slot);
         }
         c = get16(hcnt, slot);
@@ -236,23 +277,25 @@ __device__ __forceinline__ unsigned long long wedge_op(const CountParams &p, int
 // One walk over the wedges of start x whose ends fall in [lb+lo, lb+hi).
 // kSecond = false: count (returns Σ old, i.e. Σ C(count, 2)).
 // kSecond = true : read the final counts and attribute δ = count − 1.
+// flags: bit 0 = cut the runs below lb+lo, bit 1 = cut them at lb+hi.
 //
-// The middles of x are taken a batch at a time (2048, or 1024 with 64-bit
-// positions).  For each middle, the run of ends in range is [s0, s1) of its
-// list (from the chunk-boundary table, or a binary search when there is
-// none).  Non-empty runs are compacted and their concatenation is cut into
-// windows of 32 wedges; each warp takes a contiguous range of windows.
-// Inside a window the run of every lane is found from a 32-bit mask of run
-// starts (reduce-or + popc), so no search is needed per wedge, and four
-// windows are in flight per iteration so their end loads overlap.
-template <int MODE, int KIND, bool kSecond, typename Pos, class SH>
-__device__ unsigned long long cta_walk(const CountParams &p, int32_t x, int32_t lb, int32_t lo,
-                                       int32_t hi, int flags, uint32_t hmask, unsigned char *ctr,
-                                       SH &sh) {
-    constexpr int kPer = Batch<Pos>::kPer;
-    constexpr int kB = Batch<Pos>::kSize;
+// The middles of x are taken a batch at a time (two per thread, or one with
+// 64-bit positions).  For each middle the run of ends in range comes from the
+// slot arrays (plus the chunk-boundary table or a binary search for dense
+// chunks).  Non-empty runs are compacted and their concatenation is cut into
+// windows of 32 wedges; each warp takes a contiguous range of windows.  Inside
+// a window the run of every lane is found from a 32-bit mask of run starts
+// (reduce-or + popc), so no search is needed per wedge, and four windows are
+// in flight per iteration so their end loads overlap.
+template <int MODE, int KIND, bool kSecond, typename Pos, int kThreads, class SH>
+__device__ unsigned long long team_walk(const CountParams &p, int32_t x, int32_t lb, int32_t lo,
+                                        int32_t hi, int flags, uint32_t hmask, unsigned char *ctr,
+                                        SH &sh, const Team<kThreads> &t) {
+    constexpr int kPer = Batch<Pos, kThreads>::kPer;
+    constexpr int kB = Batch<Pos, kThreads>::kSize;
+    constexpr int kWarps = kThreads / 32;
     constexpr int kU = 4;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = t.tid, lane = tid & 31, warp = tid >> 5;
     const int64_t e0 = p.off[x];
     // Algorithm 2: the middles are the cut[x] lower-priority neighbours;
     // Algorithm 3: every neighbour is a middle
@@ -268,7 +311,7 @@ __device__ unsigned long long cta_walk(const CountParams &p, int32_t x, int32_t 
         long long pk[kPer];
 #pragma unroll
         for (int i = 0; i < kPer; ++i) {
-            const int32_t j = mb + i * kCountThreads + tid;
+            const int32_t j = mb + i * kThreads + tid;
             len[i] = 0; v[i] = 0; src[i] = 0; e[i] = 0;
             if (j < nmid) {
                 e[i] = e0 + j;
@@ -298,7 +341,7 @@ __device__ unsigned long long cta_walk(const CountParams &p, int32_t x, int32_t 
             packed_run += pk[i];
         }
         long long packed_total;
-        long long packed = block_excl_scan(packed_run, sh, &packed_total);
+        long long packed = team_excl_scan(packed_run, sh, t, &packed_total);
         const int32_t total = (int32_t)(packed_total >> 20);
         const int nnz = (int)(packed_total & 0xfffff);
         int nzs[kPer];
@@ -314,10 +357,10 @@ __device__ unsigned long long cta_walk(const CountParams &p, int32_t x, int32_t 
             packed += pk[i];
         }
         if (tid == 0) sh.start[nnz] = total;
-        __syncthreads();
+        t.sync();
         const int32_t nwin = (total + 31) >> 5;
-        int32_t wb = (int32_t)(((int64_t)warp * nwin) >> 5);
-        const int32_t wend = (int32_t)(((int64_t)(warp + 1) * nwin) >> 5);
+        int32_t wb = (int32_t)(((int64_t)warp * nwin) / kWarps);
+        const int32_t wend = (int32_t)(((int64_t)(warp + 1) * nwin) / kWarps);
         if (wb < wend) {
             int32_t k0 = wb << 5;
             int q0 = last_le(sh.start, nnz, k0);
@@ -354,11 +397,13 @@ __device__ unsigned long long cta_walk(const CountParams &p, int32_t x, int32_t 
                 }
 #pragma unroll
                 for (int u = 0; u < kU; ++u)
-                    if (ok[u]) acc += wedge_op<MODE, KIND, kSecond, Pos>(p, w[u], pos[u], q[u], lb, lo, span, hmask, ctr, sh.msum, &sh.overflow, &sh.inserts);
+                    if (ok[u])
+                        acc += wedge_op<MODE, KIND, kSecond, Pos>(p, w[u], pos[u], q[u], lb, lo, span, hmask,
+                                                                  ctr, sh.msum, &sh.overflow, &sh.inserts);
                 k0 += 32 * kU;
             }
         }
-        __syncthreads();
+        t.sync();
         if (KIND == kHash && !kSecond && sh.overflow) break;   // uniform: read after the barrier
         if (kSecond) {
 #pragma unroll
@@ -376,23 +421,26 @@ __device__ unsigned long long cta_walk(const CountParams &p, int32_t x, int32_t 
     return acc;
 }
 
-template <int MODE, int KIND, typename Pos, class SH>
-__device__ unsigned long long cta_item_body(const CountParams &p, int32_t x, int32_t lb,
-                                            int32_t lo, int32_t hi, int flags, uint32_t hmask,
-                                            unsigned char *ctr, SH &sh) {
-    unsigned long long acc = cta_walk<MODE, KIND, false, Pos>(p, x, lb, lo, hi, flags, hmask, ctr, sh);
-    if (KIND == kHash && p.orient) {
-        __syncthreads();
+// First walk, then (per-vertex / per-edge) the end contributions and the
+// second walk.  Returns Σ C(count, 2) over the pairs of this item, or 0 with
+// sh.overflow set when a hash table filled up (nothing is attributed then).
+template <int MODE, int KIND, typename Pos, int kThreads, class SH>
+__device__ unsigned long long item_body(const CountParams &p, int32_t x, int32_t lb, int32_t lo,
+                                        int32_t hi, int flags, uint32_t hmask, unsigned char *ctr,
+                                        SH &sh, const Team<kThreads> &t) {
+    unsigned long long acc = team_walk<MODE, KIND, false, Pos>(p, x, lb, lo, hi, flags, hmask, ctr, sh, t);
+    if (KIND == kHash) {
+        t.sync();
         if (sh.overflow) return 0;   // the caller re-queues x
     }
     if (has_second_walk(MODE)) {
-        __syncthreads();
+        t.sync();
         if (MODE == kModeVertices) {
             // ends: each pair (x, w) adds C(count, 2) to ⋈_w
             if (KIND == kHash) {
                 const int32_t *hkeys = reinterpret_cast<const int32_t *>(ctr);
                 const uint32_t *hcnt = reinterpret_cast<const uint32_t *>(ctr + (size_t)(hmask + 1) * 4);
-                for (uint32_t s = threadIdx.x; s <= hmask; s += kCountThreads) {
+                for (uint32_t s = t.tid; s <= hmask; s += kThreads) {
                     const int32_t k = hkeys[s];
                     if (k >= 0) {
                         const unsigned long long b = c2(get16(hcnt, (int)s));
@@ -401,88 +449,157 @@ __device__ unsigned long long cta_item_body(const CountParams &p, int32_t x, int
                 }
             } else {
                 const uint32_t *w32 = reinterpret_cast<const uint32_t *>(ctr);
-                for (int32_t i = threadIdx.x; i < hi - lo; i += kCountThreads) {
+                for (int32_t i = t.tid; i < hi - lo; i += kThreads) {
                     const uint32_t c = (KIND == kDenseWide) ? w32[i] : get16(w32, i);
                     if (c >= 2) atomicAdd(p.pv + lb + lo + i, c2(c));
                 }
             }
         }
-        cta_walk<MODE, KIND, true, Pos>(p, x, lb, lo, hi, flags, hmask, ctr, sh);
+        team_walk<MODE, KIND, true, Pos>(p, x, lb, lo, hi, flags, hmask, ctr, sh, t);
         if (MODE == kModeVertices) {
-            const unsigned long long t = block_sum(acc, sh);
-            if (threadIdx.x == 0 && t) atomicAdd(p.pv + x, t);
+            const unsigned long long s = team_sum(acc, sh, t);
+            if (t.tid == 0 && s) atomicAdd(p.pv + x, s);
         }
     }
     return acc;
 }
 
-__device__ __forceinline__ void zero_smem(unsigned char *p, int bytes, uint32_t fill) {
-    uint4 *q = reinterpret_cast<uint4 *>(p);
-    const int n16 = (bytes + 15) >> 4;
-    const uint4 f = make_uint4(fill, fill, fill, fill);
-    for (int i = threadIdx.x; i < n16; i += kCountThreads) q[i] = f;
+// first id of x's part of its layer, and one past its last
+__device__ __forceinline__ int32_t range_lo(const CountParams &p, int32_t x) {
+    return p.vbase ? __ldg(p.vbase + x) : (x >= p.l ? p.l : 0);
+}
+__device__ __forceinline__ int32_t range_hi(const CountParams &p, int32_t x) {
+    return p.vend ? __ldg(p.vend + x) : (x >= p.l ? p.n : p.l);
 }
 
+// How many distinct ends x can have: the vertices below it (Algorithm 2) or
+// above it (Algorithm 3) in its part of its layer, and at most one per wedge.
+__device__ __forceinline__ unsigned long long end_bound(const CountParams &p, int32_t x,
+                                                        int32_t lb) {
+    const unsigned long long range = p.orient ? (unsigned long long)(range_hi(p, x) - x - 1)
+                                              : (unsigned long long)(x - lb);
+    const unsigned long long w = p.work[x];
+    return w < range ? w : range;
+}
+
+// A count_wedge is at most the number of middles: cut[x] (Algorithm 2) or
+// deg(x) (Algorithm 3).
+__device__ __forceinline__ int64_t middles(const CountParams &p, int32_t x) {
+    return p.orient ? p.off[x + 1] - p.off[x] : (int64_t)p.cut[x];
+}
+
+// A start counted by the team with one hash table of at most `max_slots`
+// slots.  Returns its Σ C(count, 2), or sets sh.overflow.
+template <int MODE, typename Pos, int kThreads, class SH>
+__device__ unsigned long long hash_item(const CountParams &p, int32_t x, unsigned char *ctr,
+                                        int max_slots, SH &sh, const Team<kThreads> &t) {
+    const int32_t lb = range_lo(p, x);
+    const unsigned long long bound = end_bound(p, x, lb);
+    uint32_t cap = 64;
+    while (cap < 2 * bound && cap < (uint32_t)max_slots) cap <<= 1;
+    // hash tables hold 16-bit counts; a count is at most min(middles, work)
+    const bool wide = middles(p, x) > (int64_t)kNarrowMaxCut && p.work[x] > (uint64_t)kNarrowMaxCut;
+    if (t.tid == 0) { sh.overflow = wide ? 1 : 0; sh.inserts = 0; }
+    team_fill(ctr, (int)cap * 4, 0xffffffffu, t);           // keys = -1
+    team_fill(ctr + (size_t)cap * 4, (int)cap * 2, 0u, t);  // packed 16-bit counts
+    t.sync();
+    if (sh.overflow) return 0;
+    return item_body<MODE, kHash, Pos>(p, x, lb, 0, 0, 0, cap - 1, ctr, sh, t);
+}
+
+// A start counted by the CTA with dense counters, chunk after chunk of its
+// end range: [0, x - lb) for Algorithm 2, (x, end of x's part) for Algorithm 3.
 template <int MODE, typename Pos, class SH>
-__device__ unsigned long long cta_item(const CountParams &p, int2 item, unsigned char *ctr,
-                                       SH &sh) {
+__device__ unsigned long long dense_all_chunks(const CountParams &p, int32_t x, unsigned char *ctr,
+                                               SH &sh, const Team<kCountThreads> &t) {
+    const int32_t lb = range_lo(p, x);
+    const bool wide = middles(p, x) > (int64_t)kNarrowMaxCut;
+    const int32_t S = wide ? kDense32 : kDense16;
+    const int32_t first = p.orient ? x + 1 - lb : 0;
+    const int32_t last = p.orient ? range_hi(p, x) - lb : x - lb;   // ends in [lb + first, lb + last)
+    unsigned long long acc = 0;
+    for (int32_t c = first / S; c * S < last; ++c) {
+        const int32_t lo = max(c * S, first), hi = min((c + 1) * S, last);
+        const int32_t span = hi - lo;
+        const int flags = (lo > first ? 1 : 0) | (hi < last ? 2 : 0);
+        team_fill(ctr, wide ? span * 4 : ((span + 1) >> 1) * 4, 0u, t);
+        t.sync();
+        acc += wide ? item_body<MODE, kDenseWide, Pos>(p, x, lb, lo, hi, flags, 0, ctr, sh, t)
+                    : item_body<MODE, kDenseNarrow, Pos>(p, x, lb, lo, hi, flags, 0, ctr, sh, t);
+        t.sync();
+    }
+    return acc;
+}
+
+template <int kThreads, class SH>
+__device__ __forceinline__ void add_to_graph(const CountParams &p, int32_t x, unsigned long long acc,
+                                             SH &sh, const Team<kThreads> &t) {
+    // a batch is a disjoint union: every butterfly of start x lies in x's graph
+    const unsigned long long s = team_sum(acc, sh, t);
+    if (t.tid == 0 && s) atomicAdd(p.gtot + p.gstar[x], s);
+}
+
+__device__ __forceinline__ void push_retry(const CountParams &p, int32_t entry) {
+    // without a retry pass the schedule's bounds rule overflow out; a count
+    // that lost a start this way fails loudly
+    if (!p.retry_on) { atomicOr(p.err, kErrHashFull); return; }
+    const int64_t k = p.retry_static + atomicAdd(p.cursors + 2, 1);
+    if (k < p.retry_cap) p.retry[k] = entry; else atomicOr(p.err, kErrBounds);
+}
+
+// ---- phase A: CTA items ---------------------------------------------------------
+template <int MODE, typename Pos, class SH>
+__device__ unsigned long long cta_item(const CountParams &p, int2 item, unsigned char *ctr, SH &sh,
+                                       const Team<kCountThreads> &t) {
     const int32_t x = item.x;
-    // ends lie in x's layer (in a batch: x's graph's part of it) from lb on
-    const int32_t lb = p.vbase ? __ldg(p.vbase + x) : (x >= p.l ? p.l : 0);
-    const int32_t R = x - lb;   // Algorithm 2: the ends are the R vertices below x
     unsigned long long acc;
     if (item.y >= 0) {          // dense items exist only for Algorithm 2
+        const int32_t lb = range_lo(p, x);
+        const int32_t R = x - lb;   // the ends are the R vertices below x
         const bool wide = (uint32_t)p.cut[x] > kNarrowMaxCut;
         const int32_t S = wide ? kDense32 : kDense16;
         const int32_t lo = item.y * S;
         const int32_t hi = min(R, lo + S);
         const int32_t span = hi - lo;
         const int flags = (lo > 0 ? 1 : 0) | (hi < R ? 2 : 0);
-        zero_smem(ctr, wide ? span * 4 : ((span + 1) >> 1) * 4, 0u);
-        __syncthreads();
-        acc = wide ? cta_item_body<MODE, kDenseWide, Pos>(p, x, lb, lo, hi, flags, 0, ctr, sh)
-                   : cta_item_body<MODE, kDenseNarrow, Pos>(p, x, lb, lo, hi, flags, 0, ctr, sh);
+        team_fill(ctr, wide ? span * 4 : ((span + 1) >> 1) * 4, 0u, t);
+        t.sync();
+        acc = wide ? item_body<MODE, kDenseWide, Pos>(p, x, lb, lo, hi, flags, 0, ctr, sh, t)
+                   : item_body<MODE, kDenseNarrow, Pos>(p, x, lb, lo, hi, flags, 0, ctr, sh, t);
     } else {
-        // how many distinct ends x can have: the vertices below it (Algorithm 2)
-        // or above it (Algorithm 3), and at most one per wedge
-        unsigned long long range = (unsigned long long)R;
-        if (p.orient) {
-            const int32_t hiend = p.vend ? __ldg(p.vend + x) : (x >= p.l ? p.n : p.l);
-            range = (unsigned long long)(hiend - x - 1);
-        }
-        const unsigned long long w = p.work[x];
-        const unsigned long long bound = w < range ? w : range;
-        uint32_t cap = 64;
-        while (cap < 2 * bound && cap < (uint32_t)kHashMaxSlots) cap <<= 1;
-        // Algorithm 3: counts are bounded by deg(x), which must fit 16 bits here
-        const bool too_wide = p.orient && (p.off[x + 1] - p.off[x]) > (int64_t)kNarrowMaxCut;
-        if (threadIdx.x == 0) { sh.overflow = too_wide ? 1 : 0; sh.inserts = 0; }
-        zero_smem(ctr, (int)cap * 4, 0xffffffffu);           // keys = -1
-        zero_smem(ctr + (size_t)cap * 4, (int)cap * 2, 0u);  // packed 16-bit counts
-        __syncthreads();
-        acc = sh.overflow ? 0ull : cta_item_body<MODE, kHash, Pos>(p, x, lb, 0, 0, 0, cap - 1, ctr, sh);
-        if (p.orient && sh.overflow) {
-            // discard this attempt: the retry pass counts x with dense chunks
-            if (threadIdx.x == 0) {
-                const int64_t k = p.retry_static + atomicAdd(p.cursors + 2, 1);
-                if (k < p.retry_cap) p.retry[k] = x; else atomicOr(p.err, kErrBounds);
-            }
-            __syncthreads();
+        acc = hash_item<MODE, Pos>(p, x, ctr, kHashMaxSlots, sh, t);
+        if (sh.overflow) {
+            // the CTA table was too small: dense chunks next
+            if (t.tid == 0) push_retry(p, -(x + 1));
+            t.sync();
             return 0;
         }
     }
-    if (MODE == kModeBatch) {
-        // the batch is a disjoint union: every butterfly of start x lies in x's graph
-        const unsigned long long t = block_sum(acc, sh);
-        if (threadIdx.x == 0 && t) atomicAdd(p.gtot + p.gstar[x], t);
-    }
-    __syncthreads();
+    if (MODE == kModeBatch) add_to_graph(p, x, acc, sh, t);
+    t.sync();
     return acc;
 }
 
-// ---- warp items -------------------------------------------------------------
-// The warp version of cta_walk for a light start: batches of 32 middles,
-// compacted runs and the same window masks, with a per-warp hash table.
+// ---- phase B: team items ----------------------------------------------------------
+template <int MODE, typename Pos, class SH>
+__device__ unsigned long long team_item(const CountParams &p, int32_t x, unsigned char *table,
+                                        SH &sh, const Team<kTeamThreads> &t) {
+    unsigned long long acc = hash_item<MODE, Pos>(p, x, table, kTeamSlots, sh, t);
+    if (sh.overflow) {
+        // a CTA table next
+        if (t.tid == 0) push_retry(p, x);
+        t.sync();
+        return 0;
+    }
+    if (MODE == kModeBatch) add_to_graph(p, x, acc, sh, t);
+    t.sync();
+    return acc;
+}
+
+// ---- phase C: warp items ----------------------------------------------------------
+// The warp version of team_walk for a light start: batches of 32 middles,
+// compacted runs and the same window masks, with a per-warp hash table that
+// always fits (at most 256 wedges, 512 slots).
 template <int MODE, bool kSecond>
 __device__ unsigned long long warp_walk(const CountParams &p, int32_t x, int32_t lb, uint32_t mask,
                                         int32_t *keys, uint32_t *cnt, unsigned long long *msum,
@@ -571,15 +688,8 @@ static_assert(kWarpStartOff + 33 * 4 <= kWarpRegion, "per-warp region overflow")
 template <int MODE>
 __device__ unsigned long long warp_item(const CountParams &p, int32_t x, unsigned char *region) {
     const int lane = threadIdx.x & 31;
-    // ends lie in x's layer (in a batch: x's graph's part of it) from lb on
-    const int32_t lb = p.vbase ? __ldg(p.vbase + x) : (x >= p.l ? p.l : 0);
-    unsigned long long range = (unsigned long long)(x - lb);
-    if (p.orient) {
-        const int32_t hiend = p.vend ? __ldg(p.vend + x) : (x >= p.l ? p.n : p.l);
-        range = (unsigned long long)(hiend - x - 1);
-    }
-    const unsigned long long w = p.work[x];
-    const unsigned long long bound = w < range ? w : range;
+    const int32_t lb = range_lo(p, x);
+    const unsigned long long bound = end_bound(p, x, lb);
     uint32_t cap = 32;
     while (cap < 2 * bound && cap < (uint32_t)kWarpSlots) cap <<= 1;
     int32_t *keys = reinterpret_cast<int32_t *>(region);
@@ -619,18 +729,40 @@ __device__ unsigned long long warp_item(const CountParams &p, int32_t x, unsigne
 template <int MODE, typename Pos>
 __global__ void __launch_bounds__(kCountThreads, 1) k_count(CountParams p) {
     extern __shared__ __align__(16) unsigned char ctr[];
-    __shared__ SharedCTA<MODE, Pos> sh;
+    __shared__ SharedTeam<MODE, Pos, kCountThreads> sh;
+    const Team<kCountThreads> cta{(int)threadIdx.x, 0};
     unsigned long long acc = 0;
-    // phase 1: CTA items, heaviest first
+    // phase A: CTA items, heaviest first
     for (;;) {
         if (threadIdx.x == 0) sh.item = atomicAdd(p.cursors, 1);
         __syncthreads();
         const int64_t it = sh.item;
         __syncthreads();
         if (it >= p.n_cta) break;
-        acc += cta_item<MODE, Pos>(p, p.cta_items[it], ctr, sh);
+        acc += cta_item<MODE, Pos>(p, p.cta_items[it], ctr, sh, cta);
     }
-    // phase 2: warp items
+    // phase B: team items.  Team k owns warps 8k..8k+7 and the 48 KB of shared
+    // memory that are their warp regions; its table is followed by its batch
+    // arrays.  A team leaves together (its item index is read before its
+    // barrier), so none of its warps is still using the region when the
+    // first one starts phase C in its own part of it.
+    if (p.n_team > 0) {
+        typedef SharedTeam<MODE, Pos, kTeamThreads> TS;
+        static_assert(kTeamTableBytes + sizeof(TS) <= kTeamRegion, "team region overflow");
+        const int k = threadIdx.x / kTeamThreads;
+        const Team<kTeamThreads> team{(int)(threadIdx.x % kTeamThreads), 1 + k};
+        unsigned char *table = ctr + (size_t)k * kTeamRegion;
+        TS &tsh = *reinterpret_cast<TS *>(table + kTeamTableBytes);
+        for (;;) {
+            if (team.tid == 0) tsh.item = atomicAdd(p.cursors + 4, 1);
+            team.sync();
+            const int64_t it = tsh.item;
+            team.sync();
+            if (it >= p.n_team) break;
+            acc += team_item<MODE, Pos>(p, p.team_items[it], table, tsh, team);
+        }
+    }
+    // phase C: warp items
     {
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
         unsigned char *region = ctr + (size_t)warp * kWarpRegion;
@@ -643,17 +775,19 @@ __global__ void __launch_bounds__(kCountThreads, 1) k_count(CountParams p) {
         }
     }
     // a7: reduction of the per-thread partial sums
-    const unsigned long long t = block_sum(acc, sh);
+    const unsigned long long t = team_sum(acc, sh, cta);
     if (threadIdx.x == 0 && t) atomicAdd(p.acc, t);
 }
 
-// Algorithm 3's retry pass: the starts whose hash table filled up (or whose
-// counts could pass 16 bits) are counted with dense counters, one CTA per
-// start, chunk after chunk of the end range (x, end of x's layer).
+// The retry pass over the starts the first launch (or prepare) re-queued.
+// Entry x >= 0: its team table filled up, so try a CTA table; entry -(x+1),
+// or a CTA table that fills up too: dense counters over the chunks of x's
+// end range.
 template <int MODE, typename Pos>
 __global__ void __launch_bounds__(kCountThreads, 1) k_count_retry(CountParams p) {
     extern __shared__ __align__(16) unsigned char ctr[];
-    __shared__ SharedCTA<MODE, Pos> sh;
+    __shared__ SharedTeam<MODE, Pos, kCountThreads> sh;
+    const Team<kCountThreads> cta{(int)threadIdx.x, 0};
     unsigned long long acc = 0;
     const int nretry = (int)min(p.retry_static + *((volatile int *)(p.cursors + 2)), p.retry_cap);
     for (;;) {
@@ -662,31 +796,21 @@ __global__ void __launch_bounds__(kCountThreads, 1) k_count_retry(CountParams p)
         const int it = sh.item;
         __syncthreads();
         if (it >= nretry) break;
-        const int32_t x = p.retry[it];
-        const int32_t lb = p.vbase ? __ldg(p.vbase + x) : (x >= p.l ? p.l : 0);
-        const int32_t hiend = p.vend ? __ldg(p.vend + x) : (x >= p.l ? p.n : p.l);
-        const bool wide = (p.off[x + 1] - p.off[x]) > (int64_t)kNarrowMaxCut;
-        const int32_t S = wide ? kDense32 : kDense16;
-        const int32_t first = x + 1 - lb, last = hiend - lb;   // ends in [lb + first, lb + last)
+        const int32_t entry = p.retry[it];
+        const int32_t x = entry >= 0 ? entry : -(entry + 1);
         unsigned long long item_acc = 0;
-        for (int32_t c = first / S; c * S < last; ++c) {
-            const int32_t lo = max(c * S, first), hi = min((c + 1) * S, last);
-            const int32_t span = hi - lo;
-            const int flags = (lo > first ? 1 : 0) | (hi < last ? 2 : 0);
-            zero_smem(ctr, wide ? span * 4 : ((span + 1) >> 1) * 4, 0u);
-            __syncthreads();
-            item_acc += wide ? cta_item_body<MODE, kDenseWide, Pos>(p, x, lb, lo, hi, flags, 0, ctr, sh)
-                             : cta_item_body<MODE, kDenseNarrow, Pos>(p, x, lb, lo, hi, flags, 0, ctr, sh);
+        bool done = false;
+        if (entry >= 0) {
+            item_acc = hash_item<MODE, Pos>(p, x, ctr, kHashMaxSlots, sh, cta);
+            done = !sh.overflow;
             __syncthreads();
         }
-        if (MODE == kModeBatch) {
-            const unsigned long long t = block_sum(item_acc, sh);
-            if (threadIdx.x == 0 && t) atomicAdd(p.gtot + p.gstar[x], t);
-            __syncthreads();
-        }
+        if (!done) item_acc = dense_all_chunks<MODE, Pos>(p, x, ctr, sh, cta);
+        if (MODE == kModeBatch) add_to_graph(p, x, item_acc, sh, cta);
+        __syncthreads();
         acc += item_acc;
     }
-    const unsigned long long t = block_sum(acc, sh);
+    const unsigned long long t = team_sum(acc, sh, cta);
     if (threadIdx.x == 0 && t) atomicAdd(p.acc, t);
 }
 
@@ -708,6 +832,22 @@ cudaError_t setup_one() {
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, kCounterBytes);
 }
 
+template <typename Pos>
+void launch_main(int mode, int grid, cudaStream_t s, const CountParams &p) {
+    if (mode == kModeTotal) k_count<kModeTotal, Pos><<<grid, kCountThreads, kCounterBytes, s>>>(p);
+    else if (mode == kModeBatch) k_count<kModeBatch, Pos><<<grid, kCountThreads, kCounterBytes, s>>>(p);
+    else if (mode == kModeVertices) k_count<kModeVertices, Pos><<<grid, kCountThreads, kCounterBytes, s>>>(p);
+    else k_count<kModeEdges, Pos><<<grid, kCountThreads, kCounterBytes, s>>>(p);
+}
+
+template <typename Pos>
+void launch_retry(int mode, int grid, cudaStream_t s, const CountParams &p) {
+    if (mode == kModeTotal) k_count_retry<kModeTotal, Pos><<<grid, kCountThreads, kCounterBytes, s>>>(p);
+    else if (mode == kModeBatch) k_count_retry<kModeBatch, Pos><<<grid, kCountThreads, kCounterBytes, s>>>(p);
+    else if (mode == kModeVertices) k_count_retry<kModeVertices, Pos><<<grid, kCountThreads, kCounterBytes, s>>>(p);
+    else k_count_retry<kModeEdges, Pos><<<grid, kCountThreads, kCounterBytes, s>>>(p);
+}
+
 }  // namespace
 
 int count_smem_setup(int device) {
@@ -717,11 +857,11 @@ int count_smem_setup(int device) {
     BFC_CUDA((setup_one<kModeTotal, int32_t>()));
     BFC_CUDA((setup_one<kModeVertices, int32_t>()));
     BFC_CUDA((setup_one<kModeEdges, int32_t>()));
-    BFC_CUDA((setup_one<kModeTotal, long long>()));
     BFC_CUDA((setup_one<kModeBatch, int32_t>()));
-    BFC_CUDA((setup_one<kModeBatch, long long>()));
+    BFC_CUDA((setup_one<kModeTotal, long long>()));
     BFC_CUDA((setup_one<kModeVertices, long long>()));
     BFC_CUDA((setup_one<kModeEdges, long long>()));
+    BFC_CUDA((setup_one<kModeBatch, long long>()));
     done[device] = true;
     return BFC_OK;
 }
@@ -732,45 +872,32 @@ int launch_count(Graph *g, cudaStream_t s, int mode, unsigned long long *pv_proj
     if (rc) return rc;
     CountParams p;
     p.off = g->off; p.adj = g->adj; p.eid = g->eid; p.plen = g->plen; p.cut = g->cut;
-    p.work = g->work; p.cta_items = g->cta_items; p.warp_items = g->warp_items;
-    p.n_cta = g->n_cta_items; p.n_warp = g->n_warp_items;
+    p.work = g->work; p.cta_items = g->cta_items; p.team_items = g->team_items;
+    p.warp_items = g->warp_items;
+    p.n_cta = g->n_cta_items; p.n_team = g->n_team_items; p.n_warp = g->n_warp_items;
     p.cursors = g->cursors; p.acc = g->acc; p.pv = pv_proj; p.pe = pe;
-    p.adj_len = 2 * g->m; p.l = g->l; p.err = g->err;
-    p.coff = g->coff; p.coff_u1 = g->coff_u1; p.coff_l1 = g->coff_l1;
-    p.gstar = g->gstar; p.gtot = gtot; p.vbase = g->vbase;
-    p.vend = g->vend; p.sbeg = g->sbeg; p.retry = g->retry; p.retry_cap = g->retry_cap;
-    p.retry_static = g->retry_static;
+    // the chunk-boundary table is relative to the start of each list, which
+    // is where Algorithm 2's runs start
+    p.coff = g->opt.orientation == 0 ? g->coff : nullptr;
+    p.coff_u1 = g->coff_u1; p.coff_l1 = g->coff_l1;
+    p.gstar = g->gstar; p.vbase = g->vbase; p.vend = g->vend; p.sbeg = g->sbeg; p.gtot = gtot;
+    p.retry = g->retry; p.retry_cap = g->retry_cap; p.retry_static = g->retry_static;
+    p.retry_on = g->may_retry ? 1 : 0;
     p.orient = g->opt.orientation; p.n = g->n;
-    BFC_CUDA(cudaMemsetAsync(g->cursors, 0, 4 * sizeof(int), s));
+    p.adj_len = 2 * g->m; p.l = g->l; p.err = g->err;
+    BFC_CUDA(cudaMemsetAsync(g->cursors, 0, 8 * sizeof(int), s));
     BFC_CUDA(cudaMemsetAsync(g->acc, 0, sizeof(unsigned long long), s));
     const int grid = g->grid;
     // 32-bit adjacency positions whenever G* has fewer than 2^31 slots
-    if (2 * g->m <= 0x7fffffffll && !g->opt.wide_positions) {
-        if (mode == kModeTotal) k_count<kModeTotal, int32_t><<<grid, kCountThreads, kCounterBytes, s>>>(p);
-        else if (mode == kModeBatch) k_count<kModeBatch, int32_t><<<grid, kCountThreads, kCounterBytes, s>>>(p);
-        else if (mode == kModeVertices) k_count<kModeVertices, int32_t><<<grid, kCountThreads, kCounterBytes, s>>>(p);
-        else k_count<kModeEdges, int32_t><<<grid, kCountThreads, kCounterBytes, s>>>(p);
-    } else {
-        if (mode == kModeTotal) k_count<kModeTotal, long long><<<grid, kCountThreads, kCounterBytes, s>>>(p);
-        else if (mode == kModeBatch) k_count<kModeBatch, long long><<<grid, kCountThreads, kCounterBytes, s>>>(p);
-        else if (mode == kModeVertices) k_count<kModeVertices, long long><<<grid, kCountThreads, kCounterBytes, s>>>(p);
-        else k_count<kModeEdges, long long><<<grid, kCountThreads, kCounterBytes, s>>>(p);
-    }
+    const bool narrow_pos = 2 * g->m <= 0x7fffffffll && !g->opt.wide_positions;
+    if (narrow_pos) launch_main<int32_t>(mode, grid, s, p);
+    else launch_main<long long>(mode, grid, s, p);
     note_launch();
     BFC_CUDA(cudaGetLastError());
-    if (g->opt.orientation == 1) {
+    if (g->may_retry) {
         // the retry pass reads how many starts the first launch re-queued
-        if (2 * g->m <= 0x7fffffffll && !g->opt.wide_positions) {
-            if (mode == kModeTotal) k_count_retry<kModeTotal, int32_t><<<grid, kCountThreads, kCounterBytes, s>>>(p);
-            else if (mode == kModeBatch) k_count_retry<kModeBatch, int32_t><<<grid, kCountThreads, kCounterBytes, s>>>(p);
-            else if (mode == kModeVertices) k_count_retry<kModeVertices, int32_t><<<grid, kCountThreads, kCounterBytes, s>>>(p);
-            else k_count_retry<kModeEdges, int32_t><<<grid, kCountThreads, kCounterBytes, s>>>(p);
-        } else {
-            if (mode == kModeTotal) k_count_retry<kModeTotal, long long><<<grid, kCountThreads, kCounterBytes, s>>>(p);
-            else if (mode == kModeBatch) k_count_retry<kModeBatch, long long><<<grid, kCountThreads, kCounterBytes, s>>>(p);
-            else if (mode == kModeVertices) k_count_retry<kModeVertices, long long><<<grid, kCountThreads, kCounterBytes, s>>>(p);
-            else k_count_retry<kModeEdges, long long><<<grid, kCountThreads, kCounterBytes, s>>>(p);
-        }
+        if (narrow_pos) launch_retry<int32_t>(mode, grid, s, p);
+        else launch_retry<long long>(mode, grid, s, p);
         note_launch();
         BFC_CUDA(cudaGetLastError());
     }
@@ -781,7 +908,8 @@ int gather_vertices(Graph *g, cudaStream_t s, uint64_t *per_u, uint64_t *per_l) 
     const int64_t nmax = g->r > g->l ? g->r : g->l;
     if (nmax == 0) return BFC_OK;
     k_gather_vertices<<<(unsigned)((nmax + 255) / 256), 256, 0, s>>>(g->pv, g->rank_u, g->rank_l,
-                                                                      g->r, g->l, per_u, per_l); note_launch();
+                                                                      g->r, g->l, per_u, per_l);
+    note_launch();
     BFC_CUDA(cudaGetLastError());
     return BFC_OK;
 }

@@ -249,26 +249,24 @@ __global__ void k_sched_keys(const uint64_t *__restrict__ work, int32_t n, uint6
 }
 
 // counts[0] = dense starts, [1] = hash starts, [2] = warp starts
+// Bins of a6: [0] dense (work > hash_max), [1] CTA hash (team_max < work <=
+// hash_max), [2] team (warp_max < work <= team_max), [3] warp (0 < work <= warp_max).
 __global__ void k_classify(const uint64_t *__restrict__ work, int32_t n, uint64_t warp_max,
-                           uint64_t hash_max, unsigned long long *counts) {
-    unsigned long long c0 = 0, c1 = 0, c2 = 0;
+                           uint64_t team_max, uint64_t hash_max, unsigned long long *counts) {
+    unsigned long long c[4] = {0, 0, 0, 0};
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
          x += (int64_t)gridDim.x * blockDim.x) {
         uint64_t w = work[x];
-        if (w > hash_max) ++c0;
-        else if (w > warp_max) ++c1;
-        else if (w > 0) ++c2;
+        if (w > hash_max) ++c[0];
+        else if (w > team_max) ++c[1];
+        else if (w > warp_max) ++c[2];
+        else if (w > 0) ++c[3];
     }
 #pragma unroll
-    for (int d = 16; d > 0; d >>= 1) {
-        c0 += __shfl_xor_sync(0xffffffffu, c0, d);
-        c1 += __shfl_xor_sync(0xffffffffu, c1, d);
-        c2 += __shfl_xor_sync(0xffffffffu, c2, d);
-    }
-    if ((threadIdx.x & 31) == 0) {
-        if (c0) atomicAdd(&counts[0], c0);
-        if (c1) atomicAdd(&counts[1], c1);
-        if (c2) atomicAdd(&counts[2], c2);
+    for (int k = 0; k < 4; ++k) {
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) c[k] += __shfl_xor_sync(0xffffffffu, c[k], d);
+        if ((threadIdx.x & 31) == 0 && c[k]) atomicAdd(&counts[k], c[k]);
     }
 }
 
@@ -288,12 +286,15 @@ __global__ void k_chunk_counts(const int32_t *__restrict__ order, int64_t n_dens
     nch[i] = dense_chunks(x, l, cut[x], vbase);
 }
 
+// starts in descending work order: dense (chunked), CTA hash, team, warp
 __global__ void k_emit_items(const int32_t *__restrict__ order, int64_t n_dense, int64_t n_hash,
-                             int64_t n_warp, const int64_t *__restrict__ nch_scan, int32_t l,
-                             const int32_t *__restrict__ cut, const int32_t *__restrict__ vbase,
-                             int2 *cta_items, int32_t *warp_items) {
+                             int64_t n_team, int64_t n_warp, const int64_t *__restrict__ nch_scan,
+                             int32_t l, const int32_t *__restrict__ cut,
+                             const int32_t *__restrict__ vbase, int2 *cta_items,
+                             int32_t *team_items, int32_t *warp_items) {
     const int64_t total_dense = nch_scan[n_dense];
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_dense + n_hash + n_warp;
+    const int64_t all = n_dense + n_hash + n_team + n_warp;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < all;
          i += (int64_t)gridDim.x * blockDim.x) {
         int32_t x = order[i];
         if (i < n_dense) {
@@ -302,15 +303,18 @@ __global__ void k_emit_items(const int32_t *__restrict__ order, int64_t n_dense,
             for (int32_t c = 0; c < k; ++c) cta_items[o + c] = make_int2(x, c);
         } else if (i < n_dense + n_hash) {
             cta_items[total_dense + (i - n_dense)] = make_int2(x, -1);
+        } else if (i < n_dense + n_hash + n_team) {
+            team_items[i - n_dense - n_hash] = x;
         } else {
-            warp_items[i - n_dense - n_hash] = x;
+            warp_items[i - n_dense - n_hash - n_team] = x;
         }
     }
 }
 
-__global__ void k_items_to_starts(const int2 *__restrict__ items, int64_t n, int32_t *starts) {
+// retry entries -(x+1): counted with dense chunks
+__global__ void k_items_to_dense_retries(const int2 *__restrict__ items, int64_t n, int32_t *starts) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) starts[i] = items[i].x;
+    if (i < n) starts[i] = -(items[i].x + 1);
 }
 
 // ----- chunk-boundary table for the dense bin ----------------------------------
@@ -424,10 +428,11 @@ __global__ void k_rows_from_off(const int64_t *__restrict__ off, int32_t n, int3
 // warp, CTA-hash and CTA-dense bins (dense starts into end-range chunks);
 // builds the chunk-boundary table when a dense start has several chunks.
 // `rows_star` (slot -> vertex of G*) may be null; it is rebuilt when needed.
-static int schedule_graph(Graph *g, cudaStream_t s, int32_t warp_max_work, int32_t hash_max_work,
-                          const int32_t *rows_star) {
+static int schedule_graph(Graph *g, cudaStream_t s, int32_t warp_max_work, int32_t team_max_work,
+                          int32_t hash_max_work, const int32_t *rows_star) {
     const int32_t r = g->r, l = g->l, n = g->n;
     const int64_t m = g->m;
+    const bool vpp = g->opt.orientation == 1;
     Allocs tmp;
     tmp.stream = s;
     struct TmpGuard { Allocs *a; ~TmpGuard() { a->release(); } } guard{&tmp};
@@ -440,12 +445,16 @@ static int schedule_graph(Graph *g, cudaStream_t s, int32_t warp_max_work, int32
         }                                                                             \
     } while (0)
     const uint64_t warp_max = (uint64_t)warp_max_work;
-    // Algorithm 3: ends concentrate on few high-priority vertices, so every
-    // start beyond the warp bin gets a CTA hash table; a start whose table
-    // fills up is counted again by the chunked retry pass
-    const uint64_t hash_max = g->opt.orientation == 1 ? ~0ull : (uint64_t)hash_max_work;
+    // Algorithm 3: ends concentrate on few high-priority vertices, so no start
+    // gets dense counters up front; every start beyond the warp bin gets a
+    // team or CTA hash table and one whose table fills up is re-queued
+    const uint64_t hash_max = vpp ? ~0ull : (uint64_t)hash_max_work;
+    const int32_t team_req = team_max_work >= 0 ? team_max_work : (vpp ? kTeamMaxWork : kTeamFitWork);
+    uint64_t team_max = std::max<uint64_t>((uint64_t)team_req, warp_max);
+    if (!vpp) team_max = std::min<uint64_t>(team_max, hash_max);
+    if (vpp && hash_max_work == 0) team_max = warp_max;   // all of them to the dense pass
     const uint64_t maxw = g->info.max_start_work;
-    int64_t n_dense = 0, n_hash = 0, n_warp = 0, n_items = 0, h_dense_items = 0;
+    int64_t n_dense = 0, n_hash = 0, n_team = 0, n_warp = 0, n_items = 0, h_dense_items = 0;
     if (n > 0 && g->info.wedges > 0) {
         const int64_t nn = (int64_t)n + 1;
         uint64_t *k0, *k1;
@@ -465,12 +474,12 @@ static int schedule_graph(Graph *g, cudaStream_t s, int32_t warp_max_work, int32
         BFC_CUDA(cudaGetLastError());
         BFC_CUDA(radix_sort_pairs(k0, v0, k1, v1, n, 0, bits_for(maxw), hist, hist_tmp, s, &which));
         const int32_t *order = which ? v1 : v0;
-        k_classify<<<grid_stride_blocks(n), kT, 0, s>>>(g->work, n, warp_max, hash_max, red); note_launch();
+        k_classify<<<grid_stride_blocks(n), kT, 0, s>>>(g->work, n, warp_max, team_max, hash_max, red); note_launch();
         BFC_CUDA(cudaGetLastError());
-        unsigned long long hc[3];
-        BFC_CUDA(cudaMemcpyAsync(hc, red, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+        unsigned long long hc[4];
+        BFC_CUDA(cudaMemcpyAsync(hc, red, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
         BFC_CUDA(cudaStreamSynchronize(s));
-        n_dense = (int64_t)hc[0]; n_hash = (int64_t)hc[1]; n_warp = (int64_t)hc[2];
+        n_dense = (int64_t)hc[0]; n_hash = (int64_t)hc[1]; n_team = (int64_t)hc[2]; n_warp = (int64_t)hc[3];
         if (n_dense > 0) {
             k_chunk_counts<<<blocks_for(n_dense), kT, 0, s>>>(order, n_dense, l, g->cut, g->vbase, nch); note_launch();
             BFC_CUDA(cudaGetLastError());
@@ -483,10 +492,12 @@ static int schedule_graph(Graph *g, cudaStream_t s, int32_t warp_max_work, int32
         BFC_CUDA(cudaStreamSynchronize(s));
         n_items = h_dense_items + n_hash;
         GET(g->mem, g->cta_items, std::max<int64_t>(n_items, 1));
+        GET(g->mem, g->team_items, std::max<int64_t>(n_team, 1));
         GET(g->mem, g->warp_items, std::max<int64_t>(n_warp, 1));
-        if (n_dense + n_hash + n_warp > 0) {
-            k_emit_items<<<grid_stride_blocks(n_dense + n_hash + n_warp), kT, 0, s>>>(
-                order, n_dense, n_hash, n_warp, nch_scan, l, g->cut, g->vbase, g->cta_items, g->warp_items); note_launch();
+        if (n_dense + n_hash + n_team + n_warp > 0) {
+            k_emit_items<<<grid_stride_blocks(n_dense + n_hash + n_team + n_warp), kT, 0, s>>>(
+                order, n_dense, n_hash, n_team, n_warp, nch_scan, l, g->cut, g->vbase, g->cta_items,
+                g->team_items, g->warp_items); note_launch();
             BFC_CUDA(cudaGetLastError());
         }
         // chunk boundaries of every list, so dense items read them instead of searching
@@ -512,43 +523,53 @@ static int schedule_graph(Graph *g, cudaStream_t s, int32_t warp_max_work, int32
         }
     } else {
         GET(g->mem, g->cta_items, 1);
+        GET(g->mem, g->team_items, 1);
         GET(g->mem, g->warp_items, 1);
     }
     g->n_cta_items = n_items;
+    g->n_team_items = n_team;
     g->n_warp_items = n_warp;
-    if (g->opt.orientation == 1) {
-        g->mem.drop(g->retry);
-        g->retry = nullptr;
-        g->retry_static = 0;
-        g->retry_cap = std::max<int64_t>(n_hash, 1);
-        GET(g->mem, g->retry, g->retry_cap);
-        if (hash_max_work == 0 && n_hash > 0) {
-            // every start beyond the warp bin goes to the dense pass directly
-            k_items_to_starts<<<blocks_for(n_hash), kT, 0, s>>>(g->cta_items, n_hash, g->retry); note_launch();
-            BFC_CUDA(cudaGetLastError());
-            g->retry_static = n_hash;
-            g->n_cta_items = 0;
-        }
+    g->team_max = (int32_t)std::min<uint64_t>(team_max, (uint64_t)kTeamMaxWork);
+    // each hash start is re-queued at most once per launch
+    g->mem.drop(g->retry);
+    g->retry = nullptr;
+    g->retry_static = 0;
+    g->retry_cap = std::max<int64_t>(n_hash + n_team, 1);
+    GET(g->mem, g->retry, g->retry_cap);
+    if (vpp && hash_max_work == 0 && n_hash > 0) {
+        // every start beyond the warp bin goes to the dense pass directly
+        k_items_to_dense_retries<<<blocks_for(n_hash), kT, 0, s>>>(g->cta_items, n_hash, g->retry); note_launch();
+        BFC_CUDA(cudaGetLastError());
+        g->retry_static = n_hash;
+        g->n_cta_items = 0;
     }
+    // Algorithm 2's tables always fit when a team start has at most 2,048
+    // wedges (4,096 slots) and a CTA start at most 16,384 (32,768 slots)
+    g->may_retry = vpp ? (n_hash + n_team > 0) : (n_team > 0 && team_max > (uint64_t)kTeamFitWork);
     g->info.dense_items = h_dense_items;
-    g->info.starts_with_work = n_dense + n_hash + n_warp;
+    g->info.starts_with_work = n_dense + n_hash + n_team + n_warp;
     g->info.dense_starts = n_dense;
     g->info.hash_starts = n_hash;
+    g->info.team_starts = n_team;
     g->info.warp_starts = n_warp;
     g->opt.warp_max_work = warp_max_work;
+    g->opt.team_max_work = team_max_work;
     g->opt.hash_max_work = hash_max_work;
     BFC_CUDA(cudaStreamSynchronize(s));
 #undef GET
     return BFC_OK;
 }
 
-int rebin_graph(Graph *g, cudaStream_t s, int32_t warp_max_work, int32_t hash_max_work) {
+int rebin_graph(Graph *g, cudaStream_t s, int32_t warp_max_work, int32_t team_max_work,
+                int32_t hash_max_work) {
     g->mem.stream = s;
     g->mem.drop(g->cta_items);
+    g->mem.drop(g->team_items);
     g->mem.drop(g->warp_items);
     g->cta_items = nullptr;
+    g->team_items = nullptr;
     g->warp_items = nullptr;
-    int rc = schedule_graph(g, s, warp_max_work, hash_max_work, nullptr);
+    int rc = schedule_graph(g, s, warp_max_work, team_max_work, hash_max_work, nullptr);
     g->info.device_bytes = (int64_t)g->mem.total;
     return rc;
 }
@@ -586,7 +607,7 @@ int prepare_graph(const bfc_csr *csr, const bfc_options *opt, cudaStream_t s, Gr
     GET(g->mem, g->plen, 2 * m);
     GET(g->mem, g->cut, n);
     GET(g->mem, g->work, n);
-    GET(g->mem, g->cursors, 4);
+    GET(g->mem, g->cursors, 8);
     GET(g->mem, g->acc, 2);
     GET(g->mem, g->pv, n);
     BFC_CUDA(cudaMemsetAsync(g->err, 0, 4 * sizeof(int), s));
@@ -783,7 +804,7 @@ int prepare_graph(const bfc_csr *csr, const bfc_options *opt, cudaStream_t s, Gr
 
     // ---- a5: heaviest-first order and bins
     {
-        int rc = schedule_graph(g, s, opt->warp_max_work, opt->hash_max_work, rows_star);
+        int rc = schedule_graph(g, s, opt->warp_max_work, opt->team_max_work, opt->hash_max_work, rows_star);
         if (rc) return rc;
     }
     g->info.num_u = r; g->info.num_l = l; g->info.num_edges = m;

@@ -144,6 +144,7 @@ int run_batch(bfc_server *sv, std::vector<Request *> &batch, cudaStream_t s,
     bfc_options_init(&opt);
     opt.warp_max_work = sv->cfg.warp_max_work > 0 ? sv->cfg.warp_max_work : opt.warp_max_work;
     opt.hash_max_work = sv->cfg.hash_max_work > 0 ? sv->cfg.hash_max_work : opt.hash_max_work;
+    opt.team_max_work = sv->cfg.team_max_work > 0 ? sv->cfg.team_max_work : opt.team_max_work;
     bfc_graph *h = nullptr;
     int rc = bfc_prepare_batch(&csr, &b, &opt, s, &h);
     if (rc) return rc;

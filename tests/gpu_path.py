@@ -17,6 +17,7 @@ def run_gpu(g, vertices=False, edges=False, options=None, export=False, device="
     G = ButterflyGraph(off, adj, g.num_u, g.num_l, options)
     try:
         out = dict(total=G.count(), info=G.info())
+        out["retries"] = int(G.export(bfc.BFC_RETRIES)[0])
         if vertices:
             pu, pl, t = G.count_vertices()
             out.update(pv_u=as_u64(pu), pv_l=as_u64(pl), total_v=t)

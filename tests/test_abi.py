@@ -38,8 +38,8 @@ def test_version_and_strings(bfc):
 
 def test_options_defaults(bfc):
     o = bfc.bfc_options_init()
-    assert (o.validate, o.warp_max_work, o.hash_max_work, o.num_ctas, o.wide_positions) == \
-        (1, 256, 16384, 0, 0)
+    assert (o.validate, o.warp_max_work, o.hash_max_work, o.num_ctas, o.wide_positions,
+            o.orientation, o.team_max_work) == (1, 256, 16384, 0, 0, 0, -1)
 
 
 def test_struct_layouts_match_header(bfc, tmp_path):
@@ -54,6 +54,9 @@ int main(void) {
   printf("%zu %zu %zu\\n", sizeof(bfc_csr), sizeof(bfc_options), sizeof(bfc_info));
   printf("%zu %zu %zu\\n", offsetof(bfc_csr, adj_u), offsetof(bfc_options, reserved),
          offsetof(bfc_info, max_deg_l));
+  printf("%zu %zu %zu\\n", offsetof(bfc_options, team_max_work), offsetof(bfc_info, team_starts),
+         sizeof(bfc_server_config));
+  printf("%zu %zu\\n", offsetof(bfc_server_config, team_max_work), sizeof(bfc_server_stats));
   return 0;
 }
 ''')
@@ -63,8 +66,11 @@ int main(void) {
     sizes = [int(x) for x in out]
     assert sizes[:3] == [ctypes.sizeof(bfc.bfc_csr), ctypes.sizeof(bfc.bfc_options),
                          ctypes.sizeof(bfc.bfc_info)]
-    assert sizes[3:] == [bfc.bfc_csr.adj_u.offset, bfc.bfc_options.reserved.offset,
-                         bfc.bfc_info.max_deg_l.offset]
+    assert sizes[3:6] == [bfc.bfc_csr.adj_u.offset, bfc.bfc_options.reserved.offset,
+                          bfc.bfc_info.max_deg_l.offset]
+    assert sizes[6:] == [bfc.bfc_options.team_max_work.offset, bfc.bfc_info.team_starts.offset,
+                         ctypes.sizeof(bfc.bfc_server_config), bfc.bfc_server_config.team_max_work.offset,
+                         ctypes.sizeof(bfc.bfc_server_stats)]
 
 
 @pytest.mark.parametrize("case", ["null", "negative", "too_many_edges", "bad_option", "null_ptr"])

@@ -50,7 +50,9 @@ def _count(h, nG):
 
 
 @pytest.mark.parametrize("opts", [{}, dict(warp_max_work=0, hash_max_work=0), dict(hash_max_work=256),
-                                  dict(orientation=1), dict(orientation=1, warp_max_work=0, hash_max_work=0)])
+                                  dict(warp_max_work=0, team_max_work=16384),
+                                  dict(orientation=1), dict(orientation=1, warp_max_work=0, hash_max_work=0),
+                                  dict(orientation=1, team_max_work=0)])
 def test_batch_totals_match_oracle(opts):
     from paper_1812_00283_gb300 import bfc
     graphs = _batch_graphs()

@@ -36,15 +36,22 @@ def _opts(**kw):
 BIN_SETTINGS = {
     "default": {},
     "all_dense": dict(warp_max_work=0, hash_max_work=0),
-    "hash_only": dict(warp_max_work=0, hash_max_work=16384),
+    "hash_only": dict(warp_max_work=0, team_max_work=0, hash_max_work=16384),
     "warp_heavy": dict(warp_max_work=256, hash_max_work=256),
+    "team_small": dict(warp_max_work=32, team_max_work=512, hash_max_work=4096),
+    # team tables may fill up: escalation to a CTA table in the retry pass
+    "team_only": dict(warp_max_work=0, team_max_work=16384, hash_max_work=16384),
     "wide_positions": dict(wide_positions=1),
     "all_dense_wide_positions": dict(warp_max_work=0, hash_max_work=0, wide_positions=1),
-    # Algorithm 3's orientation: hash tables with the chunked retry pass
+    "team_only_wide_positions": dict(warp_max_work=0, team_max_work=16384, hash_max_work=16384,
+                                     wide_positions=1),
+    # Algorithm 3's orientation: team / CTA hash tables with the retry pass
     "vpp": dict(orientation=1),
     "vpp_retry_all": dict(orientation=1, warp_max_work=0, hash_max_work=0),
     "vpp_retry_beyond_warp": dict(orientation=1, warp_max_work=256, hash_max_work=0),
     "vpp_no_warp": dict(orientation=1, warp_max_work=0),
+    "vpp_no_team": dict(orientation=1, team_max_work=0),
+    "vpp_team_small": dict(orientation=1, team_max_work=2048),
     "vpp_wide_positions": dict(orientation=1, wide_positions=1),
 }
 
@@ -168,6 +175,24 @@ def test_multi_chunk_retry_pass(wide):
     g = G.chung_lu_bipartite(230_000, 20_000, 900_000, 2.1, 2.1, 43)
     _check_against_oracle(g, _opts(orientation=1, warp_max_work=0, hash_max_work=0,
                                    wide_positions=wide))
+
+
+# Regular circulants on Sidon shift sets: starts at either end of the U order
+# have ~3p^2 distinct ends, more than a team table (3,072 at load 3/4) holds
+# for p = 37 and more than a CTA table (24,576) for p = 97.
+SIDON = {37: (37, 3000, 12000), 97: (97, 20000, 78000)}
+
+
+@pytest.mark.parametrize("p,mode,retries", [(37, "vpp", True), (37, "team_only", True),
+                                            (37, "vpp_team_small", False), (97, "vpp", True),
+                                            (97, "vpp_no_team", True), (97, "team_only", True)])
+def test_retry_escalation(p, mode, retries):
+    # team table full -> CTA table in the retry pass; CTA table full -> dense
+    # chunks of the end range (Algorithm 3), all bit-exact.  Team starts of at
+    # most 2,048 wedges always fit (vpp_team_small).
+    g = G.shifted_sidon_circulant(*SIDON[p])
+    got, ref = _check_against_oracle(g, _opts(**BIN_SETTINGS[mode]), edges=(p == 37))
+    assert (got["retries"] > 0) == retries
 
 
 def test_orientations_agree_on_wedges_and_work():

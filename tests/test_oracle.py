@@ -88,6 +88,28 @@ def test_complete_bipartite(a, b):
     assert oracle.vppp(g)[1] == y * c2(x)
 
 
+@pytest.mark.parametrize("p,c,n", [(5, 13, 60), (7, 40, 300), (11, 100, 700), (13, 7, 90)])
+def test_circulant_closed_form(p, c, n):
+    # U vertex x is joined to L vertex x + s (mod n) for s in a shift set S.
+    # Two U vertices at distance d share cnt(d) = #{(s, s') : s - s' = d mod n}
+    # neighbours, so ⋈ = (n / 2) * sum_{d != 0} C(cnt(d), 2) (each unordered
+    # pair is seen at d and at -d), and by rotation every vertex of either
+    # layer lies in 2 ⋈ / n butterflies.
+    g = G.shifted_sidon_circulant(p, c, n)
+    t = [2 * p * k + (k * k) % p for k in range(p)]
+    shifts = sorted({x % n for x in t} | {(x + c) % n for x in t})
+    cnt = [0] * n
+    for a in shifts:
+        for b in shifts:
+            cnt[(a - b) % n] += 1
+    tot = n * sum(c2(k) for k in cnt[1:]) // 2
+    r = oracle.vp(g, vertices=True, edges=True)
+    assert r["total"] == tot and tot > 0
+    assert np.all(r["pv_u"] == 2 * tot // n) and np.all(r["pv_l"] == 2 * tot // n)
+    assert int(r["pe"].sum()) == 4 * tot
+    assert oracle.vppp(g)[0] == tot
+
+
 @pytest.mark.parametrize("k", [3, 4, 5, 10])
 def test_long_cycles_have_none(k):
     g = G.cycle(k)
