@@ -286,11 +286,16 @@ def run_serve(args, rank, world):
     return 0
 
 
-def algorithmic_bytes(W: int, m: int, n: int) -> int:
+def algorithmic_bytes(W: int, m: int, n: int, outputs: str = "total") -> int:
     """Bytes the count must move at least once: 4 B per processed wedge (the
     end id), 12 B per oriented edge (middle id + the middle's offset), 12 B
-    per start (offset + cut)."""
-    return 4 * W + 12 * m + 12 * n
+    per start (offset + cut).  With per-vertex and per-edge outputs the
+    second walk reads every end again with its edge id (8 B per wedge) and
+    the outputs are written once (8 B per vertex and per edge)."""
+    B = 4 * W + 12 * m + 12 * n
+    if outputs == "all":
+        B += 8 * W + 8 * m + 8 * n
+    return B
 
 
 def measured_peaks() -> dict:
@@ -310,17 +315,21 @@ def count_kernel_hash() -> str:
     return h.hexdigest()
 
 
-def recorded_traffic(workload: str):
+def recorded_traffic(workload: str, outputs: str = "total"):
     """DRAM bytes per count launch from a committed ncu summary, if it was
-    taken on this workload with the current kernel source; else None."""
+    taken on this workload and outputs with the current kernel source (or
+    scaled from a smaller case of the same kernel, as the entry says); else
+    None."""
     p = os.path.join(ROOT, "profiles", "count_traffic.json")
     if not os.path.exists(p):
         return None
     with open(p) as f:
         d = json.load(f)
-    if d.get("source_sha256") != count_kernel_hash() or d.get("workload") != workload:
-        return None
-    return int(d["dram_bytes_per_launch"])
+    for e in d.get("entries", []):
+        if (e.get("source_sha256") == count_kernel_hash() and e.get("workload") == workload
+                and e.get("outputs", "total") == outputs):
+            return int(e["dram_bytes_per_launch"])
+    return None
 
 
 class ClockSampler:
@@ -388,31 +397,63 @@ def dist_setup():
     return rank, world, local
 
 
+def default_outputs(workload: str) -> str:
+    # the shopping workload is specified with per-vertex and per-edge counts
+    return "all" if workload == "shopping_300m" else "total"
+
+
+def oracle_run(g, outputs: str, threads: int) -> tuple[dict, float]:
+    import oracle
+    t0 = time.perf_counter()
+    r = oracle.vp(g, threads=threads, vertices=outputs == "all", edges=outputs == "all")
+    return r, time.perf_counter() - t0
+
+
+def oracle_sample(g, outputs: str, threads: int, target_s: float):
+    """A bounded sample of the workload for the CPU oracle: the whole graph
+    if one run fits target_s, else the subgraph of a seeded fraction of U
+    sized from a calibration run.  Returns (graph, fraction, one run's result
+    and seconds)."""
+    from bfc_inputs import generators as G
+    if g.num_edges <= 25_000_000:
+        r, dt = oracle_run(g, outputs, threads)
+        if dt <= 2 * target_s:
+            return g, 1.0, r, dt
+        f = max(1e-4, target_s / dt)
+    else:
+        f = min(1.0, 2e6 / g.num_edges)
+        s = G.sample_u(g, f, 77)
+        r, dt = oracle_run(s, outputs, threads)
+        f = min(1.0, f * target_s / max(dt, 1e-3))
+    s = G.sample_u(g, f, 77)
+    r, dt = oracle_run(s, outputs, threads)
+    return s, f, r, dt
+
+
+def sample_desc(workload: str, frac: float, sample, r: dict, outputs: str) -> str:
+    what = f"full {workload} graph" if frac == 1.0 else \
+        f"{workload} graph restricted to a seeded {100 * frac:.3g}% of U"
+    outs = "total + per-vertex + per-edge" if outputs == "all" else "total"
+    return f"{what}, {sample.num_edges} edges, W={r['wedges']}, {outs}; oracle incl. its own preparation"
+
+
 def run_reference(args, rank, world):
     """The CPU oracle (Algorithm 2 scheduled as Algorithm 5) timed on the
-    host cores, on the same workload."""
+    host cores, on the same workload (a bounded sample of it)."""
     if rank != 0:
         return 0
-    import numpy as np  # noqa: F401
-
-    import oracle
-    from bfc_inputs import generators as G
     g = make_graph(args.workload, 0, "cpu")
-    frac = 1.0 if args.steps + args.warmup <= 20 else 0.5
-    sample = g if frac == 1.0 else G.sample_u(g, frac, 77)
+    outputs = args.outputs or default_outputs(args.workload)
     threads = os.cpu_count() or 1
-    times, W = [], 0
+    per_step = min(10.0, 150.0 / (args.steps + args.warmup))
+    sample, frac, r, _ = oracle_sample(g, outputs, threads, per_step)
+    times, W = [], r["wedges"]
     for i in range(args.warmup + args.steps):
-        t0 = time.perf_counter()
-        r = oracle.vp(sample, threads=threads)
-        dt = time.perf_counter() - t0
-        W = r["wedges"]
+        r, dt = oracle_run(sample, outputs, threads)
         if i >= args.warmup:
             times.append(dt)
     v = W * len(times) / sum(times)
-    desc = (f"full {args.workload} graph" if frac == 1.0 else
-            f"{args.workload} graph restricted to a seeded {frac:.0%} of U")
-    desc += f", {sample.num_edges} edges, W={W}; oracle timed per step incl. its own preparation"
+    desc = sample_desc(args.workload, frac, sample, r, outputs) + "; timed per step"
     out = dict(metric=METRIC, value=v, unit=UNIT, impl="reference", n_gpus=world,
                steps=args.steps, warmup=args.warmup, ms_per_step=1e3 * statistics.mean(times),
                higher_is_better=True, scaling="weak", vs_baseline=None, dtype="u64",
@@ -433,6 +474,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--orientation", type=int, default=0, choices=[0, 1],
                     help="0 = Algorithm 2 (start highest), 1 = Algorithm 3 (end highest)")
+    ap.add_argument("--outputs", default=None, choices=["total", "all"],
+                    help="total only, or total + per-vertex + per-edge (default: all for shopping_300m)")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--batch-graphs", type=int, default=4096)
     ap.add_argument("--serve-pool", type=int, default=256)
@@ -470,6 +513,11 @@ def main():
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
     step_opts = bfc.bfc_options_init(orientation=args.orientation)
+    outputs = args.outputs or default_outputs(args.workload)
+    if outputs == "all":
+        per_u = torch.empty(max(r, 1), dtype=torch.int64, device=dev)
+        per_l = torch.empty(max(l, 1), dtype=torch.int64, device=dev)
+        per_e = torch.empty(max(m, 1), dtype=torch.int64, device=dev)
 
     def one_step(ev=None):
         if ev:
@@ -477,7 +525,10 @@ def main():
         h = bfc.bfc_prepare(r, l, m, off.data_ptr(), adj.data_ptr(), step_opts, sp)
         if ev:
             ev[1].record(stream)
-        bfc.bfc_count(h, sp, total.data_ptr())
+        if outputs == "all":
+            bfc.bfc_count_all(h, sp, per_u.data_ptr(), per_l.data_ptr(), per_e.data_ptr(), total.data_ptr())
+        else:
+            bfc.bfc_count(h, sp, total.data_ptr())
         if ev:
             ev[2].record(stream)
         info = bfc.bfc_graph_info(h)
@@ -531,17 +582,51 @@ def main():
 
     peaks = measured_peaks()
     cnt_s = statistics.median(count_ms) / 1e3
-    B = algorithmic_bytes(W, m, n)
+    B = algorithmic_bytes(W, m, n, outputs)
     achieved = B / cnt_s / 1e9
-    traffic = recorded_traffic(args.workload)
+    traffic = recorded_traffic(args.workload, outputs)
     roofline = dict(bound="hbm", achieved=achieved, peak=peaks["hbm_gbs"], unit="GB/s",
                     frac=achieved / peaks["hbm_gbs"], traffic=traffic,
-                    kernel="k_count (bfc_count)", peak_source=peaks["source"],
+                    kernel="k_count (bfc_count_all)" if outputs == "all" else "k_count (bfc_count)",
+                    peak_source=peaks["source"],
                     algorithmic_bytes_per_launch=B, count_ms_median=1e3 * cnt_s)
 
     # end to end through the C ABI from pinned host buffers
     e2e = None
-    if args.e2e_steps > 0:
+    if args.e2e_steps > 0 and outputs == "all":
+        # through the C ABI: H2D of the CSR, prepare, the combined count, D2H
+        # of the per-vertex and per-edge arrays and the total
+        off_h = torch.from_numpy(g.off_u).pin_memory()
+        adj_h = torch.from_numpy(g.adj_u).pin_memory()
+        pu_h = torch.empty(max(r, 1), dtype=torch.int64).pin_memory()
+        pl_h = torch.empty(max(l, 1), dtype=torch.int64).pin_memory()
+        pe_h = torch.empty(max(m, 1), dtype=torch.int64).pin_memory()
+        tot_h = torch.empty(1, dtype=torch.int64).pin_memory()
+        ts = []
+        for i in range(args.e2e_steps + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            off_d = off_h.to(dev, non_blocking=True)
+            adj_d = adj_h.to(dev, non_blocking=True)
+            h = bfc.bfc_prepare(r, l, m, off_d.data_ptr(), adj_d.data_ptr(), step_opts, sp)
+            bfc.bfc_count_all(h, sp, per_u.data_ptr(), per_l.data_ptr(), per_e.data_ptr(), total.data_ptr())
+            pu_h.copy_(per_u, non_blocking=True)
+            pl_h.copy_(per_l, non_blocking=True)
+            pe_h.copy_(per_e, non_blocking=True)
+            tot_h.copy_(total, non_blocking=True)
+            bfc.bfc_sync(h, sp)
+            ts.append(time.perf_counter() - t0)
+            bfc.bfc_release(h)
+            del off_d, adj_d
+            if (int(tot_h.item()) & ((1 << 64) - 1)) != expect:
+                raise SystemExit("end-to-end count disagrees with the device-resident count")
+        ts = ts[1:]
+        e2e = dict(value=W / statistics.median(ts), unit=UNIT,
+                   h2d_bytes_per_step=4 * (r + 1) + 4 * m, d2h_bytes_per_step=8 * (r + l + m) + 8,
+                   ms_per_step=1e3 * statistics.median(ts),
+                   note="H2D of the CSR from pinned memory, bfc_prepare, bfc_count_all, "
+                        "D2H of per-vertex, per-edge and total")
+    elif args.e2e_steps > 0:
         off_h = torch.from_numpy(g.off_u).pin_memory()
         adj_h = torch.from_numpy(g.adj_u).pin_memory()
         ts = []
@@ -561,16 +646,12 @@ def main():
     cpu = None
     verified = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        import oracle
         threads = os.cpu_count() or 1
-        t0 = time.perf_counter()
-        ref = oracle.vp(g, threads=threads)
-        dt = time.perf_counter() - t0
-        verified = (ref["total"] == expect and ref["wedges"] == W)
+        sample, frac, ref, dt = oracle_sample(g, outputs, threads, 15.0)
+        if frac == 1.0:
+            verified = (ref["total"] == expect and ref["wedges"] == W)
         cpu = dict(value=ref["wedges"] / dt, unit=UNIT, cores=threads, kind="oracle",
-                   sample=f"one run of the oracle on the full {args.workload} graph "
-                          f"({m} edges, W={ref['wedges']}), incl. its own preparation, "
-                          f"{dt:.1f} s")
+                   sample=sample_desc(args.workload, frac, sample, ref, outputs) + f", one run, {dt:.1f} s")
 
     if rank == 0:
         out = dict(
@@ -586,8 +667,11 @@ def main():
                         prepare_ms_median=statistics.median(prep_ms),
                         count_ms_median=statistics.median(count_ms),
                         count_only_wedges_per_s=W / cnt_s,
+                        outputs="total + per-vertex + per-edge (bfc_count_all)" if outputs == "all"
+                        else "total (bfc_count)",
                         bins=dict(dense_starts=info["dense_starts"], dense_items=info["dense_items"],
-                                  hash_starts=info["hash_starts"], warp_starts=info["warp_starts"]),
+                                  hash_starts=info["hash_starts"], team_starts=info["team_starts"],
+                                  warp_starts=info["warp_starts"]),
                         oracle_agrees=verified),
             roofline=roofline, cpu_baseline=cpu, e2e=e2e,
             gpu_launches=launches, clocks=clocks)

@@ -169,6 +169,14 @@ int bfc_count_vertices(bfc_graph *g, void *stream, uint64_t *per_u_dev, uint64_t
  * NULL.  Asynchronous; no allocation. */
 int bfc_count_edges(bfc_graph *g, void *stream, uint64_t *per_edge_dev, uint64_t *total_dev);
 
+/* Steps a8 and a9 together: the outputs of bfc_count_vertices and
+ * bfc_count_edges from ONE first walk and ONE second walk (Algorithm 4's
+ * pass attributes to vertices and edges at once).  per_u_dev / per_l_dev may
+ * be NULL; per_edge_dev may be NULL only when num_edges is 0.  Asynchronous;
+ * no allocation. */
+int bfc_count_all(bfc_graph *g, void *stream, uint64_t *per_u_dev, uint64_t *per_l_dev,
+                  uint64_t *per_edge_dev, uint64_t *total_dev);
+
 /* A batch of independent graphs given as one disjoint union: the union's
  * U-side CSR (bfc_csr; L ids global) plus, per graph g, its U vertices
  * [graph_u_start[g], graph_u_start[g+1]) and L vertices

@@ -151,6 +151,102 @@ int orc_brute_vertices(int32_t r, int32_t l, const int32_t *off, const int32_t *
     return 0;
 }
 
+/* Checks of the U-side CSR and its transpose (L-side lists of U ids, in no
+ * particular order) for the sampled counts. */
+static int transpose_u_side(int32_t r, int32_t l, const int32_t *off, const int32_t *adj,
+                            int64_t **loff_out, int32_t **lu_out) {
+    if (r < 0 || l < 0 || off == NULL || off[0] != 0) return -1;
+    for (int32_t u = 0; u < r; ++u)
+        if (off[u + 1] < off[u]) return -1;
+    const int64_t m = off[r];
+    if (m > 0 && adj == NULL) return -1;
+    int64_t *loff = calloc((size_t)l + 1, sizeof(int64_t));
+    int32_t *lu = malloc(sizeof(int32_t) * (size_t)(m + 1));
+    int64_t *fill = malloc(sizeof(int64_t) * (size_t)(l + 1));
+    if (!loff || !lu || !fill) { free(loff); free(lu); free(fill); return -2; }
+    for (int64_t e = 0; e < m; ++e) {
+        if (adj[e] < 0 || adj[e] >= l) { free(loff); free(lu); free(fill); return -1; }
+        loff[adj[e] + 1] += 1;
+    }
+    for (int32_t v = 0; v < l; ++v) loff[v + 1] += loff[v];
+    memcpy(fill, loff, sizeof(int64_t) * (size_t)(l + 1));
+    for (int32_t u = 0; u < r; ++u)
+        for (int64_t e = off[u]; e < off[u + 1]; ++e) lu[fill[adj[e]]++] = u;
+    free(fill);
+    *loff_out = loff;
+    *lu_out = lu;
+    return 0;
+}
+
+int orc_vertices_sampled(int32_t r, int32_t l, const int32_t *off, const int32_t *adj,
+                         int layer, const int32_t *xs, int64_t k, uint64_t *out) {
+    int64_t *loff;
+    int32_t *lu;
+    int rc = transpose_u_side(r, l, off, adj, &loff, &lu);
+    if (rc) return rc;
+    const int32_t nl = layer ? l : r;   /* size of x's layer */
+    uint32_t *c = calloc((size_t)nl + 1, sizeof(uint32_t));
+    int32_t *touched = malloc(sizeof(int32_t) * ((size_t)nl + 1));
+    if (!c || !touched) { free(c); free(touched); free(loff); free(lu); return -2; }
+    for (int64_t i = 0; i < k; ++i) {
+        const int32_t x = xs[i];
+        if (x < 0 || x >= nl) { rc = -1; break; }
+        int32_t nt = 0;
+        /* two-hop paths x - v - y: U side goes through off/adj then the
+         * transpose, L side the other way round */
+        const int64_t b = layer ? loff[x] : off[x], e = layer ? loff[x + 1] : off[x + 1];
+        for (int64_t j = b; j < e; ++j) {
+            const int32_t v = layer ? lu[j] : adj[j];
+            const int64_t b2 = layer ? off[v] : loff[v], e2 = layer ? off[v + 1] : loff[v + 1];
+            for (int64_t t = b2; t < e2; ++t) {
+                const int32_t y = layer ? adj[t] : lu[t];
+                if (y == x) continue;
+                if (c[y]++ == 0) touched[nt++] = y;
+            }
+        }
+        uint64_t sum = 0;
+        for (int32_t t = 0; t < nt; ++t) { sum += choose2(c[touched[t]]); c[touched[t]] = 0; }
+        out[i] = sum;
+    }
+    free(c); free(touched); free(loff); free(lu);
+    return rc;
+}
+
+int orc_edges_sampled(int32_t r, int32_t l, const int32_t *off, const int32_t *adj,
+                      const int64_t *es, int64_t k, uint64_t *out) {
+    int64_t *loff;
+    int32_t *lu;
+    int rc = transpose_u_side(r, l, off, adj, &loff, &lu);
+    if (rc) return rc;
+    const int64_t m = off[r];
+    unsigned char *mark = calloc((size_t)l + 1, 1);
+    if (!mark) { free(loff); free(lu); return -2; }
+    for (int64_t i = 0; i < k; ++i) {
+        const int64_t e = es[i];
+        if (e < 0 || e >= m) { rc = -1; break; }
+        /* owner u of slot e: the last u with off[u] <= e */
+        int32_t lo = 0, hi = r;
+        while (hi - lo > 1) {
+            const int32_t mid = lo + (hi - lo) / 2;
+            if (off[mid] <= e) lo = mid; else hi = mid;
+        }
+        const int32_t u = lo, v = adj[e];
+        for (int64_t j = off[u]; j < off[u + 1]; ++j) mark[adj[j]] = 1;
+        uint64_t sum = 0;
+        for (int64_t j = loff[v]; j < loff[v + 1]; ++j) {
+            const int32_t w = lu[j];
+            if (w == u) continue;
+            uint64_t cw = 0;   /* |N(u) ∩ N(w)|, at least 1 (v) */
+            for (int64_t t = off[w]; t < off[w + 1]; ++t) cw += mark[adj[t]];
+            sum += cw - 1;
+        }
+        for (int64_t j = off[u]; j < off[u + 1]; ++j) mark[adj[j]] = 0;
+        out[i] = sum;
+    }
+    free(mark); free(loff); free(lu);
+    return rc;
+}
+
 int orc_brute_edges(int32_t r, int32_t l, const int32_t *off, const int32_t *adj, uint64_t *pe) {
     graph_t g;
     int rc = graph_build(r, l, off, adj, &g);

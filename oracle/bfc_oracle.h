@@ -44,6 +44,19 @@ int orc_brute_vertices(int32_t r, int32_t l, const int32_t *off, const int32_t *
 int orc_brute_edges(int32_t r, int32_t l, const int32_t *off, const int32_t *adj,
                     uint64_t *pe);
 
+/* Eq. 1 for the listed vertices only, for graphs too large for the loops
+ * above: for x, every two-hop path x - v - y with y != x adds one to
+ * c_y = |N(x) ∩ N(y)|, and ⋈_x = Σ_y C(c_y, 2).  layer 0: xs are U ids,
+ * layer 1: L ids.  out[i] belongs to xs[i].  O(m + Σ two-hop paths). */
+int orc_vertices_sampled(int32_t r, int32_t l, const int32_t *off, const int32_t *adj,
+                         int layer, const int32_t *xs, int64_t k, uint64_t *out);
+
+/* Eq. 7 for the listed edges only (U-side slots es[i]): for e = (u, v),
+ * ⋈_e = Σ_{w ∈ N(v), w ≠ u} (|N(u) ∩ N(w)| − 1), with N(u) marked once and
+ * each |N(u) ∩ N(w)| counted over N(w).  out[i] belongs to es[i]. */
+int orc_edges_sampled(int32_t r, int32_t l, const int32_t *off, const int32_t *adj,
+                      const int64_t *es, int64_t k, uint64_t *out);
+
 /* Algorithm 1 (BFC-IBS, layer priority).  The start layer S is U unless
  * Σ_U deg² < Σ_L deg², in which case S = L; wedges (u, v, w) with
  * w.id > u.id are hashed per start; total = Σ C(count, 2).  *wedges = number

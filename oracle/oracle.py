@@ -52,6 +52,9 @@ def _load():
                 "orc_brute_total": [c.c_int32, c.c_int32, _i32p, _i32p, c.c_int, _u64p],
                 "orc_brute_vertices": [c.c_int32, c.c_int32, _i32p, _i32p, _u64p, _u64p],
                 "orc_brute_edges": [c.c_int32, c.c_int32, _i32p, _i32p, _u64p],
+                "orc_vertices_sampled": [c.c_int32, c.c_int32, _i32p, _i32p, c.c_int, _i32p,
+                                         c.c_int64, _u64p],
+                "orc_edges_sampled": [c.c_int32, c.c_int32, _i32p, _i32p, _i64p, c.c_int64, _u64p],
                 "orc_ibs": [c.c_int32, c.c_int32, _i32p, _i32p, _u64p, _u64p, c.POINTER(c.c_int)],
                 "orc_priority": [c.c_int32, c.c_int32, _i32p, _i32p, _i32p, _i32p, _i32p],
                 "orc_projection": [c.c_int32, c.c_int32, _i32p, _i32p, _i64p, _i32p, _i32p,
@@ -114,6 +117,27 @@ def brute_edges(g) -> np.ndarray:
     _check(_load().orc_brute_edges(g.num_u, g.num_l, _p(off, _i32p), _p(adj, _i32p),
                                    _p(pe, _u64p)), "brute_edges")
     return pe[:g.num_edges]
+
+
+def vertices_sampled(g, layer: int, xs) -> np.ndarray:
+    """Eq. 1 for the listed vertices of one layer (0 = U, 1 = L), by counting
+    two-hop paths; for graphs too large for the full oracle."""
+    off, adj = _csr(g)
+    xs = np.ascontiguousarray(np.asarray(xs, dtype=np.int32))
+    out = np.zeros(max(xs.size, 1), dtype=np.uint64)
+    _check(_load().orc_vertices_sampled(g.num_u, g.num_l, _p(off, _i32p), _p(adj, _i32p), int(layer),
+                                        _p(xs, _i32p), xs.size, _p(out, _u64p)), "vertices_sampled")
+    return out[:xs.size]
+
+
+def edges_sampled(g, es) -> np.ndarray:
+    """Eq. 7 for the listed edges (U-side slots)."""
+    off, adj = _csr(g)
+    es = np.ascontiguousarray(np.asarray(es, dtype=np.int64))
+    out = np.zeros(max(es.size, 1), dtype=np.uint64)
+    _check(_load().orc_edges_sampled(g.num_u, g.num_l, _p(off, _i32p), _p(adj, _i32p),
+                                     _p(es, _i64p), es.size, _p(out, _u64p)), "edges_sampled")
+    return out[:es.size]
 
 
 def ibs(g) -> tuple[int, int, int]:

@@ -94,6 +94,19 @@ class ButterflyGraph:
         bfc.bfc_sync(self._h, sp)
         return pe[:self.num_edges], int(self._total.item()) & ((1 << 64) - 1)
 
+    def count_all(self, stream=None):
+        """Returns (per_u, per_l, per_edge, total) from one combined pass."""
+        import torch
+        pu = torch.empty(max(self.num_u, 1), dtype=torch.int64, device=self.device)
+        pl = torch.empty(max(self.num_l, 1), dtype=torch.int64, device=self.device)
+        pe = torch.empty(max(self.num_edges, 1), dtype=torch.int64, device=self.device)
+        sp, _ = _stream(stream)
+        bfc = _lib()
+        bfc.bfc_count_all(self._h, sp, pu.data_ptr(), pl.data_ptr(), pe.data_ptr(), self._total.data_ptr())
+        bfc.bfc_sync(self._h, sp)
+        return (pu[:self.num_u], pl[:self.num_l], pe[:self.num_edges],
+                int(self._total.item()) & ((1 << 64) - 1))
+
     def info(self) -> dict:
         return _lib().bfc_graph_info(self._h)
 

@@ -85,6 +85,7 @@ _SIGS = {
     "bfc_count": (c_int, [c_void_p, c_void_p, c_void_p]),
     "bfc_count_vertices": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "bfc_count_edges": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "bfc_count_all": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "bfc_sync": (c_int, [c_void_p, c_void_p]),
     "bfc_graph_info": (c_int, [c_void_p, ctypes.POINTER(bfc_info)]),
     "bfc_export": (c_int, [c_void_p, c_int, c_void_p, c_void_p]),
@@ -160,6 +161,11 @@ def bfc_count_vertices(g: int, stream: int, per_u_dev: int | None, per_l_dev: in
 
 def bfc_count_edges(g: int, stream: int, per_edge_dev: int, total_dev: int | None):
     _check(_lib.bfc_count_edges(g, stream, per_edge_dev, total_dev), "bfc_count_edges")
+
+
+def bfc_count_all(g: int, stream: int, per_u_dev: int | None, per_l_dev: int | None,
+                  per_edge_dev: int, total_dev: int | None):
+    _check(_lib.bfc_count_all(g, stream, per_u_dev, per_l_dev, per_edge_dev, total_dev), "bfc_count_all")
 
 
 def bfc_sync(g: int, stream: int = 0):

@@ -171,23 +171,24 @@ int bfc_prepare(const bfc_csr *csr, const bfc_options *opt_in, void *stream, bfc
 }
 
 static int count_common(bfc_graph *h, void *stream, int mode, uint64_t *per_a, uint64_t *per_b,
-                        uint64_t *total_dev) {
+                        uint64_t *total_dev, uint64_t *per_edge = nullptr) {
     bfc::set_last_error("");
     if (!h) { bfc::set_last_error("null graph"); return BFC_ERR_INVALID_ARGUMENT; }
     Graph *g = &h->g;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     g->stream = s;
     unsigned long long *pv = nullptr, *pe = nullptr;
-    if (mode == bfc::kModeVertices) {
+    if (bfc::wants_vertices(mode)) {
         pv = g->pv;
         BFC_CUDA(cudaMemsetAsync(pv, 0, sizeof(unsigned long long) * (size_t)(g->n > 0 ? g->n : 1), s));
-    } else if (mode == bfc::kModeEdges) {
-        pe = reinterpret_cast<unsigned long long *>(per_a);
+    }
+    if (bfc::wants_edges(mode)) {
+        pe = reinterpret_cast<unsigned long long *>(mode == bfc::kModeEdges ? per_a : per_edge);
         if (g->m > 0) BFC_CUDA(cudaMemsetAsync(pe, 0, sizeof(uint64_t) * (size_t)g->m, s));
     }
     int rc = bfc::launch_count(g, s, mode, pv, pe);
     if (rc) return rc;
-    if (mode == bfc::kModeVertices) {
+    if (bfc::wants_vertices(mode)) {
         rc = bfc::gather_vertices(g, s, per_a, per_b);
         if (rc) return rc;
     }
@@ -325,6 +326,15 @@ int bfc_count_edges(bfc_graph *g, void *stream, uint64_t *per_edge_dev, uint64_t
         bfc::set_last_error("null per_edge_dev"); return BFC_ERR_INVALID_ARGUMENT;
     }
     return count_common(g, stream, bfc::kModeEdges, per_edge_dev, nullptr, total_dev);
+}
+
+int bfc_count_all(bfc_graph *g, void *stream, uint64_t *per_u_dev, uint64_t *per_l_dev,
+                  uint64_t *per_edge_dev, uint64_t *total_dev) {
+    if (!g) { bfc::set_last_error("null graph"); return BFC_ERR_INVALID_ARGUMENT; }
+    if (!per_edge_dev && g->g.m > 0) {
+        bfc::set_last_error("null per_edge_dev"); return BFC_ERR_INVALID_ARGUMENT;
+    }
+    return count_common(g, stream, bfc::kModeAll, per_u_dev, per_l_dev, total_dev, per_edge_dev);
 }
 
 int bfc_sync(bfc_graph *h, void *stream) {

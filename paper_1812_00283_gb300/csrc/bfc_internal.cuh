@@ -198,9 +198,12 @@ cudaError_t reduce_max_u64(const uint64_t *in, int64_t n, unsigned long long *ou
 int prepare_graph(const bfc_csr *csr, const bfc_options *opt, cudaStream_t s, Graph *g,
                   int32_t num_graphs = 0, const int32_t *graph_u_start = nullptr,
                   const int32_t *graph_l_start = nullptr);
-// kModeBatch = total plus per-graph totals for a batch prepared as a disjoint union
-enum CountMode { kModeTotal = 0, kModeVertices = 1, kModeEdges = 2, kModeBatch = 3 };
-__host__ __device__ constexpr bool has_second_walk(int mode) { return mode == kModeVertices || mode == kModeEdges; }
+// kModeBatch = total plus per-graph totals for a batch prepared as a disjoint union;
+// kModeAll = per-vertex and per-edge counts from one first walk and one second walk
+enum CountMode { kModeTotal = 0, kModeVertices = 1, kModeEdges = 2, kModeBatch = 3, kModeAll = 4 };
+__host__ __device__ constexpr bool wants_vertices(int mode) { return mode == kModeVertices || mode == kModeAll; }
+__host__ __device__ constexpr bool wants_edges(int mode) { return mode == kModeEdges || mode == kModeAll; }
+__host__ __device__ constexpr bool has_second_walk(int mode) { return wants_vertices(mode) || wants_edges(mode); }
 int launch_count(Graph *g, cudaStream_t s, int mode, unsigned long long *pv_proj,
                  unsigned long long *pe, unsigned long long *gtot = nullptr);
 int rebin_graph(Graph *g, cudaStream_t s, int32_t warp_max_work, int32_t team_max_work,

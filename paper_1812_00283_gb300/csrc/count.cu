@@ -268,7 +268,7 @@ __device__ __forceinline__ unsigned long long wedge_op(const CountParams &p, int
     }
     const unsigned long long delta = (unsigned long long)c - 1ull;
     if (delta) {
-        if (MODE == kModeEdges) atomicAdd(p.pe + __ldg(p.eid + pos), delta);
+        if (wants_edges(MODE)) atomicAdd(p.pe + __ldg(p.eid + pos), delta);
         atomicAdd(msum + q, delta);
     }
     return 0;
@@ -411,8 +411,8 @@ __device__ unsigned long long team_walk(const CountParams &p, int32_t x, int32_t
                 if (len[i] > 0) {
                     const unsigned long long dsum = sh.msum[nzs[i]];
                     if (dsum) {
-                        if (MODE == kModeVertices) atomicAdd(p.pv + v[i], dsum);
-                        if (MODE == kModeEdges) atomicAdd(p.pe + __ldg(p.eid + e[i]), dsum);
+                        if (wants_vertices(MODE)) atomicAdd(p.pv + v[i], dsum);
+                        if (wants_edges(MODE)) atomicAdd(p.pe + __ldg(p.eid + e[i]), dsum);
                     }
                 }
             }
@@ -435,7 +435,7 @@ __device__ unsigned long long item_body(const CountParams &p, int32_t x, int32_t
     }
     if (has_second_walk(MODE)) {
         t.sync();
-        if (MODE == kModeVertices) {
+        if (wants_vertices(MODE)) {
             // ends: each pair (x, w) adds C(count, 2) to ⋈_w
             if (KIND == kHash) {
                 const int32_t *hkeys = reinterpret_cast<const int32_t *>(ctr);
@@ -456,7 +456,7 @@ __device__ unsigned long long item_body(const CountParams &p, int32_t x, int32_t
             }
         }
         team_walk<MODE, KIND, true, Pos>(p, x, lb, lo, hi, flags, hmask, ctr, sh, t);
-        if (MODE == kModeVertices) {
+        if (wants_vertices(MODE)) {
             const unsigned long long s = team_sum(acc, sh, t);
             if (t.tid == 0 && s) atomicAdd(p.pv + x, s);
         }
@@ -659,7 +659,7 @@ __device__ unsigned long long warp_walk(const CountParams &p, int32_t x, int32_t
                 } else {
                     const unsigned long long delta = (unsigned long long)cnt[slot] - 1ull;
                     if (delta) {
-                        if (MODE == kModeEdges) atomicAdd(p.pe + __ldg(p.eid + pos), delta);
+                        if (wants_edges(MODE)) atomicAdd(p.pe + __ldg(p.eid + pos), delta);
                         atomicAdd(msum + q, delta);
                     }
                 }
@@ -669,8 +669,8 @@ __device__ unsigned long long warp_walk(const CountParams &p, int32_t x, int32_t
         if (kSecond && len > 0) {
             const unsigned long long dsum = msum[nz];
             if (dsum) {
-                if (MODE == kModeVertices) atomicAdd(p.pv + v, dsum);
-                if (MODE == kModeEdges) atomicAdd(p.pe + __ldg(p.eid + e), dsum);
+                if (wants_vertices(MODE)) atomicAdd(p.pv + v, dsum);
+                if (wants_edges(MODE)) atomicAdd(p.pe + __ldg(p.eid + e), dsum);
             }
         }
         __syncwarp();
@@ -702,14 +702,14 @@ __device__ unsigned long long warp_item(const CountParams &p, int32_t x, unsigne
     unsigned long long acc = warp_walk<MODE, false>(p, x, lb, cap - 1, keys, cnt, msum, wstart, wsrc);
     if (has_second_walk(MODE)) {
         __syncwarp();
-        if (MODE == kModeVertices) {
+        if (wants_vertices(MODE)) {
             for (uint32_t s = lane; s < cap; s += 32) {
                 const int32_t k = keys[s];
                 if (k >= 0 && cnt[s] >= 2) atomicAdd(p.pv + lb + k, c2(cnt[s]));
             }
         }
         warp_walk<MODE, true>(p, x, lb, cap - 1, keys, cnt, msum, wstart, wsrc);
-        if (MODE == kModeVertices) {
+        if (wants_vertices(MODE)) {
             unsigned long long t = acc;
 #pragma unroll
             for (int d = 16; d > 0; d >>= 1) t += __shfl_xor_sync(0xffffffffu, t, d);
@@ -837,6 +837,7 @@ void launch_main(int mode, int grid, cudaStream_t s, const CountParams &p) {
     if (mode == kModeTotal) k_count<kModeTotal, Pos><<<grid, kCountThreads, kCounterBytes, s>>>(p);
     else if (mode == kModeBatch) k_count<kModeBatch, Pos><<<grid, kCountThreads, kCounterBytes, s>>>(p);
     else if (mode == kModeVertices) k_count<kModeVertices, Pos><<<grid, kCountThreads, kCounterBytes, s>>>(p);
+    else if (mode == kModeAll) k_count<kModeAll, Pos><<<grid, kCountThreads, kCounterBytes, s>>>(p);
     else k_count<kModeEdges, Pos><<<grid, kCountThreads, kCounterBytes, s>>>(p);
 }
 
@@ -845,6 +846,7 @@ void launch_retry(int mode, int grid, cudaStream_t s, const CountParams &p) {
     if (mode == kModeTotal) k_count_retry<kModeTotal, Pos><<<grid, kCountThreads, kCounterBytes, s>>>(p);
     else if (mode == kModeBatch) k_count_retry<kModeBatch, Pos><<<grid, kCountThreads, kCounterBytes, s>>>(p);
     else if (mode == kModeVertices) k_count_retry<kModeVertices, Pos><<<grid, kCountThreads, kCounterBytes, s>>>(p);
+    else if (mode == kModeAll) k_count_retry<kModeAll, Pos><<<grid, kCountThreads, kCounterBytes, s>>>(p);
     else k_count_retry<kModeEdges, Pos><<<grid, kCountThreads, kCounterBytes, s>>>(p);
 }
 
@@ -862,6 +864,8 @@ int count_smem_setup(int device) {
     BFC_CUDA((setup_one<kModeVertices, long long>()));
     BFC_CUDA((setup_one<kModeEdges, long long>()));
     BFC_CUDA((setup_one<kModeBatch, long long>()));
+    BFC_CUDA((setup_one<kModeAll, int32_t>()));
+    BFC_CUDA((setup_one<kModeAll, long long>()));
     done[device] = true;
     return BFC_OK;
 }

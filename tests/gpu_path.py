@@ -24,6 +24,10 @@ def run_gpu(g, vertices=False, edges=False, options=None, export=False, device="
         if edges:
             pe, t = G.count_edges()
             out.update(pe=as_u64(pe), total_e=t)
+        if vertices and edges:
+            # the combined pass must give exactly the separate passes' outputs
+            pu, pl, pe, t = G.count_all()
+            out.update(all_pv_u=as_u64(pu), all_pv_l=as_u64(pl), all_pe=as_u64(pe), total_all=t)
         if export:
             out["rank_u"] = G.export(bfc.BFC_RANK_U).cpu().numpy()
             out["rank_l"] = G.export(bfc.BFC_RANK_L).cpu().numpy()

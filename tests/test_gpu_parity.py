@@ -68,6 +68,10 @@ def _check_against_oracle(g, opts=None, vertices=True, edges=True):
     if edges:
         assert got["total_e"] == ref["total"]
         assert np.array_equal(got["pe"], ref["pe"])
+    if vertices and edges:
+        assert got["total_all"] == ref["total"]
+        assert np.array_equal(got["all_pv_u"], ref["pv_u"]) and np.array_equal(got["all_pv_l"], ref["pv_l"])
+        assert np.array_equal(got["all_pe"], ref["pe"])
     return got, ref
 
 

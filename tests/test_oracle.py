@@ -207,6 +207,35 @@ def test_tiny_graphs_against_enumeration(seed):
     assert np.array_equal(oracle.brute_edges(g), ref["pe"])
     assert oracle.ibs(g)[0] == ref["total"]
     assert oracle.vppp(g)[0] == ref["total"]
+    # the sampled forms of Eq. 1 and Eq. 7 for every vertex and edge
+    assert np.array_equal(oracle.vertices_sampled(g, 0, np.arange(g.num_u)), ref["pv_u"])
+    assert np.array_equal(oracle.vertices_sampled(g, 1, np.arange(g.num_l)), ref["pv_l"])
+    assert np.array_equal(oracle.edges_sampled(g, np.arange(g.num_edges)), ref["pe"])
+
+
+@pytest.mark.parametrize("a,b", [(2, 2), (3, 5), (6, 4)])
+def test_sampled_closed_forms(a, b):
+    g = G.complete_bipartite(a, b)
+    assert np.all(oracle.vertices_sampled(g, 0, np.arange(a)) == (a - 1) * c2(b))
+    assert np.all(oracle.vertices_sampled(g, 1, np.arange(b)) == (b - 1) * c2(a))
+    assert np.all(oracle.edges_sampled(g, np.arange(a * b)) == (a - 1) * (b - 1))
+    # any order, repeats allowed
+    assert list(oracle.vertices_sampled(g, 1, [b - 1, 0, b - 1])) == [(b - 1) * c2(a)] * 3
+    with pytest.raises(ValueError):
+        oracle.vertices_sampled(g, 0, [a])
+    with pytest.raises(ValueError):
+        oracle.edges_sampled(g, [a * b])
+
+
+def test_sampled_on_larger_graph_agrees_with_full_oracle():
+    g = G.chung_lu_bipartite(3000, 1500, 40000, 2.1, 2.1, 16)
+    ref = oracle.vp(g, vertices=True, edges=True)
+    xs = np.arange(0, g.num_u, 7)
+    ys = np.arange(0, g.num_l, 5)
+    es = np.arange(0, g.num_edges, 13)
+    assert np.array_equal(oracle.vertices_sampled(g, 0, xs), ref["pv_u"][xs])
+    assert np.array_equal(oracle.vertices_sampled(g, 1, ys), ref["pv_l"][ys])
+    assert np.array_equal(oracle.edges_sampled(g, es), ref["pe"][es])
 
 
 # ---------------------------------------------------------------------------
