@@ -36,7 +36,7 @@ def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="powerlaw_20m")
     ap.add_argument("--repeat", type=int, default=1)
-    ap.add_argument("--mode", default="total", choices=["total", "vertices", "edges"])
+    ap.add_argument("--mode", default="total", choices=["total", "vertices", "edges", "all"])
     ap.add_argument("--warp-max-work", type=int, default=None)
     ap.add_argument("--hash-max-work", type=int, default=None)
     ap.add_argument("--team-max-work", type=int, default=None)
@@ -78,8 +78,10 @@ def main(argv=None):
             bfc.bfc_count(h, sp, total.data_ptr())
         elif args.mode == "vertices":
             bfc.bfc_count_vertices(h, sp, pu.data_ptr(), pl.data_ptr(), total.data_ptr())
-        else:
+        elif args.mode == "edges":
             bfc.bfc_count_edges(h, sp, pe.data_ptr(), total.data_ptr())
+        else:
+            bfc.bfc_count_all(h, sp, pu.data_ptr(), pl.data_ptr(), pe.data_ptr(), total.data_ptr())
         e1.record(s)
         torch.cuda.synchronize()
         times.append(e0.elapsed_time(e1))

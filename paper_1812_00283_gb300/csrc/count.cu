@@ -231,13 +231,12 @@ enum CounterKind { kDenseNarrow = 0, kDenseWide = 1, kHash = 2 };
 
 // The counter operation for one wedge whose end id is w and whose end sits at
 // adjacency slot pos.  First walk: increment count_wedge(w), return the old
-// value.  Second walk: read the final count and attribute δ = count − 1 to the
-// edge (middle, w) and to the middle's batch sum.
+// value.  Second walk: read the final count, attribute δ = count − 1 to the
+// edge (middle, w) and return δ for the middle's batch sum.
 template <int MODE, int KIND, bool kSecond, typename Pos>
 __device__ __forceinline__ unsigned long long wedge_op(const CountParams &p, int32_t w, Pos pos,
-                                                       int q, int32_t lb, int32_t lo, int32_t span,
-                                                       uint32_t hmask, unsigned char *ctr,
-                                                       unsigned long long *msum, int *ovf,
+                                                       int32_t lb, int32_t lo, int32_t span,
+                                                       uint32_t hmask, unsigned char *ctr, int *ovf,
                                                        int *ins) {
     uint32_t *w32 = reinterpret_cast<uint32_t *>(ctr);
     uint32_t c;
@@ -266,12 +265,25 @@ __device__ __forceinline__ unsigned long long wedge_op(const CountParams &p, int
         if (!kSecond) return (KIND == kDenseWide) ? atomicAdd(w32 + idx, 1u) : inc16(w32, idx);
         c = (KIND == kDenseWide) ? w32[idx] : get16(w32, idx);
     }
+    // δ = count − 1 for the edge (middle, w); the caller sums it per middle
     const unsigned long long delta = (unsigned long long)c - 1ull;
-    if (delta) {
-        if (wants_edges(MODE)) atomicAdd(p.pe + __ldg(p.eid + pos), delta);
-        atomicAdd(msum + q, delta);
+    if (wants_edges(MODE) && delta) atomicAdd(p.pe + __ldg(p.eid + pos), delta);
+    return delta;
+}
+
+// Adds each lane's x to msum[q], where equal q occupy consecutive lanes (the
+// runs of a window are contiguous): a segmented scan over the warp leaves
+// each run's sum in its last lane, which makes the one shared atomic.
+template <typename T>
+__device__ __forceinline__ void run_add(unsigned long long *msum, int q, T x, int lane) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const T t = __shfl_up_sync(0xffffffffu, x, o);
+        const int qq = __shfl_up_sync(0xffffffffu, q, o);
+        if (lane >= o && qq == q) x += t;
     }
-    return 0;
+    const int qn = __shfl_down_sync(0xffffffffu, q, 1);
+    if ((lane == 31 || qn != q) && x) atomicAdd(msum + q, (unsigned long long)x);
 }
 
 // One walk over the wedges of start x whose ends fall in [lb+lo, lb+hi).
@@ -396,10 +408,21 @@ __device__ unsigned long long team_walk(const CountParams &p, int32_t x, int32_t
                     w[u] = ok[u] ? __ldg(p.adj + pos[u]) : 0;
                 }
 #pragma unroll
-                for (int u = 0; u < kU; ++u)
-                    if (ok[u])
-                        acc += wedge_op<MODE, KIND, kSecond, Pos>(p, w[u], pos[u], q[u], lb, lo, span, hmask,
-                                                                  ctr, sh.msum, &sh.overflow, &sh.inserts);
+                for (int u = 0; u < kU; ++u) {
+                    if (!kSecond) {
+                        if (ok[u])
+                            acc += wedge_op<MODE, KIND, false, Pos>(p, w[u], pos[u], lb, lo, span, hmask,
+                                                                    ctr, &sh.overflow, &sh.inserts);
+                    } else if (wb + u < wend) {   // warp-uniform: all lanes take part in run_add
+                        const unsigned long long d =
+                            ok[u] ? wedge_op<MODE, KIND, true, Pos>(p, w[u], pos[u], lb, lo, span, hmask,
+                                                                    ctr, &sh.overflow, &sh.inserts)
+                                  : 0ull;
+                        // 16-bit counts keep a window's δ sum below 2^21
+                        if (KIND == kDenseWide) run_add<unsigned long long>(sh.msum, q[u], d, lane);
+                        else run_add<uint32_t>(sh.msum, q[u], (uint32_t)d, lane);
+                    }
+                }
                 k0 += 32 * kU;
             }
         }
@@ -646,24 +669,26 @@ __device__ unsigned long long warp_walk(const CountParams &p, int32_t x, int32_t
             const int q = q0 + __popc(m & le_mask);
             q0 += __popc(__ballot_sync(0xffffffffu, d <= 32));
             const int32_t k = k0 + lane;
+            uint32_t delta = 0;
             if (k < total) {
                 const long long pos = wsrc[q] + k;
+                bool good = true;
 #if BFC_CHECKED
-                if (pos < 0 || pos >= p.adj_len) { atomicOr(p.err, kErrBounds); continue; }
+                if (pos < 0 || pos >= p.adj_len) { atomicOr(p.err, kErrBounds); good = false; }
 #endif
-                const int32_t w = __ldg(p.adj + pos);
-                const int slot = hash_find(keys, mask, w - lb, !kSecond);
-                if (slot < 0) { atomicOr(p.err, kErrHashFull); continue; }
-                if (!kSecond) {
-                    acc += atomicAdd(cnt + slot, 1u);
-                } else {
-                    const unsigned long long delta = (unsigned long long)cnt[slot] - 1ull;
-                    if (delta) {
-                        if (wants_edges(MODE)) atomicAdd(p.pe + __ldg(p.eid + pos), delta);
-                        atomicAdd(msum + q, delta);
+                const int32_t w = good ? __ldg(p.adj + pos) : 0;
+                const int slot = good ? hash_find(keys, mask, w - lb, !kSecond) : -1;
+                if (good && slot < 0) atomicOr(p.err, kErrHashFull);
+                if (slot >= 0) {
+                    if (!kSecond) {
+                        acc += atomicAdd(cnt + slot, 1u);
+                    } else {
+                        delta = cnt[slot] - 1u;   // at most 255
+                        if (wants_edges(MODE) && delta) atomicAdd(p.pe + __ldg(p.eid + pos), (unsigned long long)delta);
                     }
                 }
             }
+            if (kSecond) run_add<uint32_t>(msum, q, delta, lane);
         }
         __syncwarp();
         if (kSecond && len > 0) {
