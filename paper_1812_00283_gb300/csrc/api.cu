@@ -153,12 +153,12 @@ int bfc_prepare(const bfc_csr *csr, const bfc_options *opt_in, void *stream, bfc
     int smem_optin = 0;
     e = cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, g->device);
     if (e != cudaSuccess) { delete h; return bfc::cuda_fail(e, "cudaDeviceGetAttribute"); }
-    if (smem_optin < bfc::kCounterBytes + 32 * 1024) {
+    if (smem_optin < bfc::kCounterBytes + 32 * 1024 / bfc::kCountCtasPerSm) {
         delete h;
         bfc::set_last_error("device has too little shared memory per block");
         return BFC_ERR_CUDA;
     }
-    g->grid = opt.num_ctas > 0 ? opt.num_ctas : g->num_sms;
+    g->grid = opt.num_ctas > 0 ? opt.num_ctas : g->num_sms * bfc::kCountCtasPerSm;
     rc = bfc::prepare_graph(csr, &opt, static_cast<cudaStream_t>(stream), g);
     if (rc != BFC_OK) {
         g->mem.release();
@@ -222,7 +222,7 @@ int bfc_prepare_batch(const bfc_csr *csr, const bfc_batch *batch, const bfc_opti
     cudaError_t e = cudaGetDevice(&g->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device);
     if (e != cudaSuccess) { delete h; return bfc::cuda_fail(e, "cudaGetDevice"); }
-    g->grid = opt.num_ctas > 0 ? opt.num_ctas : g->num_sms;
+    g->grid = opt.num_ctas > 0 ? opt.num_ctas : g->num_sms * bfc::kCountCtasPerSm;
     rc = bfc::prepare_graph(csr, &opt, static_cast<cudaStream_t>(stream), g, batch->num_graphs,
                             batch->graph_u_start, batch->graph_l_start);
     if (rc != BFC_OK) {

@@ -22,12 +22,13 @@ constexpr int kSortItems = 16;                            // per thread
 constexpr int kSortTile = kSortThreads * kSortItems;      // 4096 keys per tile
 constexpr int kSortWarpSpan = kSortTile / (kSortThreads / 32);  // 512 consecutive keys per warp
 
-constexpr int kCountThreads = 1024;                       // 32 warps, one CTA per SM
+constexpr int kCountCtasPerSm = 1;                        // persistent count CTAs per SM
+constexpr int kCountThreads = 1024 / kCountCtasPerSm;     // 32 warps per SM
 constexpr int kCountWarps = kCountThreads / 32;
-constexpr int kCounterBytes = 192 * 1024;                 // dynamic shared memory for counters
+constexpr int kCounterBytes = 192 * 1024 / kCountCtasPerSm;  // dynamic shared memory for counters
 constexpr int kDense16 = kCounterBytes / 2;               // 98,304 packed 16-bit counters
 constexpr int kDense32 = kCounterBytes / 4;               // 49,152 32-bit counters
-constexpr int kHashMaxSlots = 32768;                      // CTA hash: 128 KB keys + 64 KB counts
+constexpr int kHashMaxSlots = 32768 / kCountCtasPerSm;    // CTA hash: 128 KB keys + 64 KB counts
 constexpr int kHashMaxWork = kHashMaxSlots / 2;           // 16,384 wedges
 constexpr int kWarpRegion = kCounterBytes / kCountWarps;  // 6 KB of counters per warp
 constexpr int kWarpSlots = 512;                           // warp hash: 2 KB keys + 2 KB counts

@@ -99,7 +99,8 @@ struct Batch {
 template <int MODE, typename Pos, int kThreads>
 struct SharedTeam {
     static constexpr int kB = Batch<Pos, kThreads>::kSize;
-    int32_t start[kB + 1];              // compacted batch: exclusive prefix of run lengths (+ sentinel)
+    int32_t start[kB + 33];             // compacted batch: exclusive prefix of run lengths, then
+                                        // the total and 32 sentinels (INT_MAX)
     Pos src[kB];                        // compacted batch: adjacency position of a run minus its prefix
     unsigned long long msum[has_second_walk(MODE) ? kB : 1];  // second walk: Σ δ per compacted middle
     long long wtot[kThreads / 32];
@@ -346,6 +347,14 @@ __device__ unsigned long long team_walk(const CountParams &p, int32_t x, int32_t
                 }
                 len[i] = s1 - s0;
                 src[i] = (Pos)(b + s0);
+#if BFC_CHECKED
+                // every wedge of a run reads a slot in [b + s0, b + s1):
+                // checking the run here covers the slot of each of its wedges
+                if (len[i] > 0 && (b + s0 < 0 || b + s1 > p.adj_len)) {
+                    atomicOr(p.err, kErrBounds);
+                    len[i] = 0;
+                }
+#endif
             }
             // run length in the high bits, "non-empty" in the low 20 bits:
             // one scan yields both the run offsets and the compacted slots
@@ -368,7 +377,7 @@ __device__ unsigned long long team_walk(const CountParams &p, int32_t x, int32_t
             }
             packed += pk[i];
         }
-        if (tid == 0) sh.start[nnz] = total;
+        if (tid <= 32) sh.start[nnz + tid] = tid == 0 ? total : 0x7fffffff;
         t.sync();
         const int32_t nwin = (total + 31) >> 5;
         int32_t wb = (int32_t)(((int64_t)warp * nwin) / kWarps);
@@ -387,9 +396,12 @@ __device__ unsigned long long team_walk(const CountParams &p, int32_t x, int32_t
                     pos[u] = 0;
                     if (wb + u < wend) {   // warp-uniform
                         const int32_t kw = k0 + 32 * u;
-                        const int idx = q0 + 1 + lane;
-                        const int32_t d = (idx <= nnz ? sh.start[idx] : 0x7fffffff) - kw;
-                        const uint32_t m = __reduce_or_sync(0xffffffffu, d < 32 ? (1u << d) : 0u);
+                        // run starts after this window's first wedge: 1 <= d, and
+                        // the sentinels keep the index below nnz + 33
+                        const int32_t d = sh.start[q0 + 1 + lane] - kw;
+                        uint32_t bit;   // 1 << d, 0 once d >= 32 (PTX clamps the shift)
+                        asm("shl.b32 %0, %1, %2;" : "=r"(bit) : "r"(1u), "r"(d));
+                        const uint32_t m = __reduce_or_sync(0xffffffffu, bit);
                         q[u] = q0 + __popc(m & le_mask);
                         q0 += __popc(__ballot_sync(0xffffffffu, d <= 32));
                         ok[u] = kw + lane < total;
@@ -398,21 +410,18 @@ __device__ unsigned long long team_walk(const CountParams &p, int32_t x, int32_t
                 }
                 int32_t w[kU];
 #pragma unroll
-                for (int u = 0; u < kU; ++u) {
-#if BFC_CHECKED
-                    if (ok[u] && (unsigned long long)pos[u] >= (unsigned long long)p.adj_len) {
-                        atomicOr(p.err, kErrBounds);
-                        ok[u] = false;
-                    }
-#endif
-                    w[u] = ok[u] ? __ldg(p.adj + pos[u]) : 0;
-                }
+                for (int u = 0; u < kU; ++u) w[u] = ok[u] ? __ldg(p.adj + pos[u]) : 0;
+                // counts below 2^16 keep four olds far below 2^32
+                uint32_t acc32 = 0;
 #pragma unroll
                 for (int u = 0; u < kU; ++u) {
                     if (!kSecond) {
-                        if (ok[u])
-                            acc += wedge_op<MODE, KIND, false, Pos>(p, w[u], pos[u], lb, lo, span, hmask,
-                                                                    ctr, &sh.overflow, &sh.inserts);
+                        if (ok[u]) {
+                            const unsigned long long old =
+                                wedge_op<MODE, KIND, false, Pos>(p, w[u], pos[u], lb, lo, span, hmask,
+                                                                 ctr, &sh.overflow, &sh.inserts);
+                            if (KIND == kDenseWide) acc += old; else acc32 += (uint32_t)old;
+                        }
                     } else if (wb + u < wend) {   // warp-uniform: all lanes take part in run_add
                         const unsigned long long d =
                             ok[u] ? wedge_op<MODE, KIND, true, Pos>(p, w[u], pos[u], lb, lo, span, hmask,
@@ -423,6 +432,7 @@ __device__ unsigned long long team_walk(const CountParams &p, int32_t x, int32_t
                         else run_add<uint32_t>(sh.msum, q[u], (uint32_t)d, lane);
                     }
                 }
+                if (KIND != kDenseWide) acc += acc32;
                 k0 += 32 * kU;
             }
         }
@@ -752,7 +762,7 @@ __device__ unsigned long long warp_item(const CountParams &p, int32_t x, unsigne
 }
 
 template <int MODE, typename Pos>
-__global__ void __launch_bounds__(kCountThreads, 1) k_count(CountParams p) {
+__global__ void __launch_bounds__(kCountThreads, kCountCtasPerSm) k_count(CountParams p) {
     extern __shared__ __align__(16) unsigned char ctr[];
     __shared__ SharedTeam<MODE, Pos, kCountThreads> sh;
     const Team<kCountThreads> cta{(int)threadIdx.x, 0};
@@ -809,7 +819,7 @@ __global__ void __launch_bounds__(kCountThreads, 1) k_count(CountParams p) {
 // or a CTA table that fills up too: dense counters over the chunks of x's
 // end range.
 template <int MODE, typename Pos>
-__global__ void __launch_bounds__(kCountThreads, 1) k_count_retry(CountParams p) {
+__global__ void __launch_bounds__(kCountThreads, kCountCtasPerSm) k_count_retry(CountParams p) {
     extern __shared__ __align__(16) unsigned char ctr[];
     __shared__ SharedTeam<MODE, Pos, kCountThreads> sh;
     const Team<kCountThreads> cta{(int)threadIdx.x, 0};
@@ -852,9 +862,16 @@ template <int MODE, typename Pos>
 cudaError_t setup_one() {
     cudaError_t e = cudaFuncSetAttribute(k_count<MODE, Pos>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, kCounterBytes);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_count_retry<MODE, Pos>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, kCounterBytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_count<MODE, Pos>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 cudaSharedmemCarveoutMaxShared);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_count_retry<MODE, Pos>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, kCounterBytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_count_retry<MODE, Pos>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 cudaSharedmemCarveoutMaxShared);
+    return e;
 }
 
 template <typename Pos>

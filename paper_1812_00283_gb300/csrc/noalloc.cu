@@ -28,8 +28,11 @@ namespace cg = cooperative_groups;
 namespace bfc {
 namespace {
 
+constexpr int kNaThreads = 1024;                  // one CTA of 32 warps per SM
+constexpr int kNaWarps = kNaThreads / 32;
+constexpr int kNaSmemBytes = 192 * 1024;          // dynamic shared memory: the dense counters
 constexpr int32_t kNaMaxVertices = 65536;        // |U| + |L|
-constexpr int32_t kNaMaxLayer = kDense32;        // 49,152 per layer (one dense 32-bit counter array)
+constexpr int32_t kNaMaxLayer = kNaSmemBytes / 4; // 49,152 per layer (one dense 32-bit counter array)
 constexpr int64_t kNaMaxEdges = 1 << 20;         // 1,048,576 edges
 // words: [0,2) 64-bit accumulator | [2] error flags | [3] pad | deg[n] | loff[l+1] | lfill[l] | ladj[m]
 constexpr int64_t kNaWords = 4 + 3ll * kNaMaxVertices + 1 + kNaMaxEdges;
@@ -50,7 +53,7 @@ __device__ __forceinline__ bool lower_priority(const int32_t *deg, int32_t a, in
     return da < db || (da == db && a < b);
 }
 
-__global__ void __launch_bounds__(kCountThreads, 1)
+__global__ void __launch_bounds__(kNaThreads, 1)
 k_count_noalloc(int32_t r, int32_t l, int32_t m, const int32_t *__restrict__ off_u,
                 const int32_t *__restrict__ adj_u, int32_t *scratch,
                 unsigned long long *total_out, int32_t *status_out) {
@@ -101,7 +104,7 @@ k_count_noalloc(int32_t r, int32_t l, int32_t m, const int32_t *__restrict__ off
     if (!bad && blockIdx.x == 0) {
         if (threadIdx.x == 0) carry = 0;
         __syncthreads();
-        for (int32_t base = 0; base < l; base += kCountThreads) {
+        for (int32_t base = 0; base < l; base += kNaThreads) {
             const int32_t i = base + threadIdx.x;
             int32_t x = i < l ? deg[i] : 0;
             int32_t v = x;
@@ -126,7 +129,7 @@ k_count_noalloc(int32_t r, int32_t l, int32_t m, const int32_t *__restrict__ off
             const int32_t incl = v + (warp > 0 ? wsum[warp - 1] : 0);
             if (i < l) loff[i] = carry + incl - x;
             __syncthreads();
-            if (threadIdx.x == kCountThreads - 1) carry += incl;
+            if (threadIdx.x == kNaThreads - 1) carry += incl;
             __syncthreads();
         }
         if (threadIdx.x == 0) loff[l] = carry;
@@ -151,12 +154,12 @@ k_count_noalloc(int32_t r, int32_t l, int32_t m, const int32_t *__restrict__ off
             const bool in_u = x >= l;
             const int32_t layer = in_u ? r : l;
             uint4 *c4 = reinterpret_cast<uint4 *>(cnt);
-            for (int32_t i = threadIdx.x; i < (layer + 3) / 4; i += kCountThreads)
+            for (int32_t i = threadIdx.x; i < (layer + 3) / 4; i += kNaThreads)
                 c4[i] = make_uint4(0, 0, 0, 0);
             __syncthreads();
             const int32_t mb = in_u ? off_u[x - l] : loff[x];
             const int32_t me = in_u ? off_u[x - l + 1] : loff[x + 1];
-            for (int32_t j = mb + warp; j < me; j += kCountWarps) {
+            for (int32_t j = mb + warp; j < me; j += kNaWarps) {
                 const int32_t v = in_u ? adj_u[j] : l + ladj[j];       // middle, global id
                 if (!lower_priority(deg, v, x)) continue;
                 const int32_t eb = in_u ? loff[v] : off_u[v - l];
@@ -200,7 +203,7 @@ int noalloc_setup(int dev, int32_t **ptr, int *grid) {
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
         e = cudaFuncSetAttribute(k_count_noalloc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 kCounterBytes);
+                                 kNaSmemBytes);
         if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(k_count_noalloc)");
         int sms = 0, per_sm = 0, coop = 0;
         e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
@@ -208,8 +211,8 @@ int noalloc_setup(int dev, int32_t **ptr, int *grid) {
         if (!coop) { set_last_error("device cannot launch cooperative kernels"); return BFC_ERR_CUDA; }
         e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_count_noalloc, kCountThreads,
-                                                          kCounterBytes);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_count_noalloc, kNaThreads,
+                                                          kNaSmemBytes);
         if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
         if (per_sm < 1) { set_last_error("k_count_noalloc does not fit on an SM"); return BFC_ERR_CUDA; }
         g_na_grid[dev] = sms * per_sm;
@@ -249,7 +252,7 @@ extern "C" int bfc_count_small_noalloc(int32_t num_u, int32_t num_l, int64_t num
     unsigned long long *tot = reinterpret_cast<unsigned long long *>(total_dev);
     void *args[] = {&r, &l, &m, (void *)&off_u_dev, (void *)&adj_u_dev, &scratch, &tot, &status_dev};
     BFC_CUDA(cudaLaunchCooperativeKernel((const void *)bfc::k_count_noalloc, dim3(grid),
-                                         dim3(bfc::kCountThreads), args, bfc::kCounterBytes,
+                                         dim3(bfc::kNaThreads), args, bfc::kNaSmemBytes,
                                          static_cast<cudaStream_t>(stream)));
     bfc::note_launch();
     return BFC_OK;
