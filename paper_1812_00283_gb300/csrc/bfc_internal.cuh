@@ -155,8 +155,9 @@ struct Graph {
     int32_t *gstar = nullptr;             // [n] graph of each vertex of G*
     int32_t *vbase = nullptr;             // [n] first G* id of x's graph in x's layer
     int32_t *vend = nullptr;              // [n] one past the last G* id of x's graph in x's layer
-    // Algorithm 3 orientation: per slot e = (x, v), the run of N(v) holding
-    // the ends above both x and v starts at sbeg[e] and has plen[e] entries
+    // per middle slot e = (x, v), the run of N(v) holding the ends starts at
+    // sbeg[e] and has plen[e] entries: the prefix below x (Algorithm 2) or the
+    // suffix above both x and v (Algorithm 3)
     int64_t *sbeg = nullptr;
     // starts re-queued for the retry pass: x (its team table filled up: try a
     // CTA table) or -(x+1) (count with dense chunks)

@@ -63,7 +63,7 @@ struct CountParams {
     const int32_t *__restrict__ gstar; // graph of each G* vertex (batch mode)
     const int32_t *__restrict__ vbase; // first id of x's graph in x's layer (batch mode)
     const int32_t *__restrict__ vend;  // one past the last id of x's graph in x's layer (batch mode)
-    const int64_t *__restrict__ sbeg;  // Algorithm 3: start of each slot's run of ends
+    const int64_t *__restrict__ sbeg;  // start of each middle slot's run of ends
     unsigned long long *gtot;          // per-graph totals (batch mode)
     int32_t *retry;                    // re-queued starts: x (CTA table next) or -(x+1) (dense)
     int64_t retry_cap;
@@ -332,7 +332,7 @@ __device__ unsigned long long team_walk(const CountParams &p, int32_t x, int32_t
                 const int32_t pl = __ldg(p.plen + e[i]);
                 // run of ends: prefix of N(v) below x (Algorithm 2) or the
                 // suffix above both x and v (Algorithm 3)
-                const int64_t b = p.orient ? __ldg(p.sbeg + e[i]) : __ldg(p.off + v[i]);
+                const int64_t b = __ldg(p.sbeg + e[i]);
                 int32_t s0 = 0, s1 = pl;
                 if (KIND != kHash) {
                     if (p.coff) {
@@ -652,7 +652,7 @@ __device__ unsigned long long warp_walk(const CountParams &p, int32_t x, int32_t
             e = e0 + j;
             v = __ldg(p.adj + e);
             len = __ldg(p.plen + e);
-            src = p.orient ? __ldg(p.sbeg + e) : __ldg(p.off + v);
+            src = __ldg(p.sbeg + e);
         }
         int32_t incl = len;
 #pragma unroll

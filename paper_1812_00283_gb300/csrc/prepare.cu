@@ -173,17 +173,20 @@ __global__ void k_cut(const int64_t *__restrict__ off, const int32_t *__restrict
 }
 
 // plen[e] for a middle slot e = (x, v): the number of ends w in N(v) with
-// p(w) < p(x), i.e. the prefix of v's ascending list below x.
+// p(w) < p(x), i.e. the prefix of v's ascending list below x; sbeg[e] = the
+// position where that prefix starts (off[v]), so the count kernel reads it
+// with the slot instead of after the slot's neighbour id.
 __global__ void k_plen(const int64_t *__restrict__ off, const int32_t *__restrict__ adj,
                        const int32_t *__restrict__ rows, const int32_t *__restrict__ cut,
-                       int64_t slots, int32_t *plen) {
+                       int64_t slots, int32_t *plen, int64_t *sbeg) {
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < slots;
          e += (int64_t)gridDim.x * blockDim.x) {
         const int32_t x = rows[e];
         int32_t out = 0;
+        int64_t b = 0;
         if (e - off[x] < cut[x]) {
             const int32_t v = adj[e];
-            const int64_t b = off[v];
+            b = off[v];
             int64_t lo = 0, hi = off[v + 1] - b;
             while (lo < hi) {
                 int64_t mid = (lo + hi) >> 1;
@@ -192,6 +195,7 @@ __global__ void k_plen(const int64_t *__restrict__ off, const int32_t *__restric
             out = (int32_t)lo;
         }
         plen[e] = out;
+        sbeg[e] = b;
     }
 }
 
@@ -775,13 +779,13 @@ int prepare_graph(const bfc_csr *csr, const bfc_options *opt, cudaStream_t s, Gr
         k_cut<<<blocks_for(n), kT, 0, s>>>(g->off, g->adj, deg_star, n, l, g->cut); note_launch();
         BFC_CUDA(cudaGetLastError());
     }
+    GET(g->mem, g->sbeg, std::max<int64_t>(2 * m, 1));
     if (m > 0 && opt->orientation == 0) {
         k_plen<<<grid_stride_blocks(2 * m), kT, 0, s>>>(g->off, g->adj, rows_star, g->cut, 2 * m,
-                                                         g->plen); note_launch();
+                                                         g->plen, g->sbeg); note_launch();
         BFC_CUDA(cudaGetLastError());
     }
     if (m > 0 && opt->orientation == 1) {
-        GET(g->mem, g->sbeg, 2 * m);
         k_slen<<<grid_stride_blocks(2 * m), kT, 0, s>>>(g->off, g->adj, rows_star, g->cut, 2 * m,
                                                          g->plen, g->sbeg); note_launch();
         BFC_CUDA(cudaGetLastError());

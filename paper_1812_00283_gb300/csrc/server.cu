@@ -27,7 +27,7 @@ namespace {
 
 // device footprint estimate of a batch (arena, prepare temporaries, union CSR)
 int64_t batch_bytes(int64_t r, int64_t l, int64_t m) {
-    return 96 * m + 64 * (r + l) + (4 << 20);
+    return 112 * m + 64 * (r + l) + (4 << 20);
 }
 
 // offsets and ids of each graph shifted into the union's id space
