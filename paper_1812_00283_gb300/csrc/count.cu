@@ -30,6 +30,8 @@
 // needed with dense chunks of its end range.
 #include "bfc_internal.cuh"
 
+#include <type_traits>
+
 #ifndef BFC_CHECKED
 #define BFC_CHECKED 1
 #endif
@@ -385,7 +387,46 @@ __device__ unsigned long long team_walk(const CountParams &p, int32_t x, int32_t
         if (wb < wend) {
             int32_t k0 = wb << 5;
             int q0 = last_le(sh.start, nnz, k0);
-            for (; wb < wend; wb += kU) {
+            // Fast path: the next N windows lie inside run q0 (most wedges do, as
+            // runs of heavy starts are long), so the slots are consecutive, no
+            // run lookup is needed and N loads are in flight per lane.
+            auto fast = [&](auto n_windows, int32_t next_run) {
+                constexpr int N = decltype(n_windows)::value;
+                const Pos base = sh.src[q0] + (Pos)(k0 + lane);
+                int32_t w[N];
+#pragma unroll
+                for (int u = 0; u < N; ++u) w[u] = __ldg(p.adj + base + (Pos)(32 * u));
+                uint32_t sum32 = 0;   // N olds (or δ) of 16-bit counts stay below 2^20
+                unsigned long long sum64 = 0;
+#pragma unroll
+                for (int u = 0; u < N; ++u) {
+                    const unsigned long long r = wedge_op<MODE, KIND, kSecond, Pos>(
+                        p, w[u], base + (Pos)(32 * u), lb, lo, span, hmask, ctr, &sh.overflow, &sh.inserts);
+                    if (KIND == kDenseWide) sum64 += r; else sum32 += (uint32_t)r;
+                }
+                if (!kSecond) {
+                    acc += (KIND == kDenseWide) ? sum64 : (unsigned long long)sum32;
+                } else if (KIND == kDenseWide) {
+                    run_add<unsigned long long>(sh.msum, q0, sum64, lane);
+                } else {
+                    // one run: the warp's δ sum goes to middle q0
+                    const uint32_t tot = __reduce_add_sync(0xffffffffu, sum32);
+                    if (lane == 0 && tot) atomicAdd(sh.msum + q0, (unsigned long long)tot);
+                }
+                if (next_run == k0 + 32 * N) ++q0;   // the next window starts run q0 + 1
+                k0 += 32 * N;
+                wb += N;
+            };
+            while (wb < wend) {
+                const int32_t next_run = sh.start[q0 + 1];   // warp-uniform
+                if (wb + 2 * kU <= wend && next_run >= k0 + 64 * kU) {
+                    fast(std::integral_constant<int, 2 * kU>(), next_run);
+                    continue;
+                }
+                if (wb + kU <= wend && next_run >= k0 + 32 * kU) {
+                    fast(std::integral_constant<int, kU>(), next_run);
+                    continue;
+                }
                 int q[kU];
                 Pos pos[kU];
                 bool ok[kU];
@@ -434,6 +475,7 @@ __device__ unsigned long long team_walk(const CountParams &p, int32_t x, int32_t
                 }
                 if (KIND != kDenseWide) acc += acc32;
                 k0 += 32 * kU;
+                wb += kU;
             }
         }
         t.sync();
