@@ -64,6 +64,7 @@ def run_batch(args, rank, world):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    dist_init(world, dev)
     num = args.batch_graphs
     t0 = time.perf_counter()
     graphs = [G.batch_graph(g, 4000 + rank * num, device=dev) for g in range(num)]
@@ -83,7 +84,7 @@ def run_batch(args, rank, world):
     h = bfc.bfc_prepare_batch(r, l, m, off.data_ptr(), adj.data_ptr(), num, us.data_ptr(),
                               ls.data_ptr(), None, sp)
     chosen = bfc.bfc_autotune(h, sp, 2)
-    opts = bfc.bfc_options_init(warp_max_work=chosen.warp_max_work,
+    opts = bfc.bfc_options_init(warp_max_work=chosen.warp_max_work, team_max_work=chosen.team_max_work,
                                 hash_max_work=chosen.hash_max_work)
     bfc.bfc_count_batch(h, sp, tots.data_ptr(), None)
     wed = torch.zeros(num, dtype=torch.int64, device=dev)
@@ -127,6 +128,7 @@ def run_batch(args, rank, world):
     props = torch.cuda.get_device_properties(dev)
     clk = ClockSampler(f"GPU-{props.uuid}" if getattr(props, "uuid", None) else str(local))
     launches0 = bfc.bfc_kernel_launches()
+    dist_barrier(world)
     torch.cuda.synchronize()
     clk.start()
     for i in range(args.steps):
@@ -135,11 +137,14 @@ def run_batch(args, rank, world):
     torch.cuda.synchronize()
     clocks = clk.stop()
     launches = bfc.bfc_kernel_launches() - launches0
+    dist_barrier(world)
     if not torch.equal(tots, expect):
         raise SystemExit("per-graph totals changed between steps")
     step_ms = [e[0].elapsed_time(e[1]) for e in evs]
-    t_total = sum(step_ms)
-    value = num * args.steps / (t_total / 1e3)
+    t_total, graphs_all, (p50_all, p99_all) = reduce_over_ranks(
+        world, dev, sum(step_ms), num * args.steps, (statistics.median(step_ms), max(step_ms)))
+    _, W_all, _ = reduce_over_ranks(world, dev, 0.0, W * args.steps)
+    value = graphs_all / (t_total / 1e3)
 
     # the per-graph path: one prepare + one count launch per graph, in turn
     lat = []
@@ -170,16 +175,19 @@ def run_batch(args, rank, world):
         config=dict(workload=WORKLOADS["batch_4096"], num_graphs=num, union_edges=m,
                     wedges_per_step=W, step="prepare over the union (a1-a5) + one persistent count launch (a6-a7)",
                     l2="flushed between steps (512 MB write outside the timed events)",
-                    autotuned=dict(warp_max_work=chosen.warp_max_work, hash_max_work=chosen.hash_max_work),
+                    autotuned=dict(warp_max_work=chosen.warp_max_work, team_max_work=chosen.team_max_work,
+                                   hash_max_work=chosen.hash_max_work),
+                    parallelism=f"replicas x{world} (each rank its own batch, no collective)",
                     generation_s=gen_s),
-        batched=dict(graphs_per_s=value, wedges_per_s=W * args.steps / (t_total / 1e3),
-                     latency_ms_p50=statistics.median(step_ms), latency_ms_p99=max(step_ms),
+        batched=dict(graphs_per_s=value, wedges_per_s=W_all / (t_total / 1e3),
+                     latency_ms_p50=p50_all, latency_ms_p99=p99_all,
                      count_only_cuda_graph_ms=graph_count_ms),
         per_graph=dict(graphs_per_s=num / per_graph_s, latency_ms_p50=pct(50), latency_ms_p99=pct(99),
                        note="bfc_prepare + bfc_count + host read of the total, one graph at a time"),
         gpu_launches=launches, clocks=clocks)
     if rank == 0:
         print(json.dumps(out), flush=True)
+    dist_done(world)
     return 0
 
 
@@ -198,6 +206,7 @@ def run_serve(args, rank, world):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    dist_init(world, dev)
     t0 = time.perf_counter()
     pool = [G.batch_graph(i, 5001 + rank * 1000, device=dev) for i in range(args.serve_pool)]
     large = [G.chung_lu_bipartite(1_000_000, 500_000, 5_000_000, 2.0, 2.0, 5900 + rank * 10 + i,
@@ -250,8 +259,10 @@ def run_serve(args, rank, world):
     plain_cfg = bfc.bfc_server_config_init(memory_budget_bytes=120 << 30, workers=1, max_batch_graphs=1)
     # warm-up: pool + kernels
     serve(batched_cfg, float("inf"))
+    dist_barrier(world)
     sat_b, lat_b, tot_b, st_b = serve(batched_cfg, float("inf"))
     sat_p, lat_p, tot_p, st_p = serve(plain_cfg, float("inf"))
+    dist_barrier(world)
     if tot_b != tot_p:
         raise SystemExit("served totals differ between batched and plain serving")
     rates = []
@@ -269,20 +280,25 @@ def run_serve(args, rank, world):
         else:
             row["per_graph"] = "not run: arrival rate above 1.5x its saturation (queue grows without bound)"
         rates.append(row)
+    # whole job: every rank serves its own stream; throughput adds up, the
+    # latency percentiles are the worst rank's
+    _, sat_b_all, (p50_b, p99_b) = reduce_over_ranks(world, dev, 0.0, sat_b, (pct(lat_b, 50), pct(lat_b, 99)))
+    _, sat_p_all, (p50_p, p99_p) = reduce_over_ranks(world, dev, 0.0, sat_p, (pct(lat_p, 50), pct(lat_p, 99)))
     out = dict(
-        metric=METRIC, value=sat_b, unit="graphs/s", n_gpus=world, steps=nreq, warmup=nreq,
+        metric=METRIC, value=sat_b_all, unit="graphs/s", n_gpus=world, steps=nreq, warmup=nreq,
         ms_per_step=1e3 / sat_b, higher_is_better=True, scaling="weak", vs_baseline=None,
         dtype="u64", data="synthetic",
         config=dict(workload=WORKLOADS["serve_poisson"], requests_per_rate=nreq, pool=len(pool),
                     large_graphs=len(large), generation_s=gen_s,
                     step="one request: H2D of its CSR, prepare + count in a batch, D2H of its total"),
-        saturation=dict(batched=dict(graphs_per_s=sat_b, p50_ms=pct(lat_b, 50), p99_ms=pct(lat_b, 99),
+        saturation=dict(batched=dict(graphs_per_s=sat_b_all, p50_ms=p50_b, p99_ms=p99_b,
                                      batches=st_b["batches"], max_batch=st_b["max_batch_graphs"],
                                      peak_bytes=st_b["peak_bytes_in_use"]),
-                        per_graph=dict(graphs_per_s=sat_p, p50_ms=pct(lat_p, 50), p99_ms=pct(lat_p, 99))),
+                        per_graph=dict(graphs_per_s=sat_p_all, p50_ms=p50_p, p99_ms=p99_p)),
         rates=rates)
     if rank == 0:
         print(json.dumps(out), flush=True)
+    dist_done(world)
     return 0
 
 
@@ -397,6 +413,43 @@ def dist_setup():
     return rank, world, local
 
 
+def dist_init(world: int, device) -> None:
+    """One process per GPU: NCCL process group (rendezvous from the env)."""
+    if world > 1:
+        import torch.distributed as dist
+        if not dist.is_initialized():
+            dist.init_process_group("nccl", device_id=device)
+
+
+def dist_barrier(world: int) -> None:
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def reduce_over_ranks(world: int, device, t_max: float, units: float, extra_max=()):
+    """Whole-job figures over the replicas: the slowest rank's time (max), the
+    units all ranks processed (sum), and any further values taken as the
+    maximum over ranks (e.g. latency percentiles).  One rank: unchanged."""
+    if world <= 1:
+        return t_max, units, list(extra_max)
+    import torch
+    import torch.distributed as dist
+    mx = torch.tensor([t_max, *extra_max], dtype=torch.float64, device=device)
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    sm = torch.tensor([units], dtype=torch.float64, device=device)
+    dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+    vals = mx.cpu().tolist()
+    return vals[0], float(sm.item()), vals[1:]
+
+
+def dist_done(world: int) -> None:
+    if world > 1:
+        import torch.distributed as dist
+        if dist.is_initialized():
+            dist.destroy_process_group()
+
+
 def default_outputs(workload: str) -> str:
     # the shopping workload is specified with per-vertex and per-edge counts
     return "all" if workload == "shopping_300m" else "total"
@@ -493,14 +546,12 @@ def main():
         return run_serve(args, rank, world)
 
     import torch
-    import torch.distributed as dist
 
     from paper_1812_00283_gb300 import bfc
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    if world > 1:
-        dist.init_process_group("nccl", device_id=dev)
+    dist_init(world, dev)
 
     g = make_graph(args.workload, rank, dev)
     off = torch.from_numpy(g.off_u).to(dev)
@@ -548,8 +599,7 @@ def main():
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
     props = torch.cuda.get_device_properties(dev)
     clk = ClockSampler(f"GPU-{props.uuid}" if getattr(props, "uuid", None) else str(local))
-    if world > 1:
-        dist.barrier()
+    dist_barrier(world)
     torch.cuda.synchronize()
     launches0 = bfc.bfc_kernel_launches()
     clk.start()
@@ -559,8 +609,7 @@ def main():
     torch.cuda.synchronize()
     clocks = clk.stop()
     launches = bfc.bfc_kernel_launches() - launches0
-    if world > 1:
-        dist.barrier()
+    dist_barrier(world)
     got = int(total.item()) & ((1 << 64) - 1)
     if got != expect:
         raise SystemExit(f"count changed between steps: {got} vs {expect}")
@@ -568,16 +617,7 @@ def main():
     step_ms = [e[0].elapsed_time(e[3]) for e in evs]
     prep_ms = [e[0].elapsed_time(e[1]) for e in evs]
     count_ms = [e[1].elapsed_time(e[2]) for e in evs]
-    t_total = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([t_total], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_total = float(t.item())
-        w = torch.tensor([W], dtype=torch.int64, device=dev)
-        dist.all_reduce(w, op=dist.ReduceOp.SUM)
-        W_all = int(w.item())
-    else:
-        W_all = W
+    t_total, W_all, _ = reduce_over_ranks(world, dev, sum(step_ms), W)
     value = W_all * args.steps / (t_total / 1e3)
 
     peaks = measured_peaks()
@@ -676,8 +716,7 @@ def main():
             roofline=roofline, cpu_baseline=cpu, e2e=e2e,
             gpu_launches=launches, clocks=clocks)
         print(json.dumps(out), flush=True)
-    if world > 1:
-        dist.destroy_process_group()
+    dist_done(world)
     return 0
 
 
