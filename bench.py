@@ -631,6 +631,14 @@ def main():
                     peak_source=peaks["source"],
                     algorithmic_bytes_per_launch=B, count_ms_median=1e3 * cnt_s)
 
+    # the second ceiling: one shared-memory counter increment per wedge
+    # (first walk; the combined pass reads each counter again in its second)
+    smem_rate, _ = bfc.bfc_bench_smem_atomics(sp, 16384)
+    smem = dict(bound="smem_atomics", achieved=W / cnt_s, peak=smem_rate, unit="increments/s",
+                frac=(W / cnt_s) / smem_rate,
+                note="peak = bfc_bench_smem_atomics (returning 32-bit shared atomicAdd on packed "
+                     "16-bit counters at random indexes, one 1024-thread CTA per SM), measured in this run")
+
     # end to end through the C ABI from pinned host buffers
     e2e = None
     if args.e2e_steps > 0 and outputs == "all":
@@ -713,7 +721,7 @@ def main():
                                   hash_starts=info["hash_starts"], team_starts=info["team_starts"],
                                   warp_starts=info["warp_starts"]),
                         oracle_agrees=verified),
-            roofline=roofline, cpu_baseline=cpu, e2e=e2e,
+            roofline=roofline, smem_roofline=smem, cpu_baseline=cpu, e2e=e2e,
             gpu_launches=launches, clocks=clocks)
         print(json.dumps(out), flush=True)
     dist_done(world)

@@ -332,6 +332,16 @@ int bfc_version(void);
  * (all devices, all threads). */
 long long bfc_kernel_launches(void);
 
+/* Measurement aid (no counterpart in the paper): the throughput of the
+ * count kernel's counter operation on the current device -- a returning
+ * 32-bit shared-memory atomicAdd on a 16-bit counter packed two per word, at
+ * pseudo-random indexes, one 1024-thread CTA with 192 KB of shared memory
+ * per SM, `iters` (>= 1) increments per thread.  Writes increments per
+ * second to *increments_per_s and the timed launch's device time to *ms
+ * (nullable).  Synchronises `stream`; allocates 256 bytes from the
+ * library's pool for the duration of the call. */
+int bfc_bench_smem_atomics(void *stream, int32_t iters, double *increments_per_s, double *ms);
+
 #ifdef __cplusplus
 }
 #endif

@@ -97,6 +97,8 @@ _SIGS = {
     "bfc_last_error": (ctypes.c_char_p, []),
     "bfc_version": (c_int, []),
     "bfc_kernel_launches": (ctypes.c_longlong, []),
+    "bfc_bench_smem_atomics": (c_int, [c_void_p, c_int32, ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(ctypes.c_double)]),
     "bfc_prepare_batch": (c_int, [ctypes.POINTER(bfc_csr), ctypes.POINTER(bfc_batch),
                                   ctypes.POINTER(bfc_options), c_void_p, ctypes.POINTER(c_void_p)]),
     "bfc_count_batch": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
@@ -289,6 +291,14 @@ def bfc_version() -> int:
 
 def bfc_kernel_launches() -> int:
     return int(_lib.bfc_kernel_launches())
+
+
+def bfc_bench_smem_atomics(stream: int, iters: int) -> tuple[float, float]:
+    """(increments per second, device ms) of the counter-operation microbenchmark."""
+    rate, ms = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    _check(_lib.bfc_bench_smem_atomics(stream, iters, ctypes.byref(rate), ctypes.byref(ms)),
+           "bfc_bench_smem_atomics")
+    return rate.value, ms.value
 
 
 def library():
