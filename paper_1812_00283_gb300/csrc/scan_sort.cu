@@ -171,20 +171,30 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint64_t *__r
 }
 
 // Stable scatter of one tile: within a warp, keys are ranked in order with
-// __match_any_sync peer groups; warps are then ordered by a per-digit
-// prefix over warps, and tiles by the scanned digit-major histogram.
+// __match_any_sync peer groups; warps are then ordered by a per-digit prefix
+// over warps, digits by a prefix over the tile's digit counts, and the tile is
+// first laid out digit-major in shared memory, so that the global writes of
+// each digit's keys are consecutive (coalesced) rather than one per key.
+constexpr int kScatterSmem = (kSortThreads / 32) * 256 * 4 + 2 * 256 * 4 + kSortTile * (8 + 4);
+
 __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
     const uint64_t *__restrict__ kin, const int32_t *__restrict__ vin, uint64_t *__restrict__ kout,
     int32_t *__restrict__ vout, int64_t n, int shift, const uint32_t *__restrict__ hist_scan,
     int64_t ntiles) {
     constexpr int kWarps = kSortThreads / 32;
-    __shared__ uint32_t wcnt[kWarps][256];
-    __shared__ uint32_t gbase[256];
+    static_assert(kSortThreads == 256, "one thread per digit");
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint64_t *skey = reinterpret_cast<uint64_t *>(smem);                       // [kSortTile]
+    int32_t *sval = reinterpret_cast<int32_t *>(skey + kSortTile);             // [kSortTile]
+    uint32_t (*wcnt)[256] = reinterpret_cast<uint32_t (*)[256]>(sval + kSortTile);  // [kWarps][256]
+    uint32_t *dstart = &wcnt[kWarps][0];                                         // [256]
+    uint32_t *gbase = dstart + 256;                                              // [256]
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int i = threadIdx.x; i < kWarps * 256; i += kSortThreads) (&wcnt[0][0])[i] = 0;
     gbase[threadIdx.x] = hist_scan[(int64_t)threadIdx.x * ntiles + blockIdx.x];
     __syncthreads();
-    const int64_t base = (int64_t)blockIdx.x * kSortTile + (int64_t)warp * kSortWarpSpan;
+    const int64_t tile0 = (int64_t)blockIdx.x * kSortTile;
+    const int64_t base = tile0 + (int64_t)warp * kSortWarpSpan;
     const uint32_t lt_mask = (1u << lane) - 1u;
     uint64_t key[kSortItems];
     int32_t val[kSortItems];
@@ -195,6 +205,10 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
         bool valid = k < n;
         key[i] = valid ? kin[k] : 0;
         val[i] = valid ? vin[k] : 0;
+    }
+#pragma unroll
+    for (int i = 0; i < kSortItems; ++i) {
+        const bool valid = base + i * 32 + lane < n;
         uint32_t d = valid ? (uint32_t)((key[i] >> shift) & 0xff) : 256u;
         uint32_t peers = __match_any_sync(0xffffffffu, d);
         uint32_t cur = valid ? wcnt[warp][d] : 0;
@@ -204,24 +218,45 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
         __syncwarp();
     }
     __syncthreads();
+    // thread t owns digit t: prefix over warps, then over digits
+    uint32_t run = 0;
+    for (int w = 0; w < kWarps; ++w) {
+        uint32_t t = wcnt[w][threadIdx.x];
+        wcnt[w][threadIdx.x] = run;
+        run += t;
+    }
     {
-        uint32_t run = 0;
-        for (int w = 0; w < kWarps; ++w) {
-            uint32_t t = wcnt[w][threadIdx.x];
-            wcnt[w][threadIdx.x] = run;
-            run += t;
+        uint32_t incl = run;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            uint32_t o = __shfl_up_sync(0xffffffffu, incl, d);
+            if (lane >= d) incl += o;
         }
+        if (lane == 31) dstart[warp] = incl;   // warp totals (dstart reused below)
+        __syncthreads();
+        uint32_t before = 0;
+        for (int w = 0; w < warp; ++w) before += dstart[w];
+        __syncthreads();
+        dstart[threadIdx.x] = before + incl - run;
     }
     __syncthreads();
 #pragma unroll
     for (int i = 0; i < kSortItems; ++i) {
-        int64_t k = base + i * 32 + lane;
-        if (k < n) {
-            uint32_t d = (uint32_t)((key[i] >> shift) & 0xff);
-            int64_t pos = (int64_t)gbase[d] + wcnt[warp][d] + rk[i];
-            kout[pos] = key[i];
-            vout[pos] = val[i];
+        if (base + i * 32 + lane < n) {
+            const uint32_t d = (uint32_t)((key[i] >> shift) & 0xff);
+            const uint32_t lp = dstart[d] + wcnt[warp][d] + rk[i];
+            skey[lp] = key[i];
+            sval[lp] = val[i];
         }
+    }
+    __syncthreads();
+    const int cnt = (int)min((int64_t)kSortTile, n - tile0);
+    for (int j = threadIdx.x; j < cnt; j += kSortThreads) {
+        const uint64_t kk = skey[j];
+        const uint32_t d = (uint32_t)((kk >> shift) & 0xff);
+        const int64_t pos = (int64_t)gbase[d] + (j - (int)dstart[d]);
+        kout[pos] = kk;
+        vout[pos] = sval[j];
     }
 }
 
@@ -287,6 +322,19 @@ cudaError_t radix_sort_pairs(uint64_t *k0, int32_t *v0, uint64_t *k1, int32_t *v
     *which = 0;
     if (n <= 1 || end_bit <= begin_bit) return cudaSuccess;
     const int64_t ntiles = (n + kSortTile - 1) / kSortTile;
+    {
+        static bool attr_set[64] = {false};
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return e;
+        if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+        if (!attr_set[dev]) {
+            e = cudaFuncSetAttribute(k_radix_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     kScatterSmem);
+            if (e != cudaSuccess) return e;
+            attr_set[dev] = true;
+        }
+    }
     uint64_t *ki = k0, *ko = k1;
     int32_t *vi = v0, *vo = v1;
     for (int shift = begin_bit; shift < end_bit; shift += 8) {
@@ -295,8 +343,8 @@ cudaError_t radix_sort_pairs(uint64_t *k0, int32_t *v0, uint64_t *k1, int32_t *v
         if (e != cudaSuccess) return e;
         e = scan_impl<uint32_t, OpSum, false>(hist, hist, 256 * ntiles, scan_tmp, s);
         if (e != cudaSuccess) return e;
-        k_radix_scatter<<<(unsigned)ntiles, kSortThreads, 0, s>>>(ki, vi, ko, vo, n, shift, hist,
-                                                                   ntiles); note_launch();
+        k_radix_scatter<<<(unsigned)ntiles, kSortThreads, kScatterSmem, s>>>(ki, vi, ko, vo, n, shift,
+                                                                              hist, ntiles); note_launch();
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         uint64_t *tk = ki; ki = ko; ko = tk;
