@@ -319,45 +319,55 @@ __device__ unsigned long long team_walk(const CountParams &p, int32_t x, int32_t
     const uint32_t le_mask = 0xffffffffu >> (31 - lane);
     unsigned long long acc = 0;
     for (int32_t mb = 0; mb < nmid; mb += kB) {
-        int32_t len[kPer], v[kPer];
+        int32_t len[kPer], v[kPer], pl[kPer];
         Pos src[kPer];
-        int64_t e[kPer];
+        int64_t e[kPer], b[kPer];
+        bool has[kPer];
+        // the slot loads of all of this thread's middles first, then the
+        // chunk-boundary loads that depend on them: two rounds of latency
+#pragma unroll
+        for (int i = 0; i < kPer; ++i) {
+            const int32_t j = mb + i * kThreads + tid;
+            has[i] = j < nmid;
+            e[i] = has[i] ? e0 + j : e0;
+            v[i] = has[i] ? __ldg(p.adj + e[i]) : 0;
+            pl[i] = has[i] ? __ldg(p.plen + e[i]) : 0;
+            // run of ends: prefix of N(v) below x (Algorithm 2) or the
+            // suffix above both x and v (Algorithm 3)
+            b[i] = has[i] ? __ldg(p.sbeg + e[i]) : 0;
+        }
+        int32_t s0[kPer], s1[kPer];
+#pragma unroll
+        for (int i = 0; i < kPer; ++i) {
+            s0[i] = 0;
+            s1[i] = pl[i];
+            if (KIND != kHash && has[i] && pl[i] > 0) {
+                if (p.coff) {
+                    const int64_t tb = v[i] < p.l ? (int64_t)v[i] * p.coff_u1
+                                                  : (int64_t)p.l * p.coff_u1 + (int64_t)(v[i] - p.l) * p.coff_l1;
+                    if (flags & 1) s0[i] = __ldg(p.coff + tb + lo / kChunkUnit);
+                    if (flags & 2) s1[i] = __ldg(p.coff + tb + hi / kChunkUnit);
+                } else {
+                    if (flags & 1) s0[i] = lower_bound_g(p.adj + b[i], pl[i], lb + lo);
+                    if (flags & 2) s1[i] = lower_bound_g(p.adj + b[i], pl[i], lb + hi);
+                }
+            }
+        }
         long long packed_run = 0;
         long long pk[kPer];
 #pragma unroll
         for (int i = 0; i < kPer; ++i) {
-            const int32_t j = mb + i * kThreads + tid;
-            len[i] = 0; v[i] = 0; src[i] = 0; e[i] = 0;
-            if (j < nmid) {
-                e[i] = e0 + j;
-                v[i] = __ldg(p.adj + e[i]);
-                const int32_t pl = __ldg(p.plen + e[i]);
-                // run of ends: prefix of N(v) below x (Algorithm 2) or the
-                // suffix above both x and v (Algorithm 3)
-                const int64_t b = __ldg(p.sbeg + e[i]);
-                int32_t s0 = 0, s1 = pl;
-                if (KIND != kHash) {
-                    if (p.coff) {
-                        const int64_t tb = v[i] < p.l ? (int64_t)v[i] * p.coff_u1
-                                                      : (int64_t)p.l * p.coff_u1 + (int64_t)(v[i] - p.l) * p.coff_l1;
-                        if (flags & 1) s0 = __ldg(p.coff + tb + lo / kChunkUnit);
-                        if (flags & 2) s1 = __ldg(p.coff + tb + hi / kChunkUnit);
-                    } else {
-                        if (flags & 1) s0 = lower_bound_g(p.adj + b, pl, lb + lo);
-                        if (flags & 2) s1 = lower_bound_g(p.adj + b, pl, lb + hi);
-                    }
-                }
-                len[i] = s1 - s0;
-                src[i] = (Pos)(b + s0);
+            len[i] = s1[i] - s0[i];
+            src[i] = (Pos)(b[i] + s0[i]);
 #if BFC_CHECKED
-                // every wedge of a run reads a slot in [b + s0, b + s1):
-                // checking the run here covers the slot of each of its wedges
-                if (len[i] > 0 && (b + s0 < 0 || b + s1 > p.adj_len)) {
-                    atomicOr(p.err, kErrBounds);
-                    len[i] = 0;
-                }
-#endif
+            // every wedge of a run reads a slot in [b + s0, b + s1): checking
+            // the run here covers the slot of each of its wedges
+            if (len[i] > 0 && (b[i] + s0[i] < 0 || b[i] + s1[i] > p.adj_len)) {
+                atomicOr(p.err, kErrBounds);
+                len[i] = 0;
             }
+#endif
+            if (len[i] < 0) len[i] = 0;
             // run length in the high bits, "non-empty" in the low 20 bits:
             // one scan yields both the run offsets and the compacted slots
             pk[i] = ((long long)len[i] << 20) | (len[i] > 0 ? 1 : 0);
