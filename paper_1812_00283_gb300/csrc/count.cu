@@ -488,7 +488,10 @@ __device__ unsigned long long team_walk(const CountParams &p, int32_t x, int32_t
                 wb += kU;
             }
         }
-        t.sync();
+        // Dense counting needs no join here: the next batch's scan barriers
+        // come before its compaction overwrites the run arrays, so warps that
+        // finish their windows early already load the next batch's slots.
+        if (KIND == kHash || kSecond) t.sync();
         if (KIND == kHash && !kSecond && sh.overflow) break;   // uniform: read after the barrier
         if (kSecond) {
 #pragma unroll
