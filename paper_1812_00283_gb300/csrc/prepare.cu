@@ -47,7 +47,7 @@ __global__ void k_deg_u(const int32_t *__restrict__ off, int32_t r, int32_t *deg
     if (u >= r) return;
     int32_t d = off[u + 1] - off[u];
     deg_u[u] = d;
-    if (d > 0) heads[off[u]] = (int32_t)u;   // row owning slot off[u]; rows via max-scan
+    if (heads && d > 0) heads[off[u]] = (int32_t)u;   // row owning slot off[u]; rows via max-scan
 }
 
 __global__ void k_deg_l(const int32_t *__restrict__ adj, int64_t m, int32_t *deg_l) {
@@ -94,41 +94,161 @@ __global__ void k_ranks(const uint64_t *__restrict__ sorted_deg, const int32_t *
 }
 
 // ----- a3: projection + sorted adjacency -------------------------------------
-// U-side composite key (rank_u, rank_l): sorting it lists every U vertex's
-// neighbours in ascending L rank, i.e. ascending priority.
-__global__ void k_edge_keys(const int32_t *__restrict__ rows, const int32_t *__restrict__ adj_u,
-                            const int32_t *__restrict__ rank_u, const int32_t *__restrict__ rank_l,
-                            int64_t m, int bl, uint64_t *keys, int32_t *vals) {
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < m;
-         k += (int64_t)gridDim.x * blockDim.x) {
-        keys[k] = ((uint64_t)(uint32_t)rank_u[rows[k]] << bl) | (uint64_t)(uint32_t)rank_l[adj_u[k]];
-        vals[k] = (int32_t)k;
+// ---- U side row by row.  Row u of the caller's CSR becomes G* row l + rank_u[u]
+// (its slots start at off_star[l + rank_u[u]]); inside the row the neighbours
+// go in ascending L rank.  The ranks of a row are distinct (E is a set), so
+// any ordering method gives the same layout.  Three tiers by degree:
+//   d <= 32            one warp, each lane's position = the lanes below it;
+//   32 < d <= 4,096    one CTA, bitonic sort of (rank, slot) in shared memory;
+//   d > 4,096          (a few hundred rows) one radix sort of their edges.
+// Each tier also writes the swapped key (rank_l, rank_u) at the U-side
+// position; U-side order is ascending in rank_u, so the stable sort of those
+// keys on the rank_l bits yields the L side.
+constexpr int kRowWarpMax = 32;
+constexpr int kRowCtaMax = 4096;
+constexpr int kRowCtaThreads = 256;
+
+struct URowOut {
+    int64_t m;
+    int32_t l;
+    int bu;
+    const int64_t *off_star;
+    int32_t *adj_star, *eid_star, *rows_star;
+    uint64_t *keys2;
+    int32_t *vals2;
+    int *err;
+    int check_dup;   // flag duplicate edges (validate)
+    __device__ __forceinline__ void put(int32_t ru, int64_t pos, int32_t rl, int32_t slot) const {
+        const int64_t k = off_star[l + ru] - m + pos;   // U-side position
+        adj_star[m + k] = rl;
+        eid_star[m + k] = slot;
+        rows_star[m + k] = l + ru;
+        keys2[k] = ((uint64_t)(uint32_t)rl << bu) | (uint64_t)(uint32_t)ru;
+        vals2[k] = slot;
+    }
+};
+
+__global__ void k_u_rows_warp(const int32_t *__restrict__ off_u, const int32_t *__restrict__ adj_u,
+                              const int32_t *__restrict__ rank_u, const int32_t *__restrict__ rank_l,
+                              int32_t r, URowOut o) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t u = w0; u < r; u += nw) {
+        const int32_t b = off_u[u], d = off_u[u + 1] - b;
+        if (d == 0 || d > kRowWarpMax) continue;   // warp-uniform
+        const int32_t rl = lane < d ? rank_l[adj_u[b + lane]] : 0x7fffffff;
+        int pos = 0;
+        bool dup = false;
+        for (int k = 0; k < d; ++k) {
+            const int32_t ok = __shfl_sync(0xffffffffu, rl, k);
+            // ties (duplicate edges) are broken by lane, so positions stay distinct
+            pos += (ok < rl || (ok == rl && k < lane)) ? 1 : 0;
+            dup |= ok == rl && k != lane;
+        }
+        if (lane < d) {
+            if (dup && o.check_dup) atomicOr(o.err, kErrDuplicate);
+            o.put(rank_u[u], pos, rl, b + lane);
+        }
     }
 }
 
-__global__ void k_dup_check(const uint64_t *__restrict__ keys, int64_t m, int *err) {
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x + 1; k < m;
-         k += (int64_t)gridDim.x * blockDim.x)
-        if (keys[k] == keys[k - 1]) atomicOr(err, kErrDuplicate);
+__global__ void __launch_bounds__(kRowCtaThreads) k_u_rows_cta(
+    const int32_t *__restrict__ off_u, const int32_t *__restrict__ adj_u,
+    const int32_t *__restrict__ rank_u, const int32_t *__restrict__ rank_l,
+    const int32_t *__restrict__ rows, int32_t nrows, URowOut o) {
+    __shared__ uint64_t buf[kRowCtaMax];
+    for (int64_t i0 = blockIdx.x; i0 < nrows; i0 += gridDim.x) {
+        const int32_t u = rows[i0];
+        const int32_t b = off_u[u], d = off_u[u + 1] - b;
+        int np = 64;
+        while (np < d) np <<= 1;
+        // (rank, slot): slots are distinct, so the sort has no ties
+        for (int i = threadIdx.x; i < np; i += kRowCtaThreads)
+            buf[i] = i < d ? ((uint64_t)(uint32_t)rank_l[adj_u[b + i]] << 32) | (uint32_t)(b + i) : ~0ull;
+        __syncthreads();
+        for (int k = 2; k <= np; k <<= 1) {
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                for (int i = threadIdx.x; i < np; i += kRowCtaThreads) {
+                    const int ij = i ^ j;
+                    if (ij > i) {
+                        const uint64_t a = buf[i], c = buf[ij];
+                        if ((a > c) == ((i & k) == 0)) { buf[i] = c; buf[ij] = a; }
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        const int32_t ru = rank_u[u];
+        for (int i = threadIdx.x; i < d; i += kRowCtaThreads) {
+            const uint64_t vv = buf[i];
+            const int32_t rl = (int32_t)(vv >> 32);
+            if (o.check_dup && i > 0 && (int32_t)(buf[i - 1] >> 32) == rl) atomicOr(o.err, kErrDuplicate);
+            o.put(ru, i, rl, (int32_t)(uint32_t)vv);
+        }
+        __syncthreads();   // buf is reused by the next row
+    }
 }
 
-// U-side lists occupy G* slots [m, 2m); also builds the swapped key
-// (rank_l, rank_u) whose stable sort on the rank_l bits yields the L side.
-__global__ void k_emit_u_side(const uint64_t *__restrict__ keys, const int32_t *__restrict__ vals,
-                              int64_t m, int bl, int bu, int32_t l, int32_t *adj_star,
-                              int32_t *eid_star, int32_t *rows_star, uint64_t *keys2,
-                              int32_t *vals2) {
-    const uint64_t mask_l = (bl >= 64) ? ~0ull : ((1ull << bl) - 1ull);
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < m;
-         k += (int64_t)gridDim.x * blockDim.x) {
-        uint64_t key = keys[k];
-        uint32_t ru = (uint32_t)(key >> bl);
-        uint32_t rl = (uint32_t)(key & mask_l);
-        adj_star[m + k] = (int32_t)rl;
-        eid_star[m + k] = vals[k];
-        rows_star[m + k] = l + (int32_t)ru;
-        keys2[k] = ((uint64_t)rl << bu) | (uint64_t)ru;
-        vals2[k] = vals[k];
+// lists of the rows of the CTA tier and of the largest rows (any order: every
+// row is written to its own slots); one atomic per warp and list
+__global__ void k_row_tiers(const int32_t *__restrict__ off_u, int32_t r, int32_t *mid,
+                            int32_t *nmid, int32_t *large, int32_t *nlarge) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t lt = (1u << lane) - 1u;
+    for (int64_t u0 = (int64_t)blockIdx.x * blockDim.x; u0 < r; u0 += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t u = u0 + threadIdx.x;
+        const int32_t d = u < r ? off_u[u + 1] - off_u[u] : 0;
+        const bool is_mid = d > kRowWarpMax && d <= kRowCtaMax, is_large = d > kRowCtaMax;
+        const uint32_t bm = __ballot_sync(0xffffffffu, is_mid), bg = __ballot_sync(0xffffffffu, is_large);
+        int32_t om = 0, og = 0;
+        if (lane == 0 && bm) om = atomicAdd(nmid, __popc(bm));
+        if (lane == 0 && bg) og = atomicAdd(nlarge, __popc(bg));
+        om = __shfl_sync(0xffffffffu, om, 0);
+        og = __shfl_sync(0xffffffffu, og, 0);
+        if (is_mid) mid[om + __popc(bm & lt)] = (int32_t)u;
+        if (is_large) large[og + __popc(bg & lt)] = (int32_t)u;
+    }
+}
+
+__global__ void k_large_deg(const int32_t *__restrict__ off_u, const int32_t *__restrict__ large,
+                            int32_t nlarge, int64_t *ldeg) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nlarge) return;
+    ldeg[i] = off_u[large[i] + 1] - off_u[large[i]];
+}
+
+// one CTA per large row copies its edges with composite keys (rank_u, rank_l)
+__global__ void k_large_keys(const int32_t *__restrict__ off_u, const int32_t *__restrict__ adj_u,
+                             const int32_t *__restrict__ rank_u, const int32_t *__restrict__ rank_l,
+                             const int32_t *__restrict__ large, const int64_t *__restrict__ loff,
+                             int32_t nlarge, int bl, uint64_t *keys, int32_t *vals) {
+    for (int64_t i0 = blockIdx.x; i0 < nlarge; i0 += gridDim.x) {
+        const int32_t u = large[i0];
+        const int64_t o = loff[i0], d = loff[i0 + 1] - o;
+        const int32_t b = off_u[u];
+        const uint64_t hi = (uint64_t)(uint32_t)rank_u[u] << bl;
+        for (int64_t i = threadIdx.x; i < d; i += blockDim.x) {
+            keys[o + i] = hi | (uint64_t)(uint32_t)rank_l[adj_u[b + i]];
+            vals[o + i] = b + (int32_t)i;
+        }
+    }
+}
+
+__global__ void k_large_heads(const uint64_t *__restrict__ keys, int64_t n, int bl, int32_t *heads) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        heads[i] = (i == 0 || (keys[i] >> bl) != (keys[i - 1] >> bl)) ? (int32_t)i : 0;
+}
+
+__global__ void k_large_emit(const uint64_t *__restrict__ keys, const int32_t *__restrict__ vals,
+                             const int32_t *__restrict__ row_first, int64_t n, int bl, URowOut o) {
+    const uint64_t mask_l = (1ull << bl) - 1ull;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t key = keys[i];
+        if (o.check_dup && i > 0 && keys[i - 1] == key) atomicOr(o.err, kErrDuplicate);
+        o.put((int32_t)(key >> bl), i - row_first[i], (int32_t)(key & mask_l), vals[i]);
     }
 }
 
@@ -669,8 +789,11 @@ int prepare_graph(const bfc_csr *csr, const bfc_options *opt, cudaStream_t s, Gr
 
     // ---- a1: degrees (and the head of each U row for the slot -> row map)
     BFC_CUDA(cudaMemsetAsync(deg_l, 0, sizeof(int32_t) * std::max<int64_t>(l, 1), s));
-    BFC_CUDA(cudaMemsetAsync(heads, 0, sizeof(int32_t) * std::max<int64_t>(m, 1), s));
-    if (r > 0) { k_deg_u<<<blocks_for(r), kT, 0, s>>>(csr->off_u, r, deg_u, heads); note_launch(); }
+    // the row of every input slot is only needed to check a batch's edges
+    if (num_graphs > 0) BFC_CUDA(cudaMemsetAsync(heads, 0, sizeof(int32_t) * std::max<int64_t>(m, 1), s));
+    if (r > 0) {
+        k_deg_u<<<blocks_for(r), kT, 0, s>>>(csr->off_u, r, deg_u, num_graphs > 0 ? heads : nullptr); note_launch();
+    }
     if (m > 0) { k_deg_l<<<grid_stride_blocks(m), kT, 0, s>>>(csr->adj_u, m, deg_l); note_launch(); }
     BFC_CUDA(cudaGetLastError());
     BFC_CUDA(reduce_max_i32(deg_u, r, maxdeg, s));
@@ -733,8 +856,8 @@ int prepare_graph(const bfc_csr *csr, const bfc_options *opt, cudaStream_t s, Gr
     const int bu = bits_for(r > 0 ? (uint64_t)(r - 1) : 0);
     const int bl = bits_for(l > 0 ? (uint64_t)(l - 1) : 0);
     if (m > 0) {
-        BFC_CUDA(max_scan_inclusive(heads, rows, m, (int32_t *)scan64_tmp, s));
         if (num_graphs > 0) {
+            BFC_CUDA(max_scan_inclusive(heads, rows, m, (int32_t *)scan64_tmp, s));
             k_check_batch_edges<<<grid_stride_blocks(m), kT, 0, s>>>(rows, csr->adj_u, m, graph_u_start,
                                                                      graph_l_start, num_graphs, g->err); note_launch();
             BFC_CUDA(cudaGetLastError());
@@ -742,21 +865,64 @@ int prepare_graph(const bfc_csr *csr, const bfc_options *opt, cudaStream_t s, Gr
             BFC_CUDA(cudaStreamSynchronize(s));
             if (herr) { set_last_error("an edge joins vertices of two different graphs of the batch"); return BFC_ERR_INVALID_GRAPH; }
         }
-        k_edge_keys<<<grid_stride_blocks(m), kT, 0, s>>>(rows, csr->adj_u, g->rank_u, g->rank_l, m,
-                                                          bl, k0, v0); note_launch();
+        // U side row by row (warp / CTA tiers, radix sort for the largest rows);
+        // the swapped keys for the L side land in (k1, v1)
+        const URowOut uo{m, l, bu, g->off, g->adj, g->eid, rows_star, k1, v1, g->err, opt->validate};
+        k_u_rows_warp<<<grid_stride_blocks((int64_t)r * 32), kT, 0, s>>>(csr->off_u, csr->adj_u, g->rank_u,
+                                                                         g->rank_l, r, uo); note_launch();
         BFC_CUDA(cudaGetLastError());
-        BFC_CUDA(radix_sort_pairs(k0, v0, k1, v1, m, 0, bu + bl, hist, hist_tmp, s, &which));
-        uint64_t *ks = which ? k1 : k0;
-        int32_t *vs = which ? v1 : v0;
-        uint64_t *ko = which ? k0 : k1;
-        int32_t *vo = which ? v0 : v1;
-        if (opt->validate) {
-            k_dup_check<<<grid_stride_blocks(m), kT, 0, s>>>(ks, m, g->err); note_launch();
+        {
+            int32_t *mid_rows, *large_rows, *tier_n;
+            GET(tmp, mid_rows, std::max<int32_t>(r, 1));
+            GET(tmp, large_rows, std::max<int32_t>(r, 1));
+            GET(tmp, tier_n, 2);
+            BFC_CUDA(cudaMemsetAsync(tier_n, 0, 2 * sizeof(int32_t), s));
+            k_row_tiers<<<grid_stride_blocks(r), kT, 0, s>>>(csr->off_u, r, mid_rows, tier_n, large_rows,
+                                                             tier_n + 1); note_launch();
             BFC_CUDA(cudaGetLastError());
+            int32_t hn[2] = {0, 0};
+            BFC_CUDA(cudaMemcpyAsync(hn, tier_n, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+            BFC_CUDA(cudaStreamSynchronize(s));
+            if (hn[0] > 0) {
+                k_u_rows_cta<<<(unsigned)std::min<int32_t>(hn[0], 152 * 16), kRowCtaThreads, 0, s>>>(
+                    csr->off_u, csr->adj_u, g->rank_u, g->rank_l, mid_rows, hn[0], uo); note_launch();
+                BFC_CUDA(cudaGetLastError());
+            }
+            const int32_t nl = hn[1];
+            int64_t *ldeg, *loff;
+            GET(tmp, ldeg, (int64_t)nl + 1);
+            GET(tmp, loff, (int64_t)nl + 1);
+            int64_t nlarge = 0;
+            if (nl > 0) {
+                k_large_deg<<<blocks_for(nl), kT, 0, s>>>(csr->off_u, large_rows, nl, ldeg); note_launch();
+                BFC_CUDA(cudaGetLastError());
+                BFC_CUDA(scan_exclusive<int64_t>(ldeg, loff, nl, scan64_tmp, s));
+                BFC_CUDA(cudaMemcpyAsync(&nlarge, loff + nl, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+                BFC_CUDA(cudaStreamSynchronize(s));
+            }
+            if (nlarge > 0) {
+                uint64_t *ka;
+                int32_t *va, *rowf;
+                GET(tmp, ka, nlarge); GET(tmp, va, nlarge); GET(tmp, rowf, nlarge);
+                k_large_keys<<<(unsigned)std::min<int32_t>(nl, 1024), kT, 0, s>>>(csr->off_u, csr->adj_u, g->rank_u,
+                                                                                   g->rank_l, large_rows, loff, nl, bl,
+                                                                                   k0, v0); note_launch();
+                BFC_CUDA(cudaGetLastError());
+                int wl = 0;
+                BFC_CUDA(radix_sort_pairs(k0, v0, ka, va, nlarge, 0, bu + bl, hist, hist_tmp, s, &wl));
+                const uint64_t *kl = wl ? ka : k0;
+                const int32_t *vl = wl ? va : v0;
+                k_large_heads<<<grid_stride_blocks(nlarge), kT, 0, s>>>(kl, nlarge, bl, heads); note_launch();
+                BFC_CUDA(cudaGetLastError());
+                BFC_CUDA(max_scan_inclusive(heads, rowf, nlarge, (int32_t *)scan64_tmp, s));
+                k_large_emit<<<grid_stride_blocks(nlarge), kT, 0, s>>>(kl, vl, rowf, nlarge, bl, uo); note_launch();
+                BFC_CUDA(cudaGetLastError());
+            }
         }
-        k_emit_u_side<<<grid_stride_blocks(m), kT, 0, s>>>(ks, vs, m, bl, bu, l, g->adj, g->eid,
-                                                            rows_star, ko, vo); note_launch();
-        BFC_CUDA(cudaGetLastError());
+        uint64_t *ks = k0;
+        int32_t *vs = v0;
+        uint64_t *ko = k1;
+        int32_t *vo = v1;
         // stable sort of the (rank_l, rank_u) keys on the rank_l bits only:
         // the input is already ascending in rank_u within each rank_l
         int which2 = 0;
