@@ -99,12 +99,14 @@ __global__ void k_ranks(const uint64_t *__restrict__ sorted_deg, const int32_t *
 // go in ascending L rank.  The ranks of a row are distinct (E is a set), so
 // any ordering method gives the same layout.  Three tiers by degree:
 //   d <= 32            one warp, each lane's position = the lanes below it;
-//   32 < d <= 4,096    one CTA, bitonic sort of (rank, slot) in shared memory;
+//   32 < d <= 256      one warp, bitonic sort of (rank, slot) in its shared memory;
+//   256 < d <= 4,096   one CTA, bitonic sort of (rank, slot) in shared memory;
 //   d > 4,096          (a few hundred rows) one radix sort of their edges.
 // Each tier also writes the swapped key (rank_l, rank_u) at the U-side
 // position; U-side order is ascending in rank_u, so the stable sort of those
 // keys on the rank_l bits yields the L side.
 constexpr int kRowWarpMax = 32;
+constexpr int kRowWarpSortMax = 256;
 constexpr int kRowCtaMax = 4096;
 constexpr int kRowCtaThreads = 256;
 
@@ -153,6 +155,51 @@ __global__ void k_u_rows_warp(const int32_t *__restrict__ off_u, const int32_t *
     }
 }
 
+// ascending bitonic sort of np (a power of two) values by the calling warp
+__device__ __forceinline__ void warp_bitonic(uint64_t *buf, int np, int lane) {
+    for (int k = 2; k <= np; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = lane; i < np; i += 32) {
+                const int ij = i ^ j;
+                if (ij > i) {
+                    const uint64_t a = buf[i], c = buf[ij];
+                    if ((a > c) == ((i & k) == 0)) { buf[i] = c; buf[ij] = a; }
+                }
+            }
+            __syncwarp();
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kRowCtaThreads) k_u_rows_warp_sort(
+    const int32_t *__restrict__ off_u, const int32_t *__restrict__ adj_u,
+    const int32_t *__restrict__ rank_u, const int32_t *__restrict__ rank_l,
+    const int32_t *__restrict__ rows, int32_t nrows, URowOut o) {
+    __shared__ uint64_t buf[kRowCtaThreads / 32][kRowWarpSortMax];
+    const int lane = threadIdx.x & 31;
+    uint64_t *wb = buf[threadIdx.x >> 5];
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i0 = w0; i0 < nrows; i0 += nw) {
+        const int32_t u = rows[i0];
+        const int32_t b = off_u[u], d = off_u[u + 1] - b;
+        int np = 64;
+        while (np < d) np <<= 1;
+        for (int i = lane; i < np; i += 32)
+            wb[i] = i < d ? ((uint64_t)(uint32_t)rank_l[adj_u[b + i]] << 32) | (uint32_t)(b + i) : ~0ull;
+        __syncwarp();
+        warp_bitonic(wb, np, lane);
+        const int32_t ru = rank_u[u];
+        for (int i = lane; i < d; i += 32) {
+            const uint64_t vv = wb[i];
+            const int32_t rl = (int32_t)(vv >> 32);
+            if (o.check_dup && i > 0 && (int32_t)(wb[i - 1] >> 32) == rl) atomicOr(o.err, kErrDuplicate);
+            o.put(ru, i, rl, (int32_t)(uint32_t)vv);
+        }
+        __syncwarp();   // the buffer is reused by the warp's next row
+    }
+}
+
 __global__ void __launch_bounds__(kRowCtaThreads) k_u_rows_cta(
     const int32_t *__restrict__ off_u, const int32_t *__restrict__ adj_u,
     const int32_t *__restrict__ rank_u, const int32_t *__restrict__ rank_l,
@@ -192,22 +239,23 @@ __global__ void __launch_bounds__(kRowCtaThreads) k_u_rows_cta(
 
 // lists of the rows of the CTA tier and of the largest rows (any order: every
 // row is written to its own slots); one atomic per warp and list
-__global__ void k_row_tiers(const int32_t *__restrict__ off_u, int32_t r, int32_t *mid,
-                            int32_t *nmid, int32_t *large, int32_t *nlarge) {
+__global__ void k_row_tiers(const int32_t *__restrict__ off_u, int32_t r, int32_t *lists,
+                            int32_t *counts) {
+    // lists[t * r ...]: rows of tier t (0: warp sort, 1: CTA sort, 2: radix)
     const int lane = threadIdx.x & 31;
     const uint32_t lt = (1u << lane) - 1u;
     for (int64_t u0 = (int64_t)blockIdx.x * blockDim.x; u0 < r; u0 += (int64_t)gridDim.x * blockDim.x) {
         const int64_t u = u0 + threadIdx.x;
         const int32_t d = u < r ? off_u[u + 1] - off_u[u] : 0;
-        const bool is_mid = d > kRowWarpMax && d <= kRowCtaMax, is_large = d > kRowCtaMax;
-        const uint32_t bm = __ballot_sync(0xffffffffu, is_mid), bg = __ballot_sync(0xffffffffu, is_large);
-        int32_t om = 0, og = 0;
-        if (lane == 0 && bm) om = atomicAdd(nmid, __popc(bm));
-        if (lane == 0 && bg) og = atomicAdd(nlarge, __popc(bg));
-        om = __shfl_sync(0xffffffffu, om, 0);
-        og = __shfl_sync(0xffffffffu, og, 0);
-        if (is_mid) mid[om + __popc(bm & lt)] = (int32_t)u;
-        if (is_large) large[og + __popc(bg & lt)] = (int32_t)u;
+        const int tier = d <= kRowWarpMax ? -1 : d <= kRowWarpSortMax ? 0 : d <= kRowCtaMax ? 1 : 2;
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {
+            const uint32_t bm = __ballot_sync(0xffffffffu, tier == t);
+            int32_t o = 0;
+            if (lane == 0 && bm) o = atomicAdd(counts + t, __popc(bm));
+            o = __shfl_sync(0xffffffffu, o, 0);
+            if (tier == t) lists[(int64_t)t * r + o + __popc(bm & lt)] = (int32_t)u;
+        }
     }
 }
 
@@ -872,23 +920,28 @@ int prepare_graph(const bfc_csr *csr, const bfc_options *opt, cudaStream_t s, Gr
                                                                          g->rank_l, r, uo); note_launch();
         BFC_CUDA(cudaGetLastError());
         {
-            int32_t *mid_rows, *large_rows, *tier_n;
-            GET(tmp, mid_rows, std::max<int32_t>(r, 1));
-            GET(tmp, large_rows, std::max<int32_t>(r, 1));
-            GET(tmp, tier_n, 2);
-            BFC_CUDA(cudaMemsetAsync(tier_n, 0, 2 * sizeof(int32_t), s));
-            k_row_tiers<<<grid_stride_blocks(r), kT, 0, s>>>(csr->off_u, r, mid_rows, tier_n, large_rows,
-                                                             tier_n + 1); note_launch();
+            int32_t *tier_rows, *tier_n;
+            GET(tmp, tier_rows, 3 * std::max<int64_t>(r, 1));
+            GET(tmp, tier_n, 4);
+            BFC_CUDA(cudaMemsetAsync(tier_n, 0, 4 * sizeof(int32_t), s));
+            k_row_tiers<<<grid_stride_blocks(r), kT, 0, s>>>(csr->off_u, r, tier_rows, tier_n); note_launch();
             BFC_CUDA(cudaGetLastError());
-            int32_t hn[2] = {0, 0};
-            BFC_CUDA(cudaMemcpyAsync(hn, tier_n, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+            int32_t hn[3] = {0, 0, 0};
+            BFC_CUDA(cudaMemcpyAsync(hn, tier_n, 3 * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
             BFC_CUDA(cudaStreamSynchronize(s));
             if (hn[0] > 0) {
-                k_u_rows_cta<<<(unsigned)std::min<int32_t>(hn[0], 152 * 16), kRowCtaThreads, 0, s>>>(
-                    csr->off_u, csr->adj_u, g->rank_u, g->rank_l, mid_rows, hn[0], uo); note_launch();
+                const int64_t warps = std::min<int64_t>(hn[0], 152 * 64);
+                k_u_rows_warp_sort<<<(unsigned)((warps * 32 + kRowCtaThreads - 1) / kRowCtaThreads), kRowCtaThreads, 0, s>>>(
+                    csr->off_u, csr->adj_u, g->rank_u, g->rank_l, tier_rows, hn[0], uo); note_launch();
                 BFC_CUDA(cudaGetLastError());
             }
-            const int32_t nl = hn[1];
+            if (hn[1] > 0) {
+                k_u_rows_cta<<<(unsigned)std::min<int32_t>(hn[1], 152 * 16), kRowCtaThreads, 0, s>>>(
+                    csr->off_u, csr->adj_u, g->rank_u, g->rank_l, tier_rows + r, hn[1], uo); note_launch();
+                BFC_CUDA(cudaGetLastError());
+            }
+            const int32_t *large_rows = tier_rows + 2 * (int64_t)r;
+            const int32_t nl = hn[2];
             int64_t *ldeg, *loff;
             GET(tmp, ldeg, (int64_t)nl + 1);
             GET(tmp, loff, (int64_t)nl + 1);
