@@ -462,25 +462,37 @@ def oracle_run(g, outputs: str, threads: int) -> tuple[dict, float]:
     return r, time.perf_counter() - t0
 
 
+def graph_stats(g) -> dict:
+    """Degree statistics recorded with every single-graph result: maximum
+    degrees, Σ deg² per layer and TC_new = Σ over edges of min(deg u, deg v)
+    (the cost bound of Lemma 3)."""
+    import numpy as np
+    du = np.diff(g.off_u.astype(np.int64))
+    dl = np.bincount(g.adj_u, minlength=g.num_l).astype(np.int64)
+    ue = np.repeat(du, du)
+    return dict(max_deg_u=int(du.max(initial=0)), max_deg_l=int(dl.max(initial=0)),
+                sum_deg2_u=int((du * du).sum()), sum_deg2_l=int((dl * dl).sum()),
+                tc_new=int(np.minimum(ue, dl[g.adj_u]).sum()))
+
+
 def oracle_sample(g, outputs: str, threads: int, target_s: float):
-    """A bounded sample of the workload for the CPU oracle: the whole graph
-    if one run fits target_s, else the subgraph of a seeded fraction of U
-    sized from a calibration run.  Returns (graph, fraction, one run's result
-    and seconds)."""
+    """A bounded sample of the workload for the CPU oracle: the subgraph of a
+    seeded fraction of U (the whole graph when that fraction reaches 1),
+    sized from a calibration run on a small sample so that one run takes
+    about target_s.  Returns (graph, fraction, one run's result, seconds)."""
     from bfc_inputs import generators as G
-    if g.num_edges <= 25_000_000:
-        r, dt = oracle_run(g, outputs, threads)
-        if dt <= 2 * target_s:
-            return g, 1.0, r, dt
-        f = max(1e-4, target_s / dt)
-    else:
-        f = min(1.0, 2e6 / g.num_edges)
-        s = G.sample_u(g, f, 77)
-        r, dt = oracle_run(s, outputs, threads)
-        f = min(1.0, f * target_s / max(dt, 1e-3))
-    s = G.sample_u(g, f, 77)
+
+    def sample(f):
+        return g if f >= 1.0 else G.sample_u(g, f, 77)
+    f = min(1.0, 1e6 * max(threads, 1) / max(g.num_edges, 1))
+    s = sample(f)
     r, dt = oracle_run(s, outputs, threads)
-    return s, f, r, dt
+    nf = min(1.0, f * target_s / max(dt, 1e-3))
+    if nf <= f:
+        return s, f, r, dt
+    s = sample(nf)
+    r, dt = oracle_run(s, outputs, threads)
+    return s, nf, r, dt
 
 
 def sample_desc(workload: str, frac: float, sample, r: dict, outputs: str) -> str:
@@ -700,6 +712,10 @@ def main():
             verified = (ref["total"] == expect and ref["wedges"] == W)
         cpu = dict(value=ref["wedges"] / dt, unit=UNIT, cores=threads, kind="oracle",
                    sample=sample_desc(args.workload, frac, sample, ref, outputs) + f", one run, {dt:.1f} s")
+        # the same oracle on one core, on a smaller sample (~10 s)
+        s1, f1, r1, dt1 = oracle_sample(g, outputs, 1, 10.0)
+        cpu["one_thread"] = dict(value=r1["wedges"] / dt1, unit=UNIT, cores=1,
+                                 sample=sample_desc(args.workload, f1, s1, r1, outputs) + f", one run, {dt1:.1f} s")
 
     if rank == 0:
         out = dict(
@@ -707,7 +723,7 @@ def main():
             warmup=args.warmup, ms_per_step=t_total / args.steps, higher_is_better=True,
             scaling="weak", vs_baseline=None, dtype="u64", data="synthetic",
             config=dict(workload=WORKLOADS[args.workload], num_u=r, num_l=l, num_edges=m,
-                        wedges_per_step=W, butterflies=expect,
+                        wedges_per_step=W, butterflies=expect, graph=graph_stats(g),
                         step="prepare (a1-a5) + count (a6-a7), CSR resident in HBM",
                         l2="flushed between steps (512 MB write outside the timed events)",
                         parallelism=f"replicas x{world} (independent graphs, no collective)",
