@@ -274,6 +274,27 @@ def shifted_sidon_circulant(p: int, c: int, n: int) -> BipartiteCSR:
     return from_edges(n, n, u, v, f"sidon_{p}_{c}_{n}")
 
 
+def rows_of_degrees(degs, num_l: int, seed: int) -> BipartiteCSR:
+    """U vertex i gets degs[i] distinct L neighbours (a + j·s mod num_l,
+    j < degs[i], with a seeded start a and a stride s coprime to num_l):
+    lists of chosen lengths, for exercising degree thresholds."""
+    degs = [int(d) for d in degs]
+    if max(degs, default=0) > num_l:
+        raise ValueError("a degree exceeds num_l")
+    h = splitmix64_np(np.arange(2 * len(degs), dtype=np.uint64), seed)
+    us, vs = [], []
+    for i, d in enumerate(degs):
+        a = int(h[2 * i] % np.uint64(num_l))
+        st = int(h[2 * i + 1] % np.uint64(num_l)) | 1
+        while math.gcd(st, num_l) != 1:
+            st += 2
+        us.append(np.full(d, i, dtype=np.int64))
+        vs.append((a + np.arange(d, dtype=np.int64) * st) % num_l)
+    u = np.concatenate(us) if us else np.zeros(0, np.int64)
+    v = np.concatenate(vs) if vs else np.zeros(0, np.int64)
+    return from_edges(len(degs), num_l, u, v, f"rows_{len(degs)}_{num_l}_{seed}")
+
+
 def random_tiny(num_u: int, num_l: int, p_num: int, p_den: int, seed: int) -> BipartiteCSR:
     """Each of the r*l pairs is an edge with probability p_num/p_den."""
     k = np.arange(num_u * num_l, dtype=np.uint64)

@@ -146,6 +146,41 @@ def test_prepare_arrays(gi):
     assert np.array_equal(got["work"], P["work"])
 
 
+# U lists on both sides of each construction threshold (warp ranking up to 32
+# neighbours, warp sort up to 256, CTA sort up to 4,096, radix above), with
+# repeated degrees so that Definition 3's tie-break decides ranks
+ROW_DEGREES = [1, 2, 31, 32, 32, 33, 64, 255, 256, 256, 257, 1000, 4095, 4096, 4096, 4097, 9000]
+
+
+def _rows_graph():
+    degs = ROW_DEGREES + [(7 * i) % 40 + 1 for i in range(300)]
+    return G.rows_of_degrees(degs, 12000, 61)
+
+
+def test_prepare_arrays_across_row_tiers():
+    g = _rows_graph()
+    got = run_gpu(g, export=True, vertices=True, edges=True)
+    ru, rl, _ = oracle.priority(g)
+    assert np.array_equal(got["rank_u"], ru) and np.array_equal(got["rank_l"], rl)
+    P = oracle.projection(g)
+    for k in ("off", "adj", "eid", "cut", "work"):
+        assert np.array_equal(got[k], P[k]), k
+    ref = oracle.vp(g, vertices=True, edges=True)
+    assert got["total"] == ref["total"]
+    assert np.array_equal(got["pe"], ref["pe"])
+
+
+@pytest.mark.parametrize("deg", [2, 32, 200, 3000, 5000])
+def test_duplicate_rejected_in_every_row_tier(deg):
+    from paper_1812_00283_gb300 import BfcError, ButterflyGraph
+    g = G.rows_of_degrees([deg, 3, 40], 6000, 62)
+    adj = g.adj_u.copy()
+    adj[deg - 1] = adj[0]          # the last neighbour of row 0 repeats its first
+    with pytest.raises(BfcError) as ei:
+        ButterflyGraph(torch.from_numpy(g.off_u).cuda(), torch.from_numpy(adj).cuda(), 3, 6000)
+    assert ei.value.status == 2
+
+
 # ---------------------------------------------------------------------------
 # totals / per-vertex / per-edge against the oracle, every bin
 # ---------------------------------------------------------------------------
