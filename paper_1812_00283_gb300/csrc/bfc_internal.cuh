@@ -13,15 +13,6 @@ namespace bfc {
 // ---------------------------------------------------------------------------
 // Sizes
 // ---------------------------------------------------------------------------
-constexpr int kScanThreads = 512;
-constexpr int kScanItems = 8;
-constexpr int kScanTile = kScanThreads * kScanItems;     // 4096 elements per block
-
-constexpr int kSortThreads = 256;                         // 8 warps
-constexpr int kSortItems = 16;                            // per thread
-constexpr int kSortTile = kSortThreads * kSortItems;      // 4096 keys per tile
-constexpr int kSortWarpSpan = kSortTile / (kSortThreads / 32);  // 512 consecutive keys per warp
-
 constexpr int kCountCtasPerSm = 1;                        // persistent count CTAs per SM
 constexpr int kCountThreads = 1024 / kCountCtasPerSm;     // 32 warps per SM
 constexpr int kCountWarps = kCountThreads / 32;

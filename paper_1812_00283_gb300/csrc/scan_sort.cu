@@ -11,6 +11,15 @@ namespace bfc {
 
 namespace {
 
+constexpr int kScanThreads = 512;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanThreads * kScanItems;     // 4096 elements per block
+
+constexpr int kSortThreads = 256;                         // 8 warps
+constexpr int kSortItems = 8;                             // per thread
+constexpr int kSortTile = kSortThreads * kSortItems;      // 2048 keys per tile
+constexpr int kSortWarpSpan = kSortTile / (kSortThreads / 32);  // 256 consecutive keys per warp
+
 struct OpSum {
     template <typename T>
     __device__ static T apply(T a, T b) { return a + b; }
