@@ -81,8 +81,9 @@ typedef struct bfc_options {
     int32_t hash_max_work;  /* Algorithm 2: starts with at most this many
                                wedges (and more than team_max_work) are counted
                                by one CTA with a shared-memory hash table of up
-                               to 32,768 slots (default 16384, range
-                               [warp_max_work, 16384]); heavier starts get dense
+                               to 32,768 slots, at most 3/4 full (default
+                               24576, range [warp_max_work, 24576]); heavier
+                               starts get dense
                                shared-memory counters over chunks of their end
                                range.  Algorithm 3: ignored, except that 0 sends
                                every start beyond the warp bin to the dense pass */
@@ -206,7 +207,7 @@ int bfc_batch_wedges(const bfc_graph *g, void *stream, uint64_t *wedges_dev);
 
 /* Autotuner for the bin thresholds of step a5: re-bins the prepared graph for
  * each candidate (Algorithm 2: warp_max_work in {32, 128, 256} x
- * team_max_work in {512, 2048} x hash_max_work in {4096, 16384}; Algorithm 3:
+ * team_max_work in {512, 2048} x hash_max_work in {4096, 24576}; Algorithm 3:
  * warp_max_work in {32, 128, 256} x team_max_work in {2048, 16384}), times
  * `iters` count launches of each with CUDA events on `stream`, keeps the
  * fastest and writes it to *chosen (nullable).  Synchronises `stream`;

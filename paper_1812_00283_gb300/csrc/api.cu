@@ -81,11 +81,11 @@ static int check_options(const bfc_options *o) {
     }
     if ((o->hash_max_work < o->warp_max_work && !(o->orientation == 1 && o->hash_max_work == 0)) ||
         o->hash_max_work > bfc::kHashMaxWork || o->hash_max_work < 0) {
-        bfc::set_last_error("hash_max_work must lie in [warp_max_work, 16384]");
+        bfc::set_last_error("hash_max_work must lie in [warp_max_work, " + std::to_string(bfc::kHashMaxWork) + "]");
         return BFC_ERR_INVALID_ARGUMENT;
     }
     if (o->team_max_work < -1 || o->team_max_work > bfc::kTeamMaxWork) {
-        bfc::set_last_error("team_max_work must be -1 (default) or lie in [0, 16384]");
+        bfc::set_last_error("team_max_work must be -1 (default) or lie in [0, " + std::to_string(bfc::kTeamMaxWork) + "]");
         return BFC_ERR_INVALID_ARGUMENT;
     }
     if (o->num_ctas < 0) {
@@ -273,10 +273,10 @@ int bfc_autotune(bfc_graph *h, void *stream, int iters, bfc_options *chosen) {
     int nc = 0;
     for (int32_t wmax : {32, 128, 256}) {
         if (g->opt.orientation == 1) {
-            for (int32_t tmax : {2048, 16384}) cands[nc++] = {wmax, tmax, bfc::kHashMaxWork};
+            for (int32_t tmax : {2048, bfc::kTeamMaxWork}) cands[nc++] = {wmax, tmax, bfc::kHashMaxWork};
         } else {
             for (int32_t tmax : {512, 2048})
-                for (int32_t hmax : {4096, 16384}) cands[nc++] = {wmax, tmax, hmax};
+                for (int32_t hmax : {4096, bfc::kHashMaxWork}) cands[nc++] = {wmax, tmax, hmax};
         }
     }
     cudaEvent_t e0, e1;

@@ -20,7 +20,7 @@ constexpr int kCounterBytes = 192 * 1024 / kCountCtasPerSm;  // dynamic shared m
 constexpr int kDense16 = kCounterBytes / 2;               // 98,304 packed 16-bit counters
 constexpr int kDense32 = kCounterBytes / 4;               // 49,152 32-bit counters
 constexpr int kHashMaxSlots = 32768 / kCountCtasPerSm;    // CTA hash: 128 KB keys + 64 KB counts
-constexpr int kHashMaxWork = kHashMaxSlots / 2;           // 16,384 wedges
+constexpr int kHashMaxWork = kHashMaxSlots / 4 * 3;       // 24,576 wedges: at most 3/4 of the slots fill
 constexpr int kWarpRegion = kCounterBytes / kCountWarps;  // 6 KB of counters per warp
 constexpr int kWarpSlots = 512;                           // warp hash: 2 KB keys + 2 KB counts
 constexpr int kWarpMaxWork = kWarpSlots / 2;              // 256 wedges
@@ -29,7 +29,7 @@ constexpr int kTeams = kCountThreads / kTeamThreads;      // 4 teams per CTA
 constexpr int kTeamRegion = kCounterBytes / kTeams;       // 48 KB of shared memory per team
 constexpr int kTeamSlots = 4096;                          // team hash: 16 KB keys + 8 KB counts
 constexpr int kTeamFitWork = kTeamSlots / 2;              // a start this light always fits a team table
-constexpr int kTeamMaxWork = kHashMaxWork;                // upper limit of team_max_work
+constexpr int kTeamMaxWork = 16384;                       // upper limit of team_max_work
 constexpr uint32_t kNarrowMaxCut = 65535;                 // counts fit 16 bits when cut <= this
 constexpr int kChunkUnit = kDense32;                      // end-range chunk unit of the boundary table
 static_assert(kDense16 % kChunkUnit == 0, "narrow chunks must be whole table units");

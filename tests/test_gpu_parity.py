@@ -36,7 +36,7 @@ def _opts(**kw):
 BIN_SETTINGS = {
     "default": {},
     "all_dense": dict(warp_max_work=0, hash_max_work=0),
-    "hash_only": dict(warp_max_work=0, team_max_work=0, hash_max_work=16384),
+    "hash_only": dict(warp_max_work=0, team_max_work=0, hash_max_work=24576),
     "warp_heavy": dict(warp_max_work=256, hash_max_work=256),
     "team_small": dict(warp_max_work=32, team_max_work=512, hash_max_work=4096),
     # team tables may fill up: escalation to a CTA table in the retry pass
