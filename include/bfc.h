@@ -102,11 +102,11 @@ typedef struct bfc_options {
     int32_t team_max_work;  /* starts with more than warp_max_work and at most
                                this many wedges are counted by a 256-thread team
                                (four per CTA) with a 4,096-slot hash table.
-                               -1 (default) = 2048 for Algorithm 2 (its tables
+                               -1 (default) = 3072 for Algorithm 2 (its tables
                                then always fit) and 16384 for Algorithm 3;
                                otherwise in [0, 16384], and a value <=
                                warp_max_work leaves the team bin empty.
-                               Algorithm 2 caps it at hash_max_work; above 2048
+                               Algorithm 2 caps it at hash_max_work; above 3072
                                a start whose team table fills up goes to the
                                retry pass. */
     int32_t reserved[9];    /* must be zero */
@@ -207,7 +207,7 @@ int bfc_batch_wedges(const bfc_graph *g, void *stream, uint64_t *wedges_dev);
 
 /* Autotuner for the bin thresholds of step a5: re-bins the prepared graph for
  * each candidate (Algorithm 2: warp_max_work in {32, 128, 256} x
- * team_max_work in {512, 2048} x hash_max_work in {4096, 24576}; Algorithm 3:
+ * team_max_work in {512, 3072} x hash_max_work in {4096, 24576}; Algorithm 3:
  * warp_max_work in {32, 128, 256} x team_max_work in {2048, 16384}), times
  * `iters` count launches of each with CUDA events on `stream`, keeps the
  * fastest and writes it to *chosen (nullable).  Synchronises `stream`;

@@ -275,7 +275,7 @@ int bfc_autotune(bfc_graph *h, void *stream, int iters, bfc_options *chosen) {
         if (g->opt.orientation == 1) {
             for (int32_t tmax : {2048, bfc::kTeamMaxWork}) cands[nc++] = {wmax, tmax, bfc::kHashMaxWork};
         } else {
-            for (int32_t tmax : {512, 2048})
+            for (int32_t tmax : {512, bfc::kTeamFitWork})
                 for (int32_t hmax : {4096, bfc::kHashMaxWork}) cands[nc++] = {wmax, tmax, hmax};
         }
     }

@@ -28,7 +28,7 @@ constexpr int kTeamThreads = 256;                         // a team: 8 warps wit
 constexpr int kTeams = kCountThreads / kTeamThreads;      // 4 teams per CTA
 constexpr int kTeamRegion = kCounterBytes / kTeams;       // 48 KB of shared memory per team
 constexpr int kTeamSlots = 4096;                          // team hash: 16 KB keys + 8 KB counts
-constexpr int kTeamFitWork = kTeamSlots / 2;              // a start this light always fits a team table
+constexpr int kTeamFitWork = kTeamSlots / 4 * 3;          // 3,072: a start this light always fits a team table
 constexpr int kTeamMaxWork = 16384;                       // upper limit of team_max_work
 constexpr uint32_t kNarrowMaxCut = 65535;                 // counts fit 16 bits when cut <= this
 constexpr int kChunkUnit = kDense32;                      // end-range chunk unit of the boundary table

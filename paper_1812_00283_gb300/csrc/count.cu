@@ -25,7 +25,7 @@
 //      4,096-slot table and its batch arrays), one start per team.
 //   C. warp items: 32 warps, each with a 512-slot table, one light start each.
 // A table sized from a bound that can be exceeded (Algorithm 3's ends, or a
-// team bound above 2,048 wedges) detects when it fills up; the start is then
+// team bound above 3,072 wedges) detects when it fills up; the start is then
 // re-queued and counted by k_count_retry, first with a CTA table, then if
 // needed with dense chunks of its end range.
 #include "bfc_internal.cuh"

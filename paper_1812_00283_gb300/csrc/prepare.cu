@@ -715,8 +715,8 @@ static int schedule_graph(Graph *g, cudaStream_t s, int32_t warp_max_work, int32
         g->retry_static = n_hash;
         g->n_cta_items = 0;
     }
-    // Algorithm 2's tables always fit when a team start has at most 2,048
-    // wedges (4,096 slots) and a CTA start at most 16,384 (32,768 slots)
+    // Algorithm 2's tables always fit when a team start has at most 3,072
+    // wedges (4,096 slots) and a CTA start at most 24,576 (32,768 slots)
     g->may_retry = vpp ? (n_hash + n_team > 0) : (n_team > 0 && team_max > (uint64_t)kTeamFitWork);
     g->info.dense_items = h_dense_items;
     g->info.starts_with_work = n_dense + n_hash + n_team + n_warp;
