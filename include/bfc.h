@@ -77,7 +77,8 @@ typedef struct bfc_options {
                                id ranges are always checked. */
     int32_t warp_max_work;  /* starts with at most this many wedges are counted
                                by one warp with a 512-slot shared-memory hash
-                               table (default 256, range [0, 256]) */
+                               table (default 384, range [0, 384]; a table is at
+                               most 3/4 full) */
     int32_t hash_max_work;  /* Algorithm 2: starts with at most this many
                                wedges (and more than team_max_work) are counted
                                by one CTA with a shared-memory hash table of up
@@ -206,9 +207,9 @@ int bfc_count_batch(bfc_graph *g, void *stream, uint64_t *totals_dev, uint64_t *
 int bfc_batch_wedges(const bfc_graph *g, void *stream, uint64_t *wedges_dev);
 
 /* Autotuner for the bin thresholds of step a5: re-bins the prepared graph for
- * each candidate (Algorithm 2: warp_max_work in {32, 128, 256} x
+ * each candidate (Algorithm 2: warp_max_work in {32, 128, 384} x
  * team_max_work in {512, 3072} x hash_max_work in {4096, 24576}; Algorithm 3:
- * warp_max_work in {32, 128, 256} x team_max_work in {2048, 16384}), times
+ * warp_max_work in {32, 128, 384} x team_max_work in {2048, 16384}), times
  * `iters` count launches of each with CUDA events on `stream`, keeps the
  * fastest and writes it to *chosen (nullable).  Synchronises `stream`;
  * allocates only the schedule arrays. */

@@ -76,7 +76,7 @@ struct bfc_graph {
 
 static int check_options(const bfc_options *o) {
     if (o->warp_max_work < 0 || o->warp_max_work > bfc::kWarpMaxWork) {
-        bfc::set_last_error("warp_max_work must lie in [0, 256]");
+        bfc::set_last_error("warp_max_work must lie in [0, " + std::to_string(bfc::kWarpMaxWork) + "]");
         return BFC_ERR_INVALID_ARGUMENT;
     }
     if ((o->hash_max_work < o->warp_max_work && !(o->orientation == 1 && o->hash_max_work == 0)) ||
@@ -271,7 +271,7 @@ int bfc_autotune(bfc_graph *h, void *stream, int iters, bfc_options *chosen) {
     struct Cand { int32_t w, t, h; };
     Cand cands[12];
     int nc = 0;
-    for (int32_t wmax : {32, 128, 256}) {
+    for (int32_t wmax : {32, 128, bfc::kWarpMaxWork}) {
         if (g->opt.orientation == 1) {
             for (int32_t tmax : {2048, bfc::kTeamMaxWork}) cands[nc++] = {wmax, tmax, bfc::kHashMaxWork};
         } else {

@@ -23,7 +23,7 @@ constexpr int kHashMaxSlots = 32768 / kCountCtasPerSm;    // CTA hash: 128 KB ke
 constexpr int kHashMaxWork = kHashMaxSlots / 4 * 3;       // 24,576 wedges: at most 3/4 of the slots fill
 constexpr int kWarpRegion = kCounterBytes / kCountWarps;  // 6 KB of counters per warp
 constexpr int kWarpSlots = 512;                           // warp hash: 2 KB keys + 2 KB counts
-constexpr int kWarpMaxWork = kWarpSlots / 2;              // 256 wedges
+constexpr int kWarpMaxWork = kWarpSlots / 4 * 3;          // 384 wedges: at most 3/4 of the slots fill
 constexpr int kTeamThreads = 256;                         // a team: 8 warps with a named barrier
 constexpr int kTeams = kCountThreads / kTeamThreads;      // 4 teams per CTA
 constexpr int kTeamRegion = kCounterBytes / kTeams;       // 48 KB of shared memory per team

@@ -687,7 +687,7 @@ __device__ unsigned long long team_item(const CountParams &p, int32_t x, unsigne
 // ---- phase C: warp items ----------------------------------------------------------
 // The warp version of team_walk for a light start: batches of 32 middles,
 // compacted runs and the same window masks, with a per-warp hash table that
-// always fits (at most 256 wedges, 512 slots).
+// always fits (at most 384 wedges, 512 slots).
 template <int MODE, bool kSecond>
 __device__ unsigned long long warp_walk(const CountParams &p, int32_t x, int32_t lb, uint32_t mask,
                                         int32_t *keys, uint32_t *cnt, unsigned long long *msum,
@@ -748,7 +748,7 @@ __device__ unsigned long long warp_walk(const CountParams &p, int32_t x, int32_t
                     if (!kSecond) {
                         acc += atomicAdd(cnt + slot, 1u);
                     } else {
-                        delta = cnt[slot] - 1u;   // at most 255
+                        delta = cnt[slot] - 1u;   // below 384
                         if (wants_edges(MODE) && delta) atomicAdd(p.pe + __ldg(p.eid + pos), (unsigned long long)delta);
                     }
                 }

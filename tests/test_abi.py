@@ -39,7 +39,7 @@ def test_version_and_strings(bfc):
 def test_options_defaults(bfc):
     o = bfc.bfc_options_init()
     assert (o.validate, o.warp_max_work, o.hash_max_work, o.num_ctas, o.wide_positions,
-            o.orientation, o.team_max_work) == (1, 256, 24576, 0, 0, 0, -1)
+            o.orientation, o.team_max_work) == (1, 384, 24576, 0, 0, 0, -1)
 
 
 def test_struct_layouts_match_header(bfc, tmp_path):

@@ -49,7 +49,7 @@ def _count(h, nG):
     return tot.cpu().numpy().view(np.uint64), int(one.item())
 
 
-@pytest.mark.parametrize("opts", [{}, dict(warp_max_work=0, hash_max_work=0), dict(hash_max_work=256),
+@pytest.mark.parametrize("opts", [{}, dict(warp_max_work=0, hash_max_work=0), dict(warp_max_work=128, hash_max_work=256),
                                   dict(warp_max_work=0, team_max_work=16384),
                                   dict(orientation=1), dict(orientation=1, warp_max_work=0, hash_max_work=0),
                                   dict(orientation=1, team_max_work=0)])
@@ -79,7 +79,7 @@ def test_batch_autotune_and_graph_capture():
     try:
         s = torch.cuda.current_stream()
         chosen = bfc.bfc_autotune(h, s.cuda_stream, 1)
-        assert chosen.warp_max_work in (32, 128, 256) and chosen.hash_max_work in (4096, 24576)
+        assert chosen.warp_max_work in (32, 128, 384) and chosen.hash_max_work in (4096, 24576)
         expect, _ = _count(h, b.num_graphs)          # first call outside capture
         tot = torch.zeros(b.num_graphs, dtype=torch.int64, device="cuda")
         cg = torch.cuda.CUDAGraph()
