@@ -32,10 +32,6 @@
 
 #include <type_traits>
 
-#ifndef BFC_CHECKED
-#define BFC_CHECKED 1
-#endif
-
 namespace bfc {
 
 namespace {
@@ -262,9 +258,7 @@ __device__ __forceinline__ unsigned long long wedge_op(const CountParams &p, int
         c = get16(hcnt, slot);
     } else {
         const int idx = w - lb - lo;
-#if BFC_CHECKED
         if ((uint32_t)idx >= (uint32_t)span) { atomicOr(p.err, kErrBounds); return 0; }
-#endif
         if (!kSecond) return (KIND == kDenseWide) ? atomicAdd(w32 + idx, 1u) : inc16(w32, idx);
         c = (KIND == kDenseWide) ? w32[idx] : get16(w32, idx);
     }
@@ -359,14 +353,12 @@ __device__ unsigned long long team_walk(const CountParams &p, int32_t x, int32_t
         for (int i = 0; i < kPer; ++i) {
             len[i] = s1[i] - s0[i];
             src[i] = (Pos)(b[i] + s0[i]);
-#if BFC_CHECKED
             // every wedge of a run reads a slot in [b + s0, b + s1): checking
             // the run here covers the slot of each of its wedges
             if (len[i] > 0 && (b[i] + s0[i] < 0 || b[i] + s1[i] > p.adj_len)) {
                 atomicOr(p.err, kErrBounds);
                 len[i] = 0;
             }
-#endif
             if (len[i] < 0) len[i] = 0;
             // run length in the high bits, "non-empty" in the low 20 bits:
             // one scan yields both the run offsets and the compacted slots
@@ -738,9 +730,7 @@ __device__ unsigned long long warp_walk(const CountParams &p, int32_t x, int32_t
             if (k < total) {
                 const long long pos = wsrc[q] + k;
                 bool good = true;
-#if BFC_CHECKED
                 if (pos < 0 || pos >= p.adj_len) { atomicOr(p.err, kErrBounds); good = false; }
-#endif
                 const int32_t w = good ? __ldg(p.adj + pos) : 0;
                 const int slot = good ? hash_find(keys, mask, w - lb, !kSecond) : -1;
                 if (good && slot < 0) atomicOr(p.err, kErrHashFull);
