@@ -41,7 +41,7 @@ def _worker(rank, world, port, out):
 
 def test_two_rank_reduction_over_gloo():
     world = 2
-    out = mp.Manager().dict()
+    out = mp.get_context("spawn").Manager().dict()   # no fork of this (threaded) process
     mp.spawn(_worker, args=(world, _free_port(), out), nprocs=world, join=True)
     for rank in range(world):
         t, units, extra = out[rank]
