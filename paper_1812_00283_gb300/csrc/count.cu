@@ -106,6 +106,7 @@ struct SharedTeam {
     int item;
     int overflow;   // this item's table filled up
     int inserts;    // distinct ends inserted so far
+    int track;      // the item's bound lets its table pass 3/4 full: count inserts
 };
 
 __device__ __forceinline__ unsigned long long c2(unsigned long long c) {
@@ -252,7 +253,8 @@ __device__ __forceinline__ unsigned long long wedge_op(const CountParams &p, int
         }
         if (!kSecond) {
             // keep the load factor at most 3/4 so probes stay short
-            if (inserted && atomicAdd(ins, 1) >= (int)((hmask + 1) / 4 * 3)) *ovf = 1;
+            // (ins is null when the start cannot reach that load)
+            if (inserted && ins && atomicAdd(ins, 1) >= (int)((hmask + 1) / 4 * 3)) *ovf = 1;
             return inc16(hcnt, slot);
         }
         c = get16(hcnt, slot);
@@ -311,6 +313,7 @@ __device__ unsigned long long team_walk(const CountParams &p, int32_t x, int32_t
     const int32_t nmid = p.orient ? (int32_t)(p.off[x + 1] - e0) : p.cut[x];
     const int32_t span = hi - lo;
     const uint32_t le_mask = 0xffffffffu >> (31 - lane);
+    int *const ins = (KIND == kHash && !kSecond && sh.track) ? &sh.inserts : nullptr;
     unsigned long long acc = 0;
     for (int32_t mb = 0; mb < nmid; mb += kB) {
         int32_t len[kPer], v[kPer], pl[kPer];
@@ -403,7 +406,7 @@ __device__ unsigned long long team_walk(const CountParams &p, int32_t x, int32_t
 #pragma unroll
                 for (int u = 0; u < N; ++u) {
                     const unsigned long long r = wedge_op<MODE, KIND, kSecond, Pos>(
-                        p, w[u], base + (Pos)(32 * u), lb, lo, span, hmask, ctr, &sh.overflow, &sh.inserts);
+                        p, w[u], base + (Pos)(32 * u), lb, lo, span, hmask, ctr, &sh.overflow, ins);
                     if (KIND == kDenseWide) sum64 += r; else sum32 += (uint32_t)r;
                 }
                 if (!kSecond) {
@@ -462,13 +465,13 @@ __device__ unsigned long long team_walk(const CountParams &p, int32_t x, int32_t
                         if (ok[u]) {
                             const unsigned long long old =
                                 wedge_op<MODE, KIND, false, Pos>(p, w[u], pos[u], lb, lo, span, hmask,
-                                                                 ctr, &sh.overflow, &sh.inserts);
+                                                                 ctr, &sh.overflow, ins);
                             if (KIND == kDenseWide) acc += old; else acc32 += (uint32_t)old;
                         }
                     } else if (wb + u < wend) {   // warp-uniform: all lanes take part in run_add
                         const unsigned long long d =
                             ok[u] ? wedge_op<MODE, KIND, true, Pos>(p, w[u], pos[u], lb, lo, span, hmask,
-                                                                    ctr, &sh.overflow, &sh.inserts)
+                                                                    ctr, &sh.overflow, ins)
                                   : 0ull;
                         // 16-bit counts keep a window's δ sum below 2^21
                         if (KIND == kDenseWide) run_add<unsigned long long>(sh.msum, q[u], d, lane);
@@ -579,7 +582,11 @@ __device__ unsigned long long hash_item(const CountParams &p, int32_t x, unsigne
     while (cap < 2 * bound && cap < (uint32_t)max_slots) cap <<= 1;
     // hash tables hold 16-bit counts; a count is at most min(middles, work)
     const bool wide = middles(p, x) > (int64_t)kNarrowMaxCut && p.work[x] > (uint64_t)kNarrowMaxCut;
-    if (t.tid == 0) { sh.overflow = wide ? 1 : 0; sh.inserts = 0; }
+    if (t.tid == 0) {
+        sh.overflow = wide ? 1 : 0;
+        sh.inserts = 0;
+        sh.track = bound > (unsigned long long)(cap / 4 * 3) ? 1 : 0;
+    }
     team_fill(ctr, (int)cap * 4, 0xffffffffu, t);           // keys = -1
     team_fill(ctr + (size_t)cap * 4, (int)cap * 2, 0u, t);  // packed 16-bit counts
     t.sync();
