@@ -643,6 +643,21 @@ def main():
                     peak_source=peaks["source"],
                     algorithmic_bytes_per_launch=B, count_ms_median=1e3 * cnt_s)
 
+    # derived statistic (Section 1): caterpillars and the bipartite clustering
+    # coefficient 4·⋈ / caterpillars, on a prepared graph (outside the steps)
+    hd = bfc.bfc_prepare(r, l, m, off.data_ptr(), adj.data_ptr(), step_opts, sp)
+    cat_t = torch.zeros(1, dtype=torch.int64, device=dev)
+    bfc.bfc_caterpillars(hd, sp, cat_t.data_ptr())     # warm-up
+    ce0, ce1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ce0.record(stream)
+    bfc.bfc_caterpillars(hd, sp, cat_t.data_ptr())
+    ce1.record(stream)
+    bfc.bfc_sync(hd, sp)
+    bfc.bfc_release(hd)
+    cat = int(cat_t.item()) & ((1 << 64) - 1)
+    derived = dict(caterpillars=cat, clustering_coefficient=(4.0 * expect / cat) if cat else 0.0,
+                   caterpillars_ms=ce0.elapsed_time(ce1))
+
     # the second ceiling: one shared-memory counter increment per wedge
     # (first walk; the combined pass reads each counter again in its second)
     smem_rate, _ = bfc.bfc_bench_smem_atomics(sp, 16384)
@@ -723,7 +738,7 @@ def main():
             warmup=args.warmup, ms_per_step=t_total / args.steps, higher_is_better=True,
             scaling="weak", vs_baseline=None, dtype="u64", data="synthetic",
             config=dict(workload=WORKLOADS[args.workload], num_u=r, num_l=l, num_edges=m,
-                        wedges_per_step=W, butterflies=expect, graph=graph_stats(g),
+                        wedges_per_step=W, butterflies=expect, graph=graph_stats(g), derived=derived,
                         step="prepare (a1-a5) + count (a6-a7), CSR resident in HBM",
                         l2="flushed between steps (512 MB write outside the timed events)",
                         parallelism=f"replicas x{world} (independent graphs, no collective)",

@@ -334,6 +334,13 @@ int bfc_version(void);
  * (all devices, all threads). */
 long long bfc_kernel_launches(void);
 
+/* Caterpillars (three-paths) of the prepared graph, the denominator of the
+ * bipartite clustering coefficient 4·⋈_G / caterpillars named among the
+ * applications of Section 1: Σ over edges (u, v) of (deg u − 1)(deg v − 1),
+ * written as one uint64 to caterpillars_dev (device).  Asynchronous on
+ * `stream`; no allocation. */
+int bfc_caterpillars(bfc_graph *g, void *stream, uint64_t *caterpillars_dev);
+
 /* Measurement aid (no counterpart in the paper): the throughput of the
  * count kernel's counter operation on the current device -- a returning
  * 32-bit shared-memory atomicAdd on a 16-bit counter packed two per word, at

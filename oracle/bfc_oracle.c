@@ -619,3 +619,18 @@ int orc_degree_stats(int32_t r, int32_t l, const int32_t *off, const int32_t *ad
     graph_free(&g);
     return 0;
 }
+
+int orc_caterpillars(int32_t r, int32_t l, const int32_t *off, const int32_t *adj,
+                     uint64_t *caterpillars) {
+    graph_t g;
+    int rc = graph_build(r, l, off, adj, &g);
+    if (rc) return rc;
+    uint64_t c = 0;
+    for (int32_t u = 0; u < r; ++u) {
+        const uint64_t du = (uint64_t)g.deg[l + u];
+        for (int64_t k = off[u]; k < off[u + 1]; ++k) c += (du - 1) * ((uint64_t)g.deg[adj[k]] - 1);
+    }
+    *caterpillars = c;
+    graph_free(&g);
+    return 0;
+}

@@ -104,6 +104,13 @@ int orc_vppp(int32_t r, int32_t l, const int32_t *off, const int32_t *adj,
 int orc_degree_stats(int32_t r, int32_t l, const int32_t *off, const int32_t *adj,
                      uint64_t *tc_new, uint64_t *sum_du2, uint64_t *sum_dl2);
 
+/* Caterpillars (three-paths) of Section 1's bipartite clustering coefficient
+ * 4·⋈_G / caterpillars: a three-path a-b-c-d is fixed by its middle edge
+ * (b, c) and a choice of a in N(b) \ {c} and d in N(c) \ {b}, so the count is
+ * Σ_{(u,v) ∈ E} (deg u − 1)(deg v − 1). */
+int orc_caterpillars(int32_t r, int32_t l, const int32_t *off, const int32_t *adj,
+                     uint64_t *caterpillars);
+
 #ifdef __cplusplus
 }
 #endif

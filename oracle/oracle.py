@@ -63,6 +63,7 @@ def _load():
                            _u64p, _u64p],
                 "orc_vppp": [c.c_int32, c.c_int32, _i32p, _i32p, _u64p, _u64p],
                 "orc_degree_stats": [c.c_int32, c.c_int32, _i32p, _i32p, _u64p, _u64p, _u64p],
+                "orc_caterpillars": [c.c_int32, c.c_int32, _i32p, _i32p, _u64p],
             }
             for name, args in sig.items():
                 f = getattr(lib, name)
@@ -215,6 +216,39 @@ def degree_stats(g) -> tuple[int, int, int]:
                                     _p(a[0:], _u64p), _p(a[1:], _u64p), _p(a[2:], _u64p)),
            "degree_stats")
     return int(a[0]), int(a[1]), int(a[2])
+
+
+def caterpillars(g) -> int:
+    """Three-paths of the graph: Σ over edges of (deg u − 1)(deg v − 1)."""
+    off, adj = _csr(g)
+    a = np.zeros(1, dtype=np.uint64)
+    _check(_load().orc_caterpillars(g.num_u, g.num_l, _p(off, _i32p), _p(adj, _i32p), _p(a, _u64p)),
+           "caterpillars")
+    return int(a[0])
+
+
+def enumerate_three_paths(g) -> int:
+    """Three-paths a-b-c-d (three distinct edges, a path read either way counted
+    once) by walking every path from every vertex, for tiny graphs."""
+    if g.num_u > 60 or g.num_l > 60:
+        raise ValueError("exhaustive enumeration is for tiny graphs only")
+    u, v = g.edges()
+    nbr = {}
+    for a, b in zip(u.tolist(), v.tolist()):
+        nbr.setdefault(("U", a), set()).add(("L", b))
+        nbr.setdefault(("L", b), set()).add(("U", a))
+    paths = set()
+    for a in nbr:
+        for b in nbr[a]:
+            for c in nbr[b]:
+                if c == a:
+                    continue
+                for d in nbr[c]:
+                    if d == b:
+                        continue
+                    p = (a, b, c, d)
+                    paths.add(min(p, p[::-1]))
+    return len(paths)
 
 
 def enumerate_butterflies(g) -> dict:

@@ -107,6 +107,22 @@ class ButterflyGraph:
         return (pu[:self.num_u], pl[:self.num_l], pe[:self.num_edges],
                 int(self._total.item()) & ((1 << 64) - 1))
 
+    # -- derived statistics (Section 1) ----------------------------------------
+    def caterpillars(self, stream=None) -> int:
+        """Three-paths: Σ over edges (deg u − 1)(deg v − 1)."""
+        import torch
+        out = torch.zeros(1, dtype=torch.int64, device=self.device)
+        sp, _ = _stream(stream)
+        bfc = _lib()
+        bfc.bfc_caterpillars(self._h, sp, out.data_ptr())
+        bfc.bfc_sync(self._h, sp)
+        return int(out.item()) & ((1 << 64) - 1)
+
+    def clustering_coefficient(self, stream=None) -> float:
+        """Bipartite clustering coefficient 4·⋈_G / caterpillars (0 without three-paths)."""
+        c = self.caterpillars(stream)
+        return 4.0 * self.count(stream) / c if c else 0.0
+
     def info(self) -> dict:
         return _lib().bfc_graph_info(self._h)
 

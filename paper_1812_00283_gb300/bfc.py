@@ -97,6 +97,7 @@ _SIGS = {
     "bfc_last_error": (ctypes.c_char_p, []),
     "bfc_version": (c_int, []),
     "bfc_kernel_launches": (ctypes.c_longlong, []),
+    "bfc_caterpillars": (c_int, [c_void_p, c_void_p, c_void_p]),
     "bfc_bench_smem_atomics": (c_int, [c_void_p, c_int32, ctypes.POINTER(ctypes.c_double),
                                        ctypes.POINTER(ctypes.c_double)]),
     "bfc_prepare_batch": (c_int, [ctypes.POINTER(bfc_csr), ctypes.POINTER(bfc_batch),
@@ -287,6 +288,10 @@ def bfc_last_error() -> str:
 
 def bfc_version() -> int:
     return int(_lib.bfc_version())
+
+
+def bfc_caterpillars(g: int, stream: int, out_dev: int):
+    _check(_lib.bfc_caterpillars(g, stream, out_dev), "bfc_caterpillars")
 
 
 def bfc_kernel_launches() -> int:

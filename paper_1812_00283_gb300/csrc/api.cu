@@ -74,6 +74,11 @@ struct bfc_graph {
     Graph g;
 };
 
+namespace bfc {
+// the graph behind a handle, for entry points defined in other files
+const Graph *graph_of_handle(const bfc_graph *h) { return &h->g; }
+}  // namespace bfc
+
 static int check_options(const bfc_options *o) {
     if (o->warp_max_work < 0 || o->warp_max_work > bfc::kWarpMaxWork) {
         bfc::set_last_error("warp_max_work must lie in [0, " + std::to_string(bfc::kWarpMaxWork) + "]");

@@ -304,3 +304,28 @@ def test_invalid_graphs_rejected():
         with pytest.raises(BfcError) as ei:
             ButterflyGraph(torch.from_numpy(off).cuda(), torch.from_numpy(adj).cuda(), 4, 4)
         assert ei.value.status == 2, what
+
+
+# ---------------------------------------------------------------------------
+# derived statistics: caterpillars and the clustering coefficient (Section 1)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("gi", range(4))
+def test_caterpillars_and_clustering(gi):
+    from paper_1812_00283_gb300 import ButterflyGraph
+    g = [G.complete_bipartite(6, 9), G.uniform_small(), G.chung_lu_bipartite(20000, 8000, 150000, 2.1, 2.0, 48),
+         G.from_edges(5, 4, [], [])][gi]
+    adj = g.adj_u if g.num_edges else np.zeros(1, np.int32)
+    bg = ButterflyGraph(torch.from_numpy(g.off_u).cuda(), torch.from_numpy(adj).cuda()[:g.num_edges],
+                        g.num_u, g.num_l)
+    try:
+        cat = bg.caterpillars()
+        cc = bg.clustering_coefficient()
+    finally:
+        bg.release()
+    ref = oracle.caterpillars(g)
+    assert cat == ref
+    tot = oracle.vp(g)["total"]
+    assert cc == (4.0 * tot / ref if ref else 0.0)
+    if gi == 0:
+        assert cc == 1.0

@@ -110,6 +110,34 @@ def test_circulant_closed_form(p, c, n):
     assert oracle.vppp(g)[0] == tot
 
 
+# ---------------------------------------------------------------------------
+# caterpillars (three-paths) of the clustering coefficient (Section 1)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("a,b", [(1, 1), (2, 2), (3, 4), (5, 2)])
+def test_caterpillars_complete_bipartite(a, b):
+    # every edge of K_{a,b} is the middle of (a-1)(b-1) three-paths; the
+    # clustering coefficient 4·C(a,2)C(b,2) / (a b (a-1)(b-1)) is 1
+    g = G.complete_bipartite(a, b)
+    cat = oracle.caterpillars(g)
+    assert cat == a * b * (a - 1) * (b - 1) == oracle.enumerate_three_paths(g)
+    if cat:
+        assert 4 * oracle.vp(g)["total"] == cat
+
+
+def test_caterpillars_closed_forms():
+    assert oracle.caterpillars(G.cycle(7)) == 14            # C_14: one per edge
+    assert oracle.caterpillars(G.star(9)) == 0               # leaves end every path
+    assert oracle.caterpillars(G.path(6)) == 4               # a path of 6 edges holds 4
+    assert oracle.caterpillars(G.from_edges(3, 3, [], [])) == 0
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_caterpillars_against_enumeration(seed):
+    g = G.random_tiny(4 + seed % 5, 3 + seed % 6, 2, 5, 100 + seed)
+    assert oracle.caterpillars(g) == oracle.enumerate_three_paths(g)
+
+
 @pytest.mark.parametrize("k", [3, 4, 5, 10])
 def test_long_cycles_have_none(k):
     g = G.cycle(k)
