@@ -634,3 +634,50 @@ int orc_caterpillars(int32_t r, int32_t l, const int32_t *off, const int32_t *ad
     graph_free(&g);
     return 0;
 }
+
+static int cmp_u64(const void *a, const void *b) {
+    const uint64_t x = *(const uint64_t *)a, y = *(const uint64_t *)b;
+    return x < y ? -1 : x > y;
+}
+
+int orc_pairs_total(int32_t r, int32_t l, const int32_t *off, const int32_t *adj,
+                    uint64_t *total, uint64_t *pairs) {
+    graph_t g;
+    int rc = graph_build(r, l, off, adj, &g);
+    if (rc) return rc;
+    int32_t *p = malloc(sizeof(int32_t) * ((size_t)g.n + 1));
+    if (!p) { graph_free(&g); return -2; }
+    rc = compute_priority(&g, p);
+    if (rc) { free(p); graph_free(&g); return rc; }
+    /* first pass: how many pairs */
+    uint64_t np = 0;
+    for (int32_t v = 0; v < g.n; ++v)
+        for (int64_t i = g.off[v]; i < g.off[v + 1]; ++i) {
+            const int32_t w = g.adj[i];
+            if (p[w] <= p[v]) continue;
+            for (int64_t j = g.off[v]; j < g.off[v + 1]; ++j)
+                if (p[g.adj[j]] < p[w]) ++np;
+        }
+    uint64_t *key = malloc(sizeof(uint64_t) * (size_t)(np + 1));
+    if (!key) { free(p); graph_free(&g); return -2; }
+    uint64_t k = 0;
+    for (int32_t v = 0; v < g.n; ++v)
+        for (int64_t i = g.off[v]; i < g.off[v + 1]; ++i) {
+            const int32_t w = g.adj[i];
+            if (p[w] <= p[v]) continue;
+            for (int64_t j = g.off[v]; j < g.off[v + 1]; ++j) {
+                const int32_t u = g.adj[j];
+                if (p[u] < p[w]) key[k++] = ((uint64_t)(uint32_t)w << 32) | (uint32_t)u;
+            }
+        }
+    qsort(key, (size_t)np, sizeof(uint64_t), cmp_u64);
+    uint64_t t = 0, run = 0;
+    for (uint64_t i = 0; i < np; ++i) {
+        run = (i > 0 && key[i] == key[i - 1]) ? run + 1 : 1;
+        t += run - 1;   /* Σ over a run of c pairs of 0 + 1 + ... + (c - 1) = C(c, 2) */
+    }
+    *total = t;
+    *pairs = np;
+    free(key); free(p); graph_free(&g);
+    return 0;
+}

@@ -104,6 +104,14 @@ int orc_vppp(int32_t r, int32_t l, const int32_t *off, const int32_t *adj,
 int orc_degree_stats(int32_t r, int32_t l, const int32_t *off, const int32_t *adj,
                      uint64_t *tc_new, uint64_t *sum_du2, uint64_t *sum_dl2);
 
+/* Section 6.3's pair formulation (BFC-EM), in memory: for every middle v,
+ * each wedge (u, v, w) with p(w) > p(v) and p(w) > p(u) is written as the
+ * pair (w, u); the pairs are sorted and every run of c equal pairs gives
+ * C(c, 2) butterflies (Lemma 1).  *pairs = pairs written (= W, Lemma 4).
+ * Holds all pairs in memory: small graphs only. */
+int orc_pairs_total(int32_t r, int32_t l, const int32_t *off, const int32_t *adj,
+                    uint64_t *total, uint64_t *pairs);
+
 /* Caterpillars (three-paths) of Section 1's bipartite clustering coefficient
  * 4·⋈_G / caterpillars: a three-path a-b-c-d is fixed by its middle edge
  * (b, c) and a choice of a in N(b) \ {c} and d in N(c) \ {b}, so the count is

@@ -64,6 +64,7 @@ def _load():
                 "orc_vppp": [c.c_int32, c.c_int32, _i32p, _i32p, _u64p, _u64p],
                 "orc_degree_stats": [c.c_int32, c.c_int32, _i32p, _i32p, _u64p, _u64p, _u64p],
                 "orc_caterpillars": [c.c_int32, c.c_int32, _i32p, _i32p, _u64p],
+                "orc_pairs_total": [c.c_int32, c.c_int32, _i32p, _i32p, _u64p, _u64p],
             }
             for name, args in sig.items():
                 f = getattr(lib, name)
@@ -216,6 +217,15 @@ def degree_stats(g) -> tuple[int, int, int]:
                                     _p(a[0:], _u64p), _p(a[1:], _u64p), _p(a[2:], _u64p)),
            "degree_stats")
     return int(a[0]), int(a[1]), int(a[2])
+
+
+def pairs_total(g) -> tuple[int, int]:
+    """Section 6.3's pair formulation in memory: (total, pairs written)."""
+    off, adj = _csr(g)
+    a = np.zeros(2, dtype=np.uint64)
+    _check(_load().orc_pairs_total(g.num_u, g.num_l, _p(off, _i32p), _p(adj, _i32p), _p(a[0:], _u64p),
+                                   _p(a[1:], _u64p)), "pairs_total")
+    return int(a[0]), int(a[1])
 
 
 def caterpillars(g) -> int:

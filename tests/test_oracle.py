@@ -111,6 +111,21 @@ def test_circulant_closed_form(p, c, n):
 
 
 # ---------------------------------------------------------------------------
+# Section 6.3's pair formulation: a second exact path by sorting wedge pairs
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("gi", range(6))
+def test_pair_formulation_agrees(gi):
+    g = [G.complete_bipartite(4, 6), G.paper_fig3(), G.cycle(6), G.uniform_bipartite(300, 200, 3000, 11),
+         G.chung_lu_bipartite(800, 500, 6000, 2.1, 2.1, 13), G.random_tiny(9, 7, 3, 5, 21)][gi]
+    tot, pairs = oracle.pairs_total(g)
+    r = oracle.vp(g)
+    assert tot == r["total"] and pairs == r["wedges"]          # Lemma 1, Lemma 4
+    if gi == 0:
+        assert tot == c2(4) * c2(6)
+
+
+# ---------------------------------------------------------------------------
 # caterpillars (three-paths) of the clustering coefficient (Section 1)
 # ---------------------------------------------------------------------------
 
