@@ -21,6 +21,9 @@
 //                    is aggregated by exactly one item and C(count, 2) is
 //                    never split;
 //      hash (u)      an open-addressing table of up to 32,768 slots.
+//      Without a second walk the dense items are streamed: each item takes
+//      the next from the queue and clears the counters inside its first
+//      batch's scan, so warps that finish early start the next item's loads.
 //   B. team items: four teams of 256 threads, each with a 48 KB region (a
 //      4,096-slot table and its batch arrays), one start per team.
 //   C. warp items: 32 warps, each with a 512-slot table, one light start each.
@@ -107,6 +110,7 @@ struct SharedTeam {
     int overflow;   // this item's table filled up
     int inserts;    // distinct ends inserted so far
     int track;      // the item's bound lets its table pass 3/4 full: count inserts
+    int64_t next[2];  // streamed dense items: the item after the current one, by parity
 };
 
 __device__ __forceinline__ unsigned long long c2(unsigned long long c) {
@@ -285,204 +289,252 @@ __device__ __forceinline__ void run_add(unsigned long long *msum, int q, T x, in
     if ((lane == 31 || qn != q) && x) atomicAdd(msum + q, (unsigned long long)x);
 }
 
+// The per-thread state of one batch of middles that the second walk needs
+// after the windows: each middle's run length, id, slot and compacted index.
+template <typename Pos, int kThreads>
+struct BatchSlots {
+    static constexpr int kPer = Batch<Pos, kThreads>::kPer;
+    int32_t len[kPer], v[kPer];
+    int64_t e[kPer];
+    int nzs[kPer];
+};
+
+// Sets up one batch of the middles of x (those with index mb .. mb+kB-1):
+// the run of ends in range for each middle comes from the slot arrays (plus
+// the chunk-boundary table or a binary search for dense chunks); non-empty
+// runs are compacted into sh.start / sh.src by one team scan of packed
+// (length, non-empty) values.  The scan's first barrier is the point after
+// which every thread of the team has finished the previous windows, so
+// `zero_bytes` > 0 clears that many bytes of counters there.  Returns the
+// batch's wedge count in *total and its non-empty runs in *nnz; the entries
+// are visible to the team after its next barrier.
+template <bool kDense, bool kSecond, typename Pos, int kThreads, class SH>
+__device__ __forceinline__ void batch_runs(const CountParams &p, int64_t e0, int32_t nmid, int32_t mb,
+                                           int32_t lb, int32_t lo, int32_t hi, int flags,
+                                           unsigned char *ctr, int zero_bytes, SH &sh,
+                                           const Team<kThreads> &t, BatchSlots<Pos, kThreads> &bs,
+                                           int32_t *total_out, int *nnz_out) {
+    constexpr int kPer = Batch<Pos, kThreads>::kPer;
+    const int tid = t.tid;
+    int32_t pl[kPer];
+    Pos src[kPer];
+    int64_t b[kPer];
+    bool has[kPer];
+    // the slot loads of all of this thread's middles first, then the
+    // chunk-boundary loads that depend on them: two rounds of latency
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) {
+        const int32_t j = mb + i * kThreads + tid;
+        has[i] = j < nmid;
+        bs.e[i] = has[i] ? e0 + j : e0;
+        bs.v[i] = has[i] ? __ldg(p.adj + bs.e[i]) : 0;
+        pl[i] = has[i] ? __ldg(p.plen + bs.e[i]) : 0;
+        // run of ends: prefix of N(v) below x (Algorithm 2) or the
+        // suffix above both x and v (Algorithm 3)
+        b[i] = has[i] ? __ldg(p.sbeg + bs.e[i]) : 0;
+    }
+    int32_t s0[kPer], s1[kPer];
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) {
+        s0[i] = 0;
+        s1[i] = pl[i];
+        if (kDense && has[i] && pl[i] > 0) {
+            if (p.coff) {
+                const int32_t v = bs.v[i];
+                const int64_t tb = v < p.l ? (int64_t)v * p.coff_u1
+                                           : (int64_t)p.l * p.coff_u1 + (int64_t)(v - p.l) * p.coff_l1;
+                if (flags & 1) s0[i] = __ldg(p.coff + tb + lo / kChunkUnit);
+                if (flags & 2) s1[i] = __ldg(p.coff + tb + hi / kChunkUnit);
+            } else {
+                if (flags & 1) s0[i] = lower_bound_g(p.adj + b[i], pl[i], lb + lo);
+                if (flags & 2) s1[i] = lower_bound_g(p.adj + b[i], pl[i], lb + hi);
+            }
+        }
+    }
+    long long packed_run = 0;
+    long long pk[kPer];
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) {
+        int32_t len = s1[i] - s0[i];
+        src[i] = (Pos)(b[i] + s0[i]);
+        // every wedge of a run reads a slot in [b + s0, b + s1): checking
+        // the run here covers the slot of each of its wedges
+        if (len > 0 && (b[i] + s0[i] < 0 || b[i] + s1[i] > p.adj_len)) {
+            atomicOr(p.err, kErrBounds);
+            len = 0;
+        }
+        if (len < 0) len = 0;
+        bs.len[i] = len;
+        // run length in the high bits, "non-empty" in the low 20 bits:
+        // one scan yields both the run offsets and the compacted slots
+        pk[i] = ((long long)len << 20) | (len > 0 ? 1 : 0);
+        packed_run += pk[i];
+    }
+    long long packed_total;
+    long long packed = team_excl_scan(packed_run, sh, t, &packed_total);
+    if (zero_bytes > 0) team_fill(ctr, zero_bytes, 0u, t);
+    const int32_t total = (int32_t)(packed_total >> 20);
+    const int nnz = (int)(packed_total & 0xfffff);
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) {
+        const int32_t excl = (int32_t)(packed >> 20);
+        bs.nzs[i] = (int)(packed & 0xfffff);
+        if (bs.len[i] > 0) {
+            sh.start[bs.nzs[i]] = excl;
+            sh.src[bs.nzs[i]] = src[i] - (Pos)excl;
+            if (kSecond) sh.msum[bs.nzs[i]] = 0;
+        }
+        packed += pk[i];
+    }
+    if (tid <= 32) sh.start[nnz + tid] = tid == 0 ? total : 0x7fffffff;
+    *total_out = total;
+    *nnz_out = nnz;
+}
+
+// The windows of one compacted batch.  The concatenated runs are cut into
+// windows of 32 wedges and each warp takes a contiguous range of windows.
+// Inside a window the run of every lane is found from a 32-bit mask of run
+// starts (reduce-or + popc), so no search is needed per wedge, and four
+// windows are in flight per iteration so their end loads overlap.
+// kSecond = false: count (returns Σ old, i.e. Σ C(count, 2)).
+// kSecond = true : read the final counts and attribute δ = count − 1.
+template <int MODE, int KIND, bool kSecond, typename Pos, int kThreads, class SH>
+__device__ __forceinline__ unsigned long long batch_windows(const CountParams &p, int32_t lb, int32_t lo,
+                                                            int32_t span, uint32_t hmask,
+                                                            unsigned char *ctr, int32_t total, int nnz,
+                                                            int *ins, SH &sh, const Team<kThreads> &t) {
+    constexpr int kWarps = kThreads / 32;
+    constexpr int kU = 4;
+    const int lane = t.tid & 31, warp = t.tid >> 5;
+    const uint32_t le_mask = 0xffffffffu >> (31 - lane);
+    unsigned long long acc = 0;
+    const int32_t nwin = (total + 31) >> 5;
+    int32_t wb = (int32_t)(((int64_t)warp * nwin) / kWarps);
+    const int32_t wend = (int32_t)(((int64_t)(warp + 1) * nwin) / kWarps);
+    if (wb < wend) {
+        int32_t k0 = wb << 5;
+        int q0 = last_le(sh.start, nnz, k0);
+        // Fast path: the next N windows lie inside run q0 (most wedges do, as
+        // runs of heavy starts are long), so the slots are consecutive, no
+        // run lookup is needed and N loads are in flight per lane.
+        auto fast = [&](auto n_windows, int32_t next_run) {
+            constexpr int N = decltype(n_windows)::value;
+            const Pos base = sh.src[q0] + (Pos)(k0 + lane);
+            int32_t w[N];
+#pragma unroll
+            for (int u = 0; u < N; ++u) w[u] = __ldg(p.adj + base + (Pos)(32 * u));
+            uint32_t sum32 = 0;   // N olds (or δ) of 16-bit counts stay below 2^20
+            unsigned long long sum64 = 0;
+#pragma unroll
+            for (int u = 0; u < N; ++u) {
+                const unsigned long long r = wedge_op<MODE, KIND, kSecond, Pos>(
+                    p, w[u], base + (Pos)(32 * u), lb, lo, span, hmask, ctr, &sh.overflow, ins);
+                if (KIND == kDenseWide) sum64 += r; else sum32 += (uint32_t)r;
+            }
+            if (!kSecond) {
+                acc += (KIND == kDenseWide) ? sum64 : (unsigned long long)sum32;
+            } else if (KIND == kDenseWide) {
+                run_add<unsigned long long>(sh.msum, q0, sum64, lane);
+            } else {
+                // one run: the warp's δ sum goes to middle q0
+                const uint32_t tot = __reduce_add_sync(0xffffffffu, sum32);
+                if (lane == 0 && tot) atomicAdd(sh.msum + q0, (unsigned long long)tot);
+            }
+            if (next_run == k0 + 32 * N) ++q0;   // the next window starts run q0 + 1
+            k0 += 32 * N;
+            wb += N;
+        };
+        while (wb < wend) {
+            const int32_t next_run = sh.start[q0 + 1];   // warp-uniform
+            if (wb + 2 * kU <= wend && next_run >= k0 + 64 * kU) {
+                fast(std::integral_constant<int, 2 * kU>(), next_run);
+                continue;
+            }
+            if (wb + kU <= wend && next_run >= k0 + 32 * kU) {
+                fast(std::integral_constant<int, kU>(), next_run);
+                continue;
+            }
+            int q[kU];
+            Pos pos[kU];
+            bool ok[kU];
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                q[u] = 0;
+                ok[u] = false;
+                pos[u] = 0;
+                if (wb + u < wend) {   // warp-uniform
+                    const int32_t kw = k0 + 32 * u;
+                    // run starts after this window's first wedge: 1 <= d, and
+                    // the sentinels keep the index below nnz + 33
+                    const int32_t d = sh.start[q0 + 1 + lane] - kw;
+                    uint32_t bit;   // 1 << d, 0 once d >= 32 (PTX clamps the shift)
+                    asm("shl.b32 %0, %1, %2;" : "=r"(bit) : "r"(1u), "r"(d));
+                    const uint32_t m = __reduce_or_sync(0xffffffffu, bit);
+                    q[u] = q0 + __popc(m & le_mask);
+                    q0 += __popc(__ballot_sync(0xffffffffu, d <= 32));
+                    ok[u] = kw + lane < total;
+                    if (ok[u]) pos[u] = sh.src[q[u]] + (Pos)(kw + lane);
+                }
+            }
+            int32_t w[kU];
+#pragma unroll
+            for (int u = 0; u < kU; ++u) w[u] = ok[u] ? __ldg(p.adj + pos[u]) : 0;
+            // counts below 2^16 keep four olds far below 2^32
+            uint32_t acc32 = 0;
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                if (!kSecond) {
+                    if (ok[u]) {
+                        const unsigned long long old =
+                            wedge_op<MODE, KIND, false, Pos>(p, w[u], pos[u], lb, lo, span, hmask,
+                                                             ctr, &sh.overflow, ins);
+                        if (KIND == kDenseWide) acc += old; else acc32 += (uint32_t)old;
+                    }
+                } else if (wb + u < wend) {   // warp-uniform: all lanes take part in run_add
+                    const unsigned long long d =
+                        ok[u] ? wedge_op<MODE, KIND, true, Pos>(p, w[u], pos[u], lb, lo, span, hmask,
+                                                                ctr, &sh.overflow, ins)
+                              : 0ull;
+                    // 16-bit counts keep a window's δ sum below 2^21
+                    if (KIND == kDenseWide) run_add<unsigned long long>(sh.msum, q[u], d, lane);
+                    else run_add<uint32_t>(sh.msum, q[u], (uint32_t)d, lane);
+                }
+            }
+            if (KIND != kDenseWide) acc += acc32;
+            k0 += 32 * kU;
+            wb += kU;
+        }
+    }
+    return acc;
+}
+
 // One walk over the wedges of start x whose ends fall in [lb+lo, lb+hi).
 // kSecond = false: count (returns Σ old, i.e. Σ C(count, 2)).
 // kSecond = true : read the final counts and attribute δ = count − 1.
 // flags: bit 0 = cut the runs below lb+lo, bit 1 = cut them at lb+hi.
-//
 // The middles of x are taken a batch at a time (two per thread, or one with
-// 64-bit positions).  For each middle the run of ends in range comes from the
-// slot arrays (plus the chunk-boundary table or a binary search for dense
-// chunks).  Non-empty runs are compacted and their concatenation is cut into
-// windows of 32 wedges; each warp takes a contiguous range of windows.  Inside
-// a window the run of every lane is found from a 32-bit mask of run starts
-// (reduce-or + popc), so no search is needed per wedge, and four windows are
-// in flight per iteration so their end loads overlap.
+// 64-bit positions): batch_runs, a barrier, batch_windows.
 template <int MODE, int KIND, bool kSecond, typename Pos, int kThreads, class SH>
 __device__ unsigned long long team_walk(const CountParams &p, int32_t x, int32_t lb, int32_t lo,
                                         int32_t hi, int flags, uint32_t hmask, unsigned char *ctr,
                                         SH &sh, const Team<kThreads> &t) {
     constexpr int kPer = Batch<Pos, kThreads>::kPer;
     constexpr int kB = Batch<Pos, kThreads>::kSize;
-    constexpr int kWarps = kThreads / 32;
-    constexpr int kU = 4;
-    const int tid = t.tid, lane = tid & 31, warp = tid >> 5;
     const int64_t e0 = p.off[x];
     // Algorithm 2: the middles are the cut[x] lower-priority neighbours;
     // Algorithm 3: every neighbour is a middle
     const int32_t nmid = p.orient ? (int32_t)(p.off[x + 1] - e0) : p.cut[x];
     const int32_t span = hi - lo;
-    const uint32_t le_mask = 0xffffffffu >> (31 - lane);
     int *const ins = (KIND == kHash && !kSecond && sh.track) ? &sh.inserts : nullptr;
     unsigned long long acc = 0;
     for (int32_t mb = 0; mb < nmid; mb += kB) {
-        int32_t len[kPer], v[kPer], pl[kPer];
-        Pos src[kPer];
-        int64_t e[kPer], b[kPer];
-        bool has[kPer];
-        // the slot loads of all of this thread's middles first, then the
-        // chunk-boundary loads that depend on them: two rounds of latency
-#pragma unroll
-        for (int i = 0; i < kPer; ++i) {
-            const int32_t j = mb + i * kThreads + tid;
-            has[i] = j < nmid;
-            e[i] = has[i] ? e0 + j : e0;
-            v[i] = has[i] ? __ldg(p.adj + e[i]) : 0;
-            pl[i] = has[i] ? __ldg(p.plen + e[i]) : 0;
-            // run of ends: prefix of N(v) below x (Algorithm 2) or the
-            // suffix above both x and v (Algorithm 3)
-            b[i] = has[i] ? __ldg(p.sbeg + e[i]) : 0;
-        }
-        int32_t s0[kPer], s1[kPer];
-#pragma unroll
-        for (int i = 0; i < kPer; ++i) {
-            s0[i] = 0;
-            s1[i] = pl[i];
-            if (KIND != kHash && has[i] && pl[i] > 0) {
-                if (p.coff) {
-                    const int64_t tb = v[i] < p.l ? (int64_t)v[i] * p.coff_u1
-                                                  : (int64_t)p.l * p.coff_u1 + (int64_t)(v[i] - p.l) * p.coff_l1;
-                    if (flags & 1) s0[i] = __ldg(p.coff + tb + lo / kChunkUnit);
-                    if (flags & 2) s1[i] = __ldg(p.coff + tb + hi / kChunkUnit);
-                } else {
-                    if (flags & 1) s0[i] = lower_bound_g(p.adj + b[i], pl[i], lb + lo);
-                    if (flags & 2) s1[i] = lower_bound_g(p.adj + b[i], pl[i], lb + hi);
-                }
-            }
-        }
-        long long packed_run = 0;
-        long long pk[kPer];
-#pragma unroll
-        for (int i = 0; i < kPer; ++i) {
-            len[i] = s1[i] - s0[i];
-            src[i] = (Pos)(b[i] + s0[i]);
-            // every wedge of a run reads a slot in [b + s0, b + s1): checking
-            // the run here covers the slot of each of its wedges
-            if (len[i] > 0 && (b[i] + s0[i] < 0 || b[i] + s1[i] > p.adj_len)) {
-                atomicOr(p.err, kErrBounds);
-                len[i] = 0;
-            }
-            if (len[i] < 0) len[i] = 0;
-            // run length in the high bits, "non-empty" in the low 20 bits:
-            // one scan yields both the run offsets and the compacted slots
-            pk[i] = ((long long)len[i] << 20) | (len[i] > 0 ? 1 : 0);
-            packed_run += pk[i];
-        }
-        long long packed_total;
-        long long packed = team_excl_scan(packed_run, sh, t, &packed_total);
-        const int32_t total = (int32_t)(packed_total >> 20);
-        const int nnz = (int)(packed_total & 0xfffff);
-        int nzs[kPer];
-#pragma unroll
-        for (int i = 0; i < kPer; ++i) {
-            const int32_t excl = (int32_t)(packed >> 20);
-            nzs[i] = (int)(packed & 0xfffff);
-            if (len[i] > 0) {
-                sh.start[nzs[i]] = excl;
-                sh.src[nzs[i]] = src[i] - (Pos)excl;
-                if (kSecond) sh.msum[nzs[i]] = 0;
-            }
-            packed += pk[i];
-        }
-        if (tid <= 32) sh.start[nnz + tid] = tid == 0 ? total : 0x7fffffff;
+        BatchSlots<Pos, kThreads> bs;
+        int32_t total;
+        int nnz;
+        batch_runs<KIND != kHash, kSecond, Pos>(p, e0, nmid, mb, lb, lo, hi, flags, ctr, 0, sh, t, bs,
+                                                 &total, &nnz);
         t.sync();
-        const int32_t nwin = (total + 31) >> 5;
-        int32_t wb = (int32_t)(((int64_t)warp * nwin) / kWarps);
-        const int32_t wend = (int32_t)(((int64_t)(warp + 1) * nwin) / kWarps);
-        if (wb < wend) {
-            int32_t k0 = wb << 5;
-            int q0 = last_le(sh.start, nnz, k0);
-            // Fast path: the next N windows lie inside run q0 (most wedges do, as
-            // runs of heavy starts are long), so the slots are consecutive, no
-            // run lookup is needed and N loads are in flight per lane.
-            auto fast = [&](auto n_windows, int32_t next_run) {
-                constexpr int N = decltype(n_windows)::value;
-                const Pos base = sh.src[q0] + (Pos)(k0 + lane);
-                int32_t w[N];
-#pragma unroll
-                for (int u = 0; u < N; ++u) w[u] = __ldg(p.adj + base + (Pos)(32 * u));
-                uint32_t sum32 = 0;   // N olds (or δ) of 16-bit counts stay below 2^20
-                unsigned long long sum64 = 0;
-#pragma unroll
-                for (int u = 0; u < N; ++u) {
-                    const unsigned long long r = wedge_op<MODE, KIND, kSecond, Pos>(
-                        p, w[u], base + (Pos)(32 * u), lb, lo, span, hmask, ctr, &sh.overflow, ins);
-                    if (KIND == kDenseWide) sum64 += r; else sum32 += (uint32_t)r;
-                }
-                if (!kSecond) {
-                    acc += (KIND == kDenseWide) ? sum64 : (unsigned long long)sum32;
-                } else if (KIND == kDenseWide) {
-                    run_add<unsigned long long>(sh.msum, q0, sum64, lane);
-                } else {
-                    // one run: the warp's δ sum goes to middle q0
-                    const uint32_t tot = __reduce_add_sync(0xffffffffu, sum32);
-                    if (lane == 0 && tot) atomicAdd(sh.msum + q0, (unsigned long long)tot);
-                }
-                if (next_run == k0 + 32 * N) ++q0;   // the next window starts run q0 + 1
-                k0 += 32 * N;
-                wb += N;
-            };
-            while (wb < wend) {
-                const int32_t next_run = sh.start[q0 + 1];   // warp-uniform
-                if (wb + 2 * kU <= wend && next_run >= k0 + 64 * kU) {
-                    fast(std::integral_constant<int, 2 * kU>(), next_run);
-                    continue;
-                }
-                if (wb + kU <= wend && next_run >= k0 + 32 * kU) {
-                    fast(std::integral_constant<int, kU>(), next_run);
-                    continue;
-                }
-                int q[kU];
-                Pos pos[kU];
-                bool ok[kU];
-#pragma unroll
-                for (int u = 0; u < kU; ++u) {
-                    q[u] = 0;
-                    ok[u] = false;
-                    pos[u] = 0;
-                    if (wb + u < wend) {   // warp-uniform
-                        const int32_t kw = k0 + 32 * u;
-                        // run starts after this window's first wedge: 1 <= d, and
-                        // the sentinels keep the index below nnz + 33
-                        const int32_t d = sh.start[q0 + 1 + lane] - kw;
-                        uint32_t bit;   // 1 << d, 0 once d >= 32 (PTX clamps the shift)
-                        asm("shl.b32 %0, %1, %2;" : "=r"(bit) : "r"(1u), "r"(d));
-                        const uint32_t m = __reduce_or_sync(0xffffffffu, bit);
-                        q[u] = q0 + __popc(m & le_mask);
-                        q0 += __popc(__ballot_sync(0xffffffffu, d <= 32));
-                        ok[u] = kw + lane < total;
-                        if (ok[u]) pos[u] = sh.src[q[u]] + (Pos)(kw + lane);
-                    }
-                }
-                int32_t w[kU];
-#pragma unroll
-                for (int u = 0; u < kU; ++u) w[u] = ok[u] ? __ldg(p.adj + pos[u]) : 0;
-                // counts below 2^16 keep four olds far below 2^32
-                uint32_t acc32 = 0;
-#pragma unroll
-                for (int u = 0; u < kU; ++u) {
-                    if (!kSecond) {
-                        if (ok[u]) {
-                            const unsigned long long old =
-                                wedge_op<MODE, KIND, false, Pos>(p, w[u], pos[u], lb, lo, span, hmask,
-                                                                 ctr, &sh.overflow, ins);
-                            if (KIND == kDenseWide) acc += old; else acc32 += (uint32_t)old;
-                        }
-                    } else if (wb + u < wend) {   // warp-uniform: all lanes take part in run_add
-                        const unsigned long long d =
-                            ok[u] ? wedge_op<MODE, KIND, true, Pos>(p, w[u], pos[u], lb, lo, span, hmask,
-                                                                    ctr, &sh.overflow, ins)
-                                  : 0ull;
-                        // 16-bit counts keep a window's δ sum below 2^21
-                        if (KIND == kDenseWide) run_add<unsigned long long>(sh.msum, q[u], d, lane);
-                        else run_add<uint32_t>(sh.msum, q[u], (uint32_t)d, lane);
-                    }
-                }
-                if (KIND != kDenseWide) acc += acc32;
-                k0 += 32 * kU;
-                wb += kU;
-            }
-        }
+        acc += batch_windows<MODE, KIND, kSecond, Pos>(p, lb, lo, span, hmask, ctr, total, nnz, ins, sh, t);
         // Dense counting needs no join here: the next batch's scan barriers
         // come before its compaction overwrites the run arrays, so warps that
         // finish their windows early already load the next batch's slots.
@@ -491,11 +543,11 @@ __device__ unsigned long long team_walk(const CountParams &p, int32_t x, int32_t
         if (kSecond) {
 #pragma unroll
             for (int i = 0; i < kPer; ++i) {
-                if (len[i] > 0) {
-                    const unsigned long long dsum = sh.msum[nzs[i]];
+                if (bs.len[i] > 0) {
+                    const unsigned long long dsum = sh.msum[bs.nzs[i]];
                     if (dsum) {
-                        if (wants_vertices(MODE)) atomicAdd(p.pv + v[i], dsum);
-                        if (wants_edges(MODE)) atomicAdd(p.pe + __ldg(p.eid + e[i]), dsum);
+                        if (wants_vertices(MODE)) atomicAdd(p.pv + bs.v[i], dsum);
+                        if (wants_edges(MODE)) atomicAdd(p.pe + __ldg(p.eid + bs.e[i]), dsum);
                     }
                 }
             }
@@ -667,6 +719,69 @@ __device__ unsigned long long cta_item(const CountParams &p, int2 item, unsigned
     return acc;
 }
 
+// Phase A's dense items when there is no second walk, streamed: the first
+// batch of each item takes the next item from the queue and clears the
+// counters after its scan's first barrier (by then every warp has left the
+// previous item's windows), so a warp that finishes its windows early goes
+// straight on to the next item's slot loads, and an item of one batch costs
+// three barriers.  `it` is the current item (dense, the same in every thread);
+// on return it is the first item that is not dense, or past the queue.  The
+// caller joins before it reuses the counters' memory.
+template <int MODE, typename Pos, class SH>
+__device__ unsigned long long dense_stream(const CountParams &p, int64_t &it, unsigned char *ctr,
+                                           SH &sh, const Team<kCountThreads> &t) {
+    constexpr int kB = Batch<Pos, kCountThreads>::kSize;
+    unsigned long long acc = 0;
+    int par = 0;
+    int2 item = p.cta_items[it];
+    for (;;) {
+        const int32_t x = item.x;
+        const int32_t lb = range_lo(p, x);
+        const int32_t R = x - lb;   // the ends are the R vertices below x
+        const bool wide = (uint32_t)p.cut[x] > kNarrowMaxCut;
+        const int32_t S = wide ? kDense32 : kDense16;
+        const int32_t lo = item.y * S;
+        const int32_t hi = min(R, lo + S);
+        const int32_t span = hi - lo;
+        const int flags = (lo > 0 ? 1 : 0) | (hi < R ? 2 : 0);
+        const int64_t e0 = p.off[x];
+        const int32_t nmid = p.cut[x];
+        unsigned long long item_acc = 0;
+        int32_t mb = 0;
+        do {
+            // sh.next[par] is written before this batch's barriers and read at
+            // the end of the item; the next write to it comes two items later,
+            // after every warp has passed the next item's barriers
+            if (mb == 0 && t.tid == 0) sh.next[par] = atomicAdd(p.cursors, 1);
+            BatchSlots<Pos, kCountThreads> bs;
+            int32_t total;
+            int nnz;
+            const int zero_bytes = mb > 0 ? 0 : (wide ? span * 4 : ((span + 1) >> 1) * 4);
+            batch_runs<true, false, Pos>(p, e0, nmid, mb, lb, lo, hi, flags, ctr, zero_bytes, sh, t, bs,
+                                         &total, &nnz);
+            t.sync();
+            item_acc += wide ? batch_windows<MODE, kDenseWide, false, Pos>(p, lb, lo, span, 0, ctr, total,
+                                                                          nnz, nullptr, sh, t)
+                             : batch_windows<MODE, kDenseNarrow, false, Pos>(p, lb, lo, span, 0, ctr, total,
+                                                                            nnz, nullptr, sh, t);
+            mb += kB;
+        } while (mb < nmid);
+        if (MODE == kModeBatch) {
+            // this warp's share of x's butterflies goes to x's graph
+            unsigned long long w = item_acc;
+#pragma unroll
+            for (int d = 16; d > 0; d >>= 1) w += __shfl_xor_sync(0xffffffffu, w, d);
+            if ((t.tid & 31) == 0 && w) atomicAdd(p.gtot + p.gstar[x], w);
+        }
+        acc += item_acc;
+        it = sh.next[par];
+        par ^= 1;
+        if (it >= p.n_cta) return acc;
+        item = p.cta_items[it];
+        if (item.y < 0) return acc;
+    }
+}
+
 // ---- phase B: team items ----------------------------------------------------------
 template <int MODE, typename Pos, class SH>
 __device__ unsigned long long team_item(const CountParams &p, int32_t x, unsigned char *table,
@@ -819,14 +934,22 @@ __global__ void __launch_bounds__(kCountThreads, kCountCtasPerSm) k_count(CountP
     __shared__ SharedTeam<MODE, Pos, kCountThreads> sh;
     const Team<kCountThreads> cta{(int)threadIdx.x, 0};
     unsigned long long acc = 0;
-    // phase A: CTA items, heaviest first
-    for (;;) {
+    // phase A: CTA items, heaviest first (the dense items, then the hash items)
+    if (threadIdx.x == 0) sh.item = atomicAdd(p.cursors, 1);
+    __syncthreads();
+    int64_t it = sh.item;
+    __syncthreads();
+    while (it < p.n_cta) {
+        if (!has_second_walk(MODE) && p.cta_items[it].y >= 0) {
+            acc += dense_stream<MODE, Pos>(p, it, ctr, sh, cta);
+            __syncthreads();   // join: the last item's slowest warps
+            continue;
+        }
+        acc += cta_item<MODE, Pos>(p, p.cta_items[it], ctr, sh, cta);
         if (threadIdx.x == 0) sh.item = atomicAdd(p.cursors, 1);
         __syncthreads();
-        const int64_t it = sh.item;
+        it = sh.item;
         __syncthreads();
-        if (it >= p.n_cta) break;
-        acc += cta_item<MODE, Pos>(p, p.cta_items[it], ctr, sh, cta);
     }
     // phase B: team items.  Team k owns warps 8k..8k+7 and the 48 KB of shared
     // memory that are their warp regions; its table is followed by its batch
