@@ -331,11 +331,11 @@ def count_kernel_hash() -> str:
     return h.hexdigest()
 
 
-def recorded_traffic(workload: str, outputs: str = "total"):
+def recorded_traffic(workload: str, outputs: str = "total", orientation: int = 0):
     """DRAM bytes per count launch from a committed ncu summary, if it was
-    taken on this workload and outputs with the current kernel source (or
-    scaled from a smaller case of the same kernel, as the entry says); else
-    None."""
+    taken on this workload, outputs and orientation (Algorithm 2 or 3) with
+    the current kernel source (or scaled from a smaller case of the same
+    kernel, as the entry says); else None."""
     p = os.path.join(ROOT, "profiles", "count_traffic.json")
     if not os.path.exists(p):
         return None
@@ -343,7 +343,7 @@ def recorded_traffic(workload: str, outputs: str = "total"):
         d = json.load(f)
     for e in d.get("entries", []):
         if (e.get("source_sha256") == count_kernel_hash() and e.get("workload") == workload
-                and e.get("outputs", "total") == outputs):
+                and e.get("outputs", "total") == outputs and e.get("orientation", 0) == orientation):
             return int(e["dram_bytes_per_launch"])
     return None
 
@@ -636,7 +636,7 @@ def main():
     cnt_s = statistics.median(count_ms) / 1e3
     B = algorithmic_bytes(W, m, n, outputs)
     achieved = B / cnt_s / 1e9
-    traffic = recorded_traffic(args.workload, outputs)
+    traffic = recorded_traffic(args.workload, outputs, args.orientation)
     roofline = dict(bound="hbm", achieved=achieved, peak=peaks["hbm_gbs"], unit="GB/s",
                     frac=achieved / peaks["hbm_gbs"], traffic=traffic,
                     kernel="k_count (bfc_count_all)" if outputs == "all" else "k_count (bfc_count)",
