@@ -681,3 +681,41 @@ int orc_pairs_total(int32_t r, int32_t l, const int32_t *off, const int32_t *adj
     free(key); free(p); graph_free(&g);
     return 0;
 }
+
+int orc_vp_chunked(int32_t r, int32_t l, const int32_t *off, const int32_t *adj, int32_t chunk,
+                   uint64_t *total) {
+    if (chunk < 1) return -1;
+    graph_t g;
+    int rc = graph_build(r, l, off, adj, &g);
+    if (rc) return rc;
+    const int32_t n = g.n;
+    int32_t *p = malloc(sizeof(int32_t) * ((size_t)n + 1));
+    uint32_t *count_wedge = calloc((size_t)n + 1, sizeof(uint32_t));
+    if (!p || !count_wedge) { free(p); free(count_wedge); graph_free(&g); return -2; }
+    rc = compute_priority(&g, p);
+    if (rc) { free(p); free(count_wedge); graph_free(&g); return rc; }
+    uint64_t t = 0;
+    for (int32_t u = 0; u < n; ++u) {
+        /* ends of u have priorities 1 .. p(u) - 1: ranges [lo, lo + chunk) */
+        for (int32_t lo = 1; lo < p[u]; lo += chunk) {
+            const int32_t hi = lo + chunk;
+            for (int64_t i = g.off[u]; i < g.off[u + 1]; ++i) {
+                const int32_t v = g.adj[i];
+                if (!(p[v] < p[u])) continue;
+                for (int64_t j = g.off[v]; j < g.off[v + 1]; ++j) {
+                    const int32_t w = g.adj[j];
+                    if (p[w] < p[u] && p[w] >= lo && p[w] < hi) count_wedge[w] += 1;
+                }
+            }
+            /* the range's pairs, then clear its counters */
+            for (int32_t w = 0; w < n; ++w) {
+                const uint64_t c = count_wedge[w];
+                if (c > 1) t += c * (c - 1) / 2;
+                count_wedge[w] = 0;
+            }
+        }
+    }
+    *total = t;
+    free(p); free(count_wedge); graph_free(&g);
+    return 0;
+}

@@ -104,6 +104,15 @@ int orc_vppp(int32_t r, int32_t l, const int32_t *off, const int32_t *adj,
 int orc_degree_stats(int32_t r, int32_t l, const int32_t *off, const int32_t *adj,
                      uint64_t *tc_new, uint64_t *sum_du2, uint64_t *sum_dl2);
 
+/* Algorithm 2 with every start's END set cut into ranges of `chunk`
+ * consecutive priorities, each range counted with its own counters (the
+ * split of one heavy start over several workers that Section 6.2 leaves
+ * open).  Every pair (u, w) falls in one range, so C(count, 2) is applied
+ * to whole counts and the total equals Algorithm 2's.  Plain loops over
+ * every range and every wedge: tiny graphs only. */
+int orc_vp_chunked(int32_t r, int32_t l, const int32_t *off, const int32_t *adj, int32_t chunk,
+                   uint64_t *total);
+
 /* Section 6.3's pair formulation (BFC-EM), in memory: for every middle v,
  * each wedge (u, v, w) with p(w) > p(v) and p(w) > p(u) is written as the
  * pair (w, u); the pairs are sorted and every run of c equal pairs gives

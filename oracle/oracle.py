@@ -65,6 +65,7 @@ def _load():
                 "orc_degree_stats": [c.c_int32, c.c_int32, _i32p, _i32p, _u64p, _u64p, _u64p],
                 "orc_caterpillars": [c.c_int32, c.c_int32, _i32p, _i32p, _u64p],
                 "orc_pairs_total": [c.c_int32, c.c_int32, _i32p, _i32p, _u64p, _u64p],
+                "orc_vp_chunked": [c.c_int32, c.c_int32, _i32p, _i32p, c.c_int32, _u64p],
             }
             for name, args in sig.items():
                 f = getattr(lib, name)
@@ -217,6 +218,16 @@ def degree_stats(g) -> tuple[int, int, int]:
                                     _p(a[0:], _u64p), _p(a[1:], _u64p), _p(a[2:], _u64p)),
            "degree_stats")
     return int(a[0]), int(a[1]), int(a[2])
+
+
+def vp_chunked(g, chunk: int) -> int:
+    """Algorithm 2 with each start's end set split into priority ranges of
+    `chunk`, each counted separately (tiny graphs)."""
+    off, adj = _csr(g)
+    a = np.zeros(1, dtype=np.uint64)
+    _check(_load().orc_vp_chunked(g.num_u, g.num_l, _p(off, _i32p), _p(adj, _i32p), int(chunk),
+                                  _p(a, _u64p)), "vp_chunked")
+    return int(a[0])
 
 
 def pairs_total(g) -> tuple[int, int]:

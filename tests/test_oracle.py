@@ -111,6 +111,50 @@ def test_circulant_closed_form(p, c, n):
 
 
 # ---------------------------------------------------------------------------
+# Splitting one start over several workers: only the end set may be split
+# ---------------------------------------------------------------------------
+
+def _middle_split_total(g):
+    """Algorithm 2 with each start's MIDDLES cut in two halves counted apart:
+    a pair whose middles fall in both halves gets C(a, 2) + C(b, 2) instead
+    of C(a + b, 2), so this undercounts (C is superadditive)."""
+    pr = oracle.projection(g)
+    off, adj, cut = pr["off"], pr["adj"], pr["cut"]
+    t = 0
+    for x in range(g.num_u + g.num_l):
+        mids = adj[off[x]:off[x] + cut[x]]
+        for half in (mids[:len(mids) // 2], mids[len(mids) // 2:]):
+            cnt = {}
+            for v in half:
+                for w in adj[off[v]:off[v + 1]]:
+                    if w < x:   # same layer as x: a lower G* id is a lower priority
+                        cnt[w] = cnt.get(w, 0) + 1
+            t += sum(c2(c) for c in cnt.values())
+    return t
+
+
+@pytest.mark.parametrize("gi", range(5))
+def test_end_range_split_is_exact(gi):
+    g = [G.complete_bipartite(3, 3), G.complete_bipartite(5, 7), G.chung_lu_bipartite(80, 60, 700, 2.1, 2.1, 9),
+         G.uniform_bipartite(60, 40, 500, 3), G.random_tiny(9, 8, 3, 6, 17)][gi]
+    ref = oracle.vp(g)["total"]
+    n = g.num_u + g.num_l
+    for chunk in (1, 2, 3, 7, n):
+        assert oracle.vp_chunked(g, chunk) == ref
+    # the other split (of the middles) is not exact wherever a pair has
+    # middles in both halves, e.g. every pair of K_{3,3} and K_{5,7}
+    wrong = _middle_split_total(g)
+    assert wrong <= ref
+    if gi < 2:
+        assert wrong < ref
+
+
+def test_chunked_rejects_bad_width():
+    with pytest.raises(ValueError):
+        oracle.vp_chunked(G.complete_bipartite(2, 2), 0)
+
+
+# ---------------------------------------------------------------------------
 # Section 6.3's pair formulation: a second exact path by sorting wedge pairs
 # ---------------------------------------------------------------------------
 
