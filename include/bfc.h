@@ -144,6 +144,8 @@ typedef enum bfc_array {
                          count's first launch and went to the retry pass */
 } bfc_array;
 
+/* Fills *opt with the defaults listed above (NULL is ignored).  Library
+ * plumbing with no counterpart in the paper. */
 void bfc_options_init(bfc_options *opt);
 
 /* Steps a1-a5 of the hot path: degrees, priority ranks (Definition 3),
@@ -197,13 +199,18 @@ typedef struct bfc_batch {
 int bfc_prepare_batch(const bfc_csr *union_csr, const bfc_batch *batch, const bfc_options *opt,
                       void *stream, bfc_graph **out);
 
-/* Steps a6-a7 for a batch in ONE persistent launch: totals_dev[g] = ⋈ of
- * graph g (uint64[num_graphs], device); total_dev (nullable) = their sum.
+/* Steps a6-a7 for a batch in ONE persistent launch (Algorithm 2 for every
+ * start of every graph, scheduled together as Section 6.2's dynamic
+ * scheduling): totals_dev[g] = ⋈ of graph g (uint64[num_graphs], device);
+ * total_dev (nullable) = their sum.  BFC_ERR_INVALID_ARGUMENT if g was not
+ * prepared by bfc_prepare_batch.
  * Asynchronous, no allocation, no host synchronisation: it can be captured
  * in a CUDA graph once a first call has been made outside capture. */
 int bfc_count_batch(bfc_graph *g, void *stream, uint64_t *totals_dev, uint64_t *total_dev);
 
-/* Processed wedges of every graph of a batch (uint64[num_graphs], device). */
+/* Processed wedges W of every graph of a batch (the wedges Algorithm 2
+ * visits, equal to Algorithm 3's by Lemma 4): uint64[num_graphs], device,
+ * caller-owned.  Asynchronous. */
 int bfc_batch_wedges(const bfc_graph *g, void *stream, uint64_t *wedges_dev);
 
 /* Autotuner for the bin thresholds of step a5: re-bins the prepared graph for
@@ -245,9 +252,12 @@ typedef struct bfc_server_stats {
     int64_t waiting;             /* requests not yet admitted */
 } bfc_server_stats;
 
+/* Fills *cfg with the defaults listed above (NULL is ignored). */
 void bfc_server_config_init(bfc_server_config *cfg);
 
-/* Starts the workers on the current device. */
+/* Starts the workers on the current device.  *out is owned by the caller
+ * until bfc_server_destroy.  BFC_ERR_INVALID_ARGUMENT for a configuration
+ * outside the ranges above. */
 int bfc_server_create(const bfc_server_config *cfg, bfc_server **out);
 
 /* Queues one request.  off_u_host[num_u + 1] / adj_u_host[num_edges] must stay
@@ -262,6 +272,7 @@ int bfc_server_submit(bfc_server *sv, int32_t num_u, int32_t num_l, int64_t num_
 int bfc_server_poll(bfc_server *sv, uint64_t request_id, int wait, uint64_t *total, int *status,
                     double *latency_s);
 
+/* A snapshot of the counters above (thread-safe). */
 int bfc_server_get_stats(bfc_server *sv, bfc_server_stats *out);
 
 /* Stops the workers after the batches in flight; requests never admitted
@@ -269,18 +280,24 @@ int bfc_server_get_stats(bfc_server *sv, bfc_server_stats *out);
 void bfc_server_destroy(bfc_server *sv);
 
 /* Waits for `stream` and reports any error a kernel of this graph flagged
- * since the last bfc_sync (BFC_ERR_INTERNAL), then clears the flag. */
+ * since the last bfc_sync (BFC_ERR_INTERNAL), then clears the flag; a CUDA
+ * failure returns BFC_ERR_CUDA.  Library plumbing (no paper counterpart). */
 int bfc_sync(bfc_graph *g, void *stream);
 
-/* Host figures of a prepared graph. */
+/* Host figures of a prepared graph (sizes, W of Section 4, bin sizes; see
+ * bfc_info).  Does not touch the GPU. */
 int bfc_graph_info(const bfc_graph *g, bfc_info *out);
 
-/* Copies one internal array (see bfc_array) to caller-owned device memory
- * dst_dev (size as listed), asynchronously on `stream`. */
+/* Copies one internal array (see bfc_array: Definition 3's ranks,
+ * Definition 4's G*, Section 4's cut, Eq. 5's per-start work) to
+ * caller-owned device memory dst_dev (size as listed), asynchronously on
+ * `stream`.  BFC_ERR_INVALID_ARGUMENT for an unknown `which`. */
 int bfc_export(const bfc_graph *g, int which, void *dst_dev, void *stream);
 
-/* End to end from HOST memory: copies the CSR to the device, prepares,
- * counts, copies ⋈_G back to *total_host and frees everything it took.
+/* Steps a1-a7 (Algorithm 2, or 3 with opt->orientation = 1) end to end from
+ * HOST memory: copies the CSR to the device, prepares, counts, copies ⋈_G
+ * back to *total_host (and W to *wedges_host, nullable) and frees everything
+ * it took.  Errors as bfc_prepare and bfc_count.
  * Synchronous.  off_u_host/adj_u_host may be pinned or pageable. */
 int bfc_count_host(int32_t num_u, int32_t num_l, int64_t num_edges, const int32_t *off_u_host,
                    const int32_t *adj_u_host, const bfc_options *opt, void *stream,
@@ -318,7 +335,7 @@ int bfc_count_small_noalloc(int32_t num_u, int32_t num_l, int64_t num_edges,
                             uint64_t *total_dev, int32_t *status_dev);
 
 /* Frees the graph's library memory (stream-ordered on the stream of its
- * last call).  NULL is ignored. */
+ * last call).  NULL is ignored.  Library plumbing (no paper counterpart). */
 void bfc_release(bfc_graph *g);
 
 /* Static text for a status code. */
