@@ -719,3 +719,56 @@ int orc_vp_chunked(int32_t r, int32_t l, const int32_t *off, const int32_t *adj,
     free(p); free(count_wedge); graph_free(&g);
     return 0;
 }
+
+int orc_vp_core_split(int32_t r, int32_t l, const int32_t *off, const int32_t *adj, int32_t K,
+                      uint64_t *total, uint64_t *core_wedges, uint64_t *core_c2, uint64_t *core_cross) {
+    if (K < 0) return -1;
+    graph_t g;
+    int rc = graph_build(r, l, off, adj, &g);
+    if (rc) return rc;
+    const int32_t n = g.n;
+    int32_t *p = malloc(sizeof(int32_t) * ((size_t)n + 1));
+    uint32_t *b = calloc((size_t)n + 1, sizeof(uint32_t));   /* count_wedge of the walk */
+    uint32_t *a = calloc((size_t)n + 1, sizeof(uint32_t));   /* core middles per core end */
+    if (!p || !a || !b) { free(p); free(a); free(b); graph_free(&g); return -2; }
+    rc = compute_priority(&g, p);
+    if (rc) { free(p); free(a); free(b); graph_free(&g); return rc; }
+    uint64_t t = 0, skipped = 0, c2a = 0, cross = 0;
+    for (int32_t u = 0; u < n; ++u) {
+        const int cu = p[u] > n - K;
+        for (int64_t i = g.off[u]; i < g.off[u + 1]; ++i) {
+            const int32_t v = g.adj[i];
+            if (!(p[v] < p[u])) continue;
+            const int cv = p[v] > n - K;
+            for (int64_t j = g.off[v]; j < g.off[v + 1]; ++j) {
+                const int32_t w = g.adj[j];
+                if (!(p[w] < p[u])) continue;
+                if (cu && cv && p[w] > n - K) {
+                    /* start, middle and end in the core: left to the core part */
+                    ++skipped;
+                    a[w] += 1;
+                    continue;
+                }
+                t += b[w];       /* running form: Σ old = Σ C(b, 2) */
+                b[w] += 1;
+            }
+        }
+        /* the pairs (u, w) with both in the core: a·b + C(a, 2) */
+        for (int32_t w = 0; w < n; ++w) {
+            if (a[w]) {
+                const uint64_t aw = a[w];
+                t += aw * (uint64_t)b[w] + aw * (aw - 1) / 2;
+                c2a += aw * (aw - 1) / 2;
+                cross += aw * (uint64_t)b[w];
+            }
+            a[w] = 0;
+            b[w] = 0;
+        }
+    }
+    *total = t;
+    *core_wedges = skipped;
+    *core_c2 = c2a;
+    *core_cross = cross;
+    free(p); free(a); free(b); graph_free(&g);
+    return 0;
+}

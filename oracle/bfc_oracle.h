@@ -113,6 +113,20 @@ int orc_degree_stats(int32_t r, int32_t l, const int32_t *off, const int32_t *ad
 int orc_vp_chunked(int32_t r, int32_t l, const int32_t *off, const int32_t *adj, int32_t chunk,
                    uint64_t *total);
 
+/* Algorithm 2 with the top-K priority vertices (the "core", both layers)
+ * split off, as a dense-core hybrid would count them.  For a start u and an
+ * end w that are both in the core, c_uw = a_uw + b_uw with a_uw the middles
+ * in the core and b_uw the others, and
+ *     C(a + b, 2) = C(b, 2) + a·b + C(a, 2)          (Lemma 1 per pair).
+ * The walk skips every wedge whose start, middle and end all lie in the core
+ * (C(b, 2) and the other pairs by the running form); a_uw is counted apart
+ * by its definition and the pair adds a·b + C(a, 2).  *total = ⋈_G for every
+ * K; *core_wedges = the wedges skipped; *core_c2 = Σ C(a_uw, 2) (the part a
+ * dense product over the core would give); *core_cross = Σ a_uw·b_uw.
+ * Plain loops: small graphs. */
+int orc_vp_core_split(int32_t r, int32_t l, const int32_t *off, const int32_t *adj, int32_t K,
+                      uint64_t *total, uint64_t *core_wedges, uint64_t *core_c2, uint64_t *core_cross);
+
 /* Section 6.3's pair formulation (BFC-EM), in memory: for every middle v,
  * each wedge (u, v, w) with p(w) > p(v) and p(w) > p(u) is written as the
  * pair (w, u); the pairs are sorted and every run of c equal pairs gives

@@ -66,6 +66,8 @@ def _load():
                 "orc_caterpillars": [c.c_int32, c.c_int32, _i32p, _i32p, _u64p],
                 "orc_pairs_total": [c.c_int32, c.c_int32, _i32p, _i32p, _u64p, _u64p],
                 "orc_vp_chunked": [c.c_int32, c.c_int32, _i32p, _i32p, c.c_int32, _u64p],
+                "orc_vp_core_split": [c.c_int32, c.c_int32, _i32p, _i32p, c.c_int32, _u64p, _u64p, _u64p,
+                                      _u64p],
             }
             for name, args in sig.items():
                 f = getattr(lib, name)
@@ -228,6 +230,18 @@ def vp_chunked(g, chunk: int) -> int:
     _check(_load().orc_vp_chunked(g.num_u, g.num_l, _p(off, _i32p), _p(adj, _i32p), int(chunk),
                                   _p(a, _u64p)), "vp_chunked")
     return int(a[0])
+
+
+def vp_core_split(g, K: int) -> tuple[int, int, int, int]:
+    """Algorithm 2 with the top-K priority core counted apart (tiny graphs):
+    (total, wedges skipped by the walk, Σ C(a_uw, 2) and Σ a_uw·b_uw over
+    core pairs)."""
+    off, adj = _csr(g)
+    a = np.zeros(4, dtype=np.uint64)
+    _check(_load().orc_vp_core_split(g.num_u, g.num_l, _p(off, _i32p), _p(adj, _i32p), int(K),
+                                     _p(a[0:], _u64p), _p(a[1:], _u64p), _p(a[2:], _u64p),
+                                     _p(a[3:], _u64p)), "vp_core_split")
+    return int(a[0]), int(a[1]), int(a[2]), int(a[3])
 
 
 def pairs_total(g) -> tuple[int, int]:

@@ -155,6 +155,71 @@ def test_chunked_rejects_bad_width():
 
 
 # ---------------------------------------------------------------------------
+# A dense core counted apart: the top-K priority vertices
+# ---------------------------------------------------------------------------
+
+def _masked_core_gram(g, K):
+    """The core part as a product of 0/1 matrices: for each layer X, the core
+    vertices of X and of the other layer Y sorted by priority, A[i, j] = 1 for
+    an edge (x_i, y_j), row i masked to the middles below x_i, and
+    a[i, i'] = (masked A[i]) · A[i'] for the ends i' < i.  Returns (Σ a, Σ C(a, 2))."""
+    _, _, p = oracle.priority(g)
+    l, n = g.num_l, g.num_u + g.num_l
+    core = p > n - K
+    u = np.repeat(np.arange(g.num_u), np.diff(g.off_u.astype(np.int64))) + l
+    v = g.adj_u.astype(np.int64)
+    s1 = s2 = 0
+    for xs_layer, ys_layer in ((np.arange(l, n), np.arange(0, l)), (np.arange(0, l), np.arange(l, n))):
+        xs = xs_layer[core[xs_layer]]
+        ys = ys_layer[core[ys_layer]]
+        if xs.size == 0 or ys.size == 0:
+            continue
+        xs = xs[np.argsort(p[xs])]
+        ys = ys[np.argsort(p[ys])]
+        xi = np.full(n, -1); xi[xs] = np.arange(xs.size)
+        yi = np.full(n, -1); yi[ys] = np.arange(ys.size)
+        A = np.zeros((xs.size, ys.size), dtype=np.int64)
+        for a_end, b_end in ((u, v), (v, u)):
+            m = (xi[a_end] >= 0) & (yi[b_end] >= 0)
+            A[xi[a_end[m]], yi[b_end[m]]] = 1
+        t = np.searchsorted(p[ys], p[xs])          # middles of x_i: y_j with j < t[i]
+        Am = A * (np.arange(ys.size)[None, :] < t[:, None])
+        a = np.tril(Am @ A.T, k=-1)                 # ends below the start
+        s1 += int(a.sum())
+        s2 += int((a * (a - 1) // 2).sum())
+    return s1, s2
+
+
+@pytest.mark.parametrize("gi", range(5))
+def test_core_split_is_exact(gi):
+    g = [G.complete_bipartite(4, 6), G.complete_bipartite(7, 5), G.chung_lu_bipartite(120, 80, 1200, 2.1, 2.1, 4),
+         G.uniform_bipartite(60, 40, 500, 3), G.random_tiny(9, 8, 3, 6, 17)][gi]
+    ref = oracle.vp(g)
+    n = g.num_u + g.num_l
+    for K in sorted({0, 1, 2, 7, n // 4, n // 2, n - 1, n}):
+        tot, skipped, c2a, _ = oracle.vp_core_split(g, K)
+        assert tot == ref["total"], K
+        # the skipped wedges and the core's own pairs, from the matrix product
+        assert (skipped, c2a) == _masked_core_gram(g, K), K
+    assert oracle.vp_core_split(g, 0)[1:] == (0, 0, 0)
+    tot, skipped, c2a, cross = oracle.vp_core_split(g, n)
+    # the whole graph is the core: no middle outside it, the product gives all
+    assert skipped == ref["wedges"] and c2a == ref["total"] and cross == 0
+
+
+def test_core_split_cross_term_matters():
+    # with a core strictly inside the graph some core pair has middles on both
+    # sides, so a·b is needed: C(a, 2) + C(b, 2) alone falls short
+    g = G.chung_lu_bipartite(120, 80, 1200, 2.1, 2.1, 4)
+    n = g.num_u + g.num_l
+    ref = oracle.vp(g)["total"]
+    for K in (n // 8, n // 4, n // 2):
+        tot, skipped, c2a, cross = oracle.vp_core_split(g, K)
+        assert tot == ref and skipped > 0 and cross > 0
+        assert tot - cross < ref
+
+
+# ---------------------------------------------------------------------------
 # Section 6.3's pair formulation: a second exact path by sorting wedge pairs
 # ---------------------------------------------------------------------------
 
