@@ -268,15 +268,21 @@ int bfc_server_submit(bfc_server *sv, int32_t num_u, int32_t num_l, int64_t num_
 
 /* *status = -1 while pending, else the request's bfc_status; when complete,
  * *total = ⋈ of its graph, *latency_s = seconds from submit to completion,
- * and the request id is retired.  wait != 0 blocks until completion. */
+ * and the request id is retired (a later poll of it returns
+ * BFC_ERR_INVALID_ARGUMENT).  wait != 0 blocks until completion.  Different
+ * requests may be polled from different threads at once; one request must
+ * not be polled by two threads at the same time. */
 int bfc_server_poll(bfc_server *sv, uint64_t request_id, int wait, uint64_t *total, int *status,
                     double *latency_s);
 
 /* A snapshot of the counters above (thread-safe). */
 int bfc_server_get_stats(bfc_server *sv, bfc_server_stats *out);
 
-/* Stops the workers after the batches in flight; requests never admitted
- * complete with BFC_ERR_INTERNAL.  No thread may be inside bfc_server_poll. */
+/* Stops the server: the workers first count every request still waiting
+ * (each fits the budget on its own, so the queue drains), then exit; a
+ * request that could still not be admitted completes with
+ * BFC_ERR_INTERNAL.  Frees every request, polled or not.  No thread may be
+ * inside bfc_server_poll or bfc_server_submit. */
 void bfc_server_destroy(bfc_server *sv);
 
 /* Waits for `stream` and reports any error a kernel of this graph flagged
