@@ -120,3 +120,96 @@ def test_unmutated_copy_passes(tmp_path):
 def test_mutant_is_caught(name, tmp_path):
     lib = _build_mutant(name, tmp_path)
     assert not _pins_pass(lib), f"planted mistake {name} went unnoticed"
+
+
+# ---------------------------------------------------------------------------
+# The second exact paths: split end ranges, the core split, the pair formulation
+# ---------------------------------------------------------------------------
+
+EXTRA_MUTANTS = {
+    "core_cross_dropped": [("t += aw * (uint64_t)b[w] + aw * (aw - 1) / 2;", "t += aw * (aw - 1) / 2;")],
+    # skips core-start, core-middle wedges whatever their end: the total
+    # survives (any split of the middles adds up), the skipped count does not
+    "core_skip_ignores_end": [("if (cu && cv && p[w] > n - K) {", "if (cu && cv) {")],
+    "core_running_form_after_increment": [("t += b[w];       /* running form", "t += b[w] + 1;   /* running form")],
+    "chunk_boundary_inclusive": [("p[w] >= lo && p[w] < hi)", "p[w] >= lo && p[w] <= hi)")],
+    "pairs_include_self": [("if (p[g.adj[j]] < p[w]) ++np;", "if (p[g.adj[j]] <= p[w]) ++np;"),
+                           ("if (p[u] < p[w]) key[k++]", "if (p[u] <= p[w]) key[k++]")],
+    "pairs_run_off_by_one": [("t += run - 1;", "t += run;")],
+}
+
+
+def _build_extra(name, tmp_path):
+    src = open(SRC).read()
+    for old, new in EXTRA_MUTANTS[name]:
+        assert src.count(old) == 1, f"mutation site for {name} not found once"
+        src = src.replace(old, new)
+    d = tmp_path / name
+    d.mkdir()
+    (d / "m.c").write_text(src)
+    subprocess.run(["gcc", "-O1", "-std=c11", "-fopenmp", "-fPIC", "-shared", "-I",
+                    os.path.dirname(SRC), "-o", str(d / "m.so"), str(d / "m.c")], check=True)
+    return ctypes.CDLL(str(d / "m.so"))
+
+
+def _csr_args(g):
+    i32 = ctypes.POINTER(ctypes.c_int32)
+    off = np.ascontiguousarray(g.off_u, dtype=np.int32)
+    adj = np.ascontiguousarray(g.adj_u if g.num_edges else np.zeros(1, np.int32), dtype=np.int32)
+    return (off, adj), (ctypes.c_int32(g.num_u), ctypes.c_int32(g.num_l), off.ctypes.data_as(i32),
+                        adj.ctypes.data_as(i32))
+
+
+def _core_wedges(g, K):
+    """Wedges of Algorithm 2 with start, middle and end among the top-K by
+    priority, counted from the edge list (priorities from the real oracle)."""
+    _, _, p = oracle.priority(g)
+    l, n = g.num_l, g.num_u + g.num_l
+    core = p > n - K
+    u = np.repeat(np.arange(g.num_u), np.diff(g.off_u.astype(np.int64))) + l
+    v = g.adj_u.astype(np.int64)
+    keep = core[u] & core[v]
+    mid = np.concatenate([u[keep], v[keep]]); nb = np.concatenate([v[keep], u[keep]])
+    o = np.lexsort((p[nb], mid)); mid, nb = mid[o], nb[o]
+    idx = np.arange(mid.size) - np.searchsorted(mid, mid, side="left")
+    return int(idx[p[nb] > p[mid]].sum())
+
+
+def _extra_pins_pass(lib) -> bool:
+    u64 = ctypes.POINTER(ctypes.c_uint64)
+    graphs = [G.complete_bipartite(4, 6), G.complete_bipartite(5, 7),
+              G.chung_lu_bipartite(120, 80, 1200, 2.1, 2.1, 4), G.uniform_bipartite(60, 40, 500, 3),
+              G.random_tiny(9, 8, 3, 6, 17)]
+    for g in graphs:
+        ref = oracle.vp(g)
+        n = g.num_u + g.num_l
+        keep, args = _csr_args(g)
+        for K in (n // 4, n // 2, n):
+            out = np.zeros(4, np.uint64)
+            rc = lib.orc_vp_core_split(*args, ctypes.c_int32(K), *(out[i:].ctypes.data_as(u64) for i in range(4)))
+            if rc != 0 or int(out[0]) != ref["total"] or int(out[1]) != _core_wedges(g, K):
+                return False
+        for chunk in (2, 3):
+            out = np.zeros(1, np.uint64)
+            rc = lib.orc_vp_chunked(*args, ctypes.c_int32(chunk), out.ctypes.data_as(u64))
+            if rc != 0 or int(out[0]) != ref["total"]:
+                return False
+        out = np.zeros(2, np.uint64)
+        rc = lib.orc_pairs_total(*args, out[0:].ctypes.data_as(u64), out[1:].ctypes.data_as(u64))
+        if rc != 0 or (int(out[0]), int(out[1])) != (ref["total"], ref["wedges"]):
+            return False
+    return True
+
+
+def test_unmutated_copy_passes_extra_pins(tmp_path):
+    d = tmp_path / "orig"
+    d.mkdir()
+    (d / "m.c").write_text(open(SRC).read())
+    subprocess.run(["gcc", "-O1", "-std=c11", "-fopenmp", "-fPIC", "-shared", "-I",
+                    os.path.dirname(SRC), "-o", str(d / "m.so"), str(d / "m.c")], check=True)
+    assert _extra_pins_pass(ctypes.CDLL(str(d / "m.so")))
+
+
+@pytest.mark.parametrize("name", sorted(EXTRA_MUTANTS))
+def test_extra_mutant_is_caught(name, tmp_path):
+    assert not _extra_pins_pass(_build_extra(name, tmp_path)), f"planted mistake {name} went unnoticed"
