@@ -158,17 +158,17 @@ def test_chunked_rejects_bad_width():
 # A dense core counted apart: the top-K priority vertices
 # ---------------------------------------------------------------------------
 
-def _masked_core_gram(g, K):
-    """The core part as a product of 0/1 matrices: for each layer X, the core
-    vertices of X and of the other layer Y sorted by priority, A[i, j] = 1 for
-    an edge (x_i, y_j), row i masked to the middles below x_i, and
-    a[i, i'] = (masked A[i]) · A[i'] for the ends i' < i.  Returns (Σ a, Σ C(a, 2))."""
+def _core_blocks(g, K):
+    """Per start layer X: the core's 0/1 adjacency A[i, j] (core vertices of X
+    and of the other layer Y, each sorted by priority) and t[i] = the number
+    of Y's core vertices below x_i, i.e. x_i's middles are y_j with j < t[i]
+    (t is non-decreasing in i)."""
     _, _, p = oracle.priority(g)
     l, n = g.num_l, g.num_u + g.num_l
     core = p > n - K
     u = np.repeat(np.arange(g.num_u), np.diff(g.off_u.astype(np.int64))) + l
     v = g.adj_u.astype(np.int64)
-    s1 = s2 = 0
+    out = []
     for xs_layer, ys_layer in ((np.arange(l, n), np.arange(0, l)), (np.arange(0, l), np.arange(l, n))):
         xs = xs_layer[core[xs_layer]]
         ys = ys_layer[core[ys_layer]]
@@ -182,12 +182,63 @@ def _masked_core_gram(g, K):
         for a_end, b_end in ((u, v), (v, u)):
             m = (xi[a_end] >= 0) & (yi[b_end] >= 0)
             A[xi[a_end[m]], yi[b_end[m]]] = 1
-        t = np.searchsorted(p[ys], p[xs])          # middles of x_i: y_j with j < t[i]
-        Am = A * (np.arange(ys.size)[None, :] < t[:, None])
+        out.append((A, np.searchsorted(p[ys], p[xs])))
+    return out
+
+
+def _masked_core_gram(g, K):
+    """The core part as a product of 0/1 matrices: row i of A masked to the
+    middles below x_i, a[i, i'] = (masked A[i]) · A[i'] for the ends i' < i.
+    Returns (Σ a, Σ C(a, 2))."""
+    s1 = s2 = 0
+    for A, t in _core_blocks(g, K):
+        Am = A * (np.arange(A.shape[1])[None, :] < t[:, None])
         a = np.tril(Am @ A.T, k=-1)                 # ends below the start
         s1 += int(a.sum())
         s2 += int((a * (a - 1) // 2).sum())
     return s1, s2
+
+
+def _tiled_core_pairs(A, t, tm, tj):
+    """The same product as a tensor-core kernel would tile it: output tiles
+    (I, I') with I' <= I only, accumulated over contraction blocks J below
+    t[last row of I]; the per-row mask is applied only in the blocks that
+    straddle t[first row of I] .. t[last row of I].  Returns (a, MACs)."""
+    X, Y = A.shape
+    acc = np.zeros((X, X), dtype=np.int64)
+    macs = 0
+    for i0 in range(0, X, tm):
+        i1 = min(i0 + tm, X)
+        tmin, tmax = int(t[i0]), int(t[i1 - 1])
+        for j0 in range(0, tmax, tj):
+            j1 = min(j0 + tj, Y)
+            rows = A[i0:i1, j0:j1]
+            if j1 > tmin:   # some row of the tile stops inside this block
+                rows = rows * (np.arange(j0, j1)[None, :] < t[i0:i1, None])
+            for k0 in range(0, i1, tm):
+                k1 = min(k0 + tm, X)
+                acc[i0:i1, k0:k1] += rows @ A[k0:k1, j0:j1].T
+                macs += (i1 - i0) * (k1 - k0) * (j1 - j0)
+    return np.tril(acc, k=-1), macs
+
+
+def test_tiled_core_product_matches_the_core_split():
+    g = G.chung_lu_bipartite(300, 200, 4000, 2.1, 2.1, 8)
+    n = g.num_u + g.num_l
+    for K in (n // 8, n // 3, n):
+        tot, skipped, c2a, _ = oracle.vp_core_split(g, K)
+        for tm, tj in ((4, 3), (8, 8), (16, 5)):
+            s1 = s2 = 0
+            macs = dense = 0
+            for A, t in _core_blocks(g, K):
+                assert np.all(np.diff(t) >= 0)
+                a, m = _tiled_core_pairs(A, t, tm, tj)
+                s1 += int(a.sum())
+                s2 += int((a * (a - 1) // 2).sum())
+                macs += m
+                dense += A.shape[0] ** 2 * A.shape[1]
+            assert (s1, s2) == (skipped, c2a), (K, tm, tj)
+            assert macs <= dense
 
 
 @pytest.mark.parametrize("gi", range(5))
