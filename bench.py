@@ -31,6 +31,8 @@ if ROOT not in sys.path:
 METRIC = "wedges/s & %HBM roofline (1 graph); graphs/s and p99 latency batched vs per-graph"
 UNIT = "wedges/s"
 L2_FLUSH_BYTES = 512 << 20
+# the largest single-GPU workload, specified with per-vertex and per-edge counts
+HEADLINE = "shopping_300m"
 WORKLOADS = {
     "powerlaw_20m": "chunglu_u1m_l500k_m20m_g2.1 (|U|=1M, |L|=500k, 20M edges, exponent 2.1 both layers, seed 2001+rank)",
     "shopping_300m": "shopping_u10m_l100k_m300m (users exponent 2.5, items exponent 1.8, top item ~1M, seed 3001+rank)",
@@ -305,12 +307,15 @@ def run_serve(args, rank, world):
 def algorithmic_bytes(W: int, m: int, n: int, outputs: str = "total") -> int:
     """Bytes the count must move at least once: 4 B per processed wedge (the
     end id), 12 B per oriented edge (middle id + the middle's offset), 12 B
-    per start (offset + cut).  With per-vertex and per-edge outputs the
-    second walk reads every end again with its edge id (8 B per wedge) and
-    the outputs are written once (8 B per vertex and per edge)."""
+    per start (offset + cut).  With per-vertex and per-edge outputs, the
+    second walk reads the same again (ends, middles, starts); the per-edge
+    sums live in one uint64 per G* slot (2m of them), written once when
+    cleared and read once when the two slots of each edge are combined,
+    which also reads both slots' edge ids (4 B each); the outputs are
+    written once (8 B per edge and per vertex)."""
     B = 4 * W + 12 * m + 12 * n
     if outputs == "all":
-        B += 8 * W + 8 * m + 8 * n
+        B += (4 * W + 12 * m + 12 * n) + 2 * 16 * m + 8 * m + 8 * m + 8 * n
     return B
 
 
@@ -507,6 +512,7 @@ def run_reference(args, rank, world):
     host cores, on the same workload (a bounded sample of it)."""
     if rank != 0:
         return 0
+    args.workload = args.workload or HEADLINE
     g = make_graph(args.workload, 0, "cpu")
     outputs = args.outputs or default_outputs(args.workload)
     threads = os.cpu_count() or 1
@@ -535,13 +541,19 @@ def main():
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="powerlaw_20m", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default=None, choices=sorted(WORKLOADS),
+                    help=f"default: {HEADLINE} (total + per-vertex + per-edge) with the 20M-edge "
+                         "power-law total count under its own key")
+    ap.add_argument("--no-history", action="store_true",
+                    help="default workload only, without the 20M-edge power-law line")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--orientation", type=int, default=0, choices=[0, 1],
                     help="0 = Algorithm 2 (start highest), 1 = Algorithm 3 (end highest)")
     ap.add_argument("--outputs", default=None, choices=["total", "all"],
                     help="total only, or total + per-vertex + per-edge (default: all for shopping_300m)")
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--core-vertices", type=int, default=0,
+                    help="total counts: the top-K priority core counted by the tensor-core product")
     ap.add_argument("--batch-graphs", type=int, default=4096)
     ap.add_argument("--serve-pool", type=int, default=256)
     ap.add_argument("--serve-requests", type=int, default=10000)
@@ -559,13 +571,37 @@ def main():
 
     import torch
 
-    from paper_1812_00283_gb300 import bfc
-
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     dist_init(world, dev)
+    workload = args.workload or HEADLINE
+    outputs = args.outputs or default_outputs(workload)
+    out = run_single(args, workload, outputs, rank, world, local, dev)
+    if args.workload is None and not args.no_history:
+        # the 20M-edge power-law graph, total count only: the count kernel's
+        # history is quoted on this workload
+        h = run_single(args, "powerlaw_20m", "total", rank, world, local, dev, one_thread=False)
+        out["powerlaw_20m"] = {k: h[k] for k in ("value", "unit", "ms_per_step", "roofline", "e2e",
+                                                 "cpu_baseline", "gpu_launches", "clocks")}
+        out["powerlaw_20m"]["config"] = {k: h["config"][k] for k in (
+            "workload", "wedges_per_step", "butterflies", "prepare_ms_median", "count_ms_median",
+            "count_only_wedges_per_s", "outputs", "oracle_agrees")}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    dist_done(world)
+    return 0
 
-    g = make_graph(args.workload, rank, dev)
+
+def run_single(args, workload: str, outputs: str, rank: int, world: int, local: int, dev,
+               one_thread: bool = True) -> dict:
+    """One graph, prepared and counted per step (the single-graph hot path):
+    the bench line of that workload, with its roofline, CPU baseline and
+    end-to-end figures."""
+    import torch
+
+    from paper_1812_00283_gb300 import bfc
+
+    g = make_graph(workload, rank, dev)
     off = torch.from_numpy(g.off_u).to(dev)
     adj = torch.from_numpy(g.adj_u).to(dev)
     r, l, m = g.num_u, g.num_l, g.num_edges
@@ -575,8 +611,8 @@ def main():
     total = torch.zeros(1, dtype=torch.int64, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
-    step_opts = bfc.bfc_options_init(orientation=args.orientation)
-    outputs = args.outputs or default_outputs(args.workload)
+    step_opts = bfc.bfc_options_init(orientation=args.orientation,
+                                     core_vertices=args.core_vertices if outputs == "total" else 0)
     if outputs == "all":
         per_u = torch.empty(max(r, 1), dtype=torch.int64, device=dev)
         per_l = torch.empty(max(l, 1), dtype=torch.int64, device=dev)
@@ -636,7 +672,7 @@ def main():
     cnt_s = statistics.median(count_ms) / 1e3
     B = algorithmic_bytes(W, m, n, outputs)
     achieved = B / cnt_s / 1e9
-    traffic = recorded_traffic(args.workload, outputs, args.orientation)
+    traffic = recorded_traffic(workload, outputs, args.orientation)
     roofline = dict(bound="hbm", achieved=achieved, peak=peaks["hbm_gbs"], unit="GB/s",
                     frac=achieved / peaks["hbm_gbs"], traffic=traffic,
                     kernel="k_count (bfc_count_all)" if outputs == "all" else "k_count (bfc_count)",
@@ -647,15 +683,18 @@ def main():
     # coefficient 4·⋈ / caterpillars, on a prepared graph (outside the steps)
     hd = bfc.bfc_prepare(r, l, m, off.data_ptr(), adj.data_ptr(), step_opts, sp)
     cat_t = torch.zeros(1, dtype=torch.int64, device=dev)
+    coef_t = torch.zeros(1, dtype=torch.float64, device=dev)
     bfc.bfc_caterpillars(hd, sp, cat_t.data_ptr())     # warm-up
     ce0, ce1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ce0.record(stream)
     bfc.bfc_caterpillars(hd, sp, cat_t.data_ptr())
     ce1.record(stream)
+    # total (from the timed steps, still on the device) -> coefficient, in the library
+    bfc.bfc_clustering_coefficient(hd, sp, total.data_ptr(), cat_t.data_ptr(), coef_t.data_ptr())
     bfc.bfc_sync(hd, sp)
     bfc.bfc_release(hd)
     cat = int(cat_t.item()) & ((1 << 64) - 1)
-    derived = dict(caterpillars=cat, clustering_coefficient=(4.0 * expect / cat) if cat else 0.0,
+    derived = dict(caterpillars=cat, clustering_coefficient=float(coef_t.item()),
                    caterpillars_ms=ce0.elapsed_time(ce1))
 
     # the second ceiling: one shared-memory counter increment per wedge
@@ -726,37 +765,41 @@ def main():
         if frac == 1.0:
             verified = (ref["total"] == expect and ref["wedges"] == W)
         cpu = dict(value=ref["wedges"] / dt, unit=UNIT, cores=threads, kind="oracle",
-                   sample=sample_desc(args.workload, frac, sample, ref, outputs) + f", one run, {dt:.1f} s")
-        # the same oracle on one core, on a smaller sample (~10 s)
-        s1, f1, r1, dt1 = oracle_sample(g, outputs, 1, 10.0)
-        cpu["one_thread"] = dict(value=r1["wedges"] / dt1, unit=UNIT, cores=1,
-                                 sample=sample_desc(args.workload, f1, s1, r1, outputs) + f", one run, {dt1:.1f} s")
+                   sample=sample_desc(workload, frac, sample, ref, outputs) + f", one run, {dt:.1f} s")
+        if one_thread:
+            # the same oracle on one core, on a smaller sample (~10 s)
+            s1, f1, r1, dt1 = oracle_sample(g, outputs, 1, 10.0)
+            cpu["one_thread"] = dict(value=r1["wedges"] / dt1, unit=UNIT, cores=1,
+                                     sample=sample_desc(workload, f1, s1, r1, outputs) +
+                                     f", one run, {dt1:.1f} s")
 
-    if rank == 0:
-        out = dict(
-            metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps,
-            warmup=args.warmup, ms_per_step=t_total / args.steps, higher_is_better=True,
-            scaling="weak", vs_baseline=None, dtype="u64", data="synthetic",
-            config=dict(workload=WORKLOADS[args.workload], num_u=r, num_l=l, num_edges=m,
-                        wedges_per_step=W, butterflies=expect, graph=graph_stats(g), derived=derived,
-                        step="prepare (a1-a5) + count (a6-a7), CSR resident in HBM",
-                        l2="flushed between steps (512 MB write outside the timed events)",
-                        parallelism=f"replicas x{world} (independent graphs, no collective)",
-                        orientation=["Algorithm 2 (BFC-VP)", "Algorithm 3 (BFC-VP++)"][args.orientation],
-                        prepare_ms_median=statistics.median(prep_ms),
-                        count_ms_median=statistics.median(count_ms),
-                        count_only_wedges_per_s=W / cnt_s,
-                        outputs="total + per-vertex + per-edge (bfc_count_all)" if outputs == "all"
-                        else "total (bfc_count)",
-                        bins=dict(dense_starts=info["dense_starts"], dense_items=info["dense_items"],
-                                  hash_starts=info["hash_starts"], team_starts=info["team_starts"],
-                                  warp_starts=info["warp_starts"]),
-                        oracle_agrees=verified),
-            roofline=roofline, smem_roofline=smem, cpu_baseline=cpu, e2e=e2e,
-            gpu_launches=launches, clocks=clocks)
-        print(json.dumps(out), flush=True)
-    dist_done(world)
-    return 0
+    out = dict(
+        metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps,
+        warmup=args.warmup, ms_per_step=t_total / args.steps, higher_is_better=True,
+        scaling="weak", vs_baseline=None, dtype="u64", data="synthetic",
+        config=dict(workload=WORKLOADS[workload], num_u=r, num_l=l, num_edges=m,
+                    wedges_per_step=W, butterflies=expect, graph=graph_stats(g), derived=derived,
+                    step="prepare (a1-a5) + count (a6-a7" + (", a8, a9" if outputs == "all" else "") +
+                         "), CSR resident in HBM",
+                    l2="flushed between steps (512 MB write outside the timed events)",
+                    parallelism=f"replicas x{world} (independent graphs, no collective)",
+                    orientation=["Algorithm 2 (BFC-VP)", "Algorithm 3 (BFC-VP++)"][args.orientation],
+                    prepare_ms_median=statistics.median(prep_ms),
+                    count_ms_median=statistics.median(count_ms),
+                    count_only_wedges_per_s=W / cnt_s,
+                    outputs="total + per-vertex + per-edge (bfc_count_all)" if outputs == "all"
+                    else "total (bfc_count)",
+                    bins=dict(dense_starts=info["dense_starts"], dense_items=info["dense_items"],
+                              hash_starts=info["hash_starts"], team_starts=info["team_starts"],
+                              warp_starts=info["warp_starts"]),
+                    oracle_agrees=verified),
+        roofline=roofline, smem_roofline=smem, cpu_baseline=cpu, e2e=e2e,
+        gpu_launches=launches, clocks=clocks)
+    del off, adj
+    if outputs == "all":
+        del per_u, per_l, per_e
+    torch.cuda.empty_cache()
+    return out
 
 
 if __name__ == "__main__":

@@ -110,7 +110,17 @@ typedef struct bfc_options {
                                Algorithm 2 caps it at hash_max_work; above 3072
                                a start whose team table fills up goes to the
                                retry pass. */
-    int32_t reserved[9];    /* must be zero */
+    int32_t core_vertices;  /* Algorithm 2 total counts (bfc_count) only: the
+                               K vertices of highest priority (Definition 3)
+                               form a core whose pairs are counted by a masked
+                               0/1 matrix product on the tensor cores (the
+                               walk skips every wedge with start, middle and
+                               end in the core and adds a·b + C(a, 2) per core
+                               pair, Lemma 1).  0 (default) = off; at most
+                               65,535 core vertices per layer.  Per-vertex and
+                               per-edge counts of the same graph walk every
+                               wedge as usual. */
+    int32_t reserved[8];    /* must be zero */
 } bfc_options;
 
 /* Figures of a prepared graph (host values). */
@@ -128,6 +138,7 @@ typedef struct bfc_info {
     int64_t device_bytes;     /* library-owned device memory held by the graph */
     int32_t max_deg_u, max_deg_l;
     int64_t team_starts;      /* starts in the team/hash bin */
+    int32_t core_u, core_l;   /* core vertices per layer (core_vertices option; 0 = no core) */
 } bfc_info;
 
 /* What bfc_export() can copy out (for parity tests; layouts as stated). */
@@ -140,8 +151,16 @@ typedef enum bfc_array {
     BFC_PROJ_EID = 4, /* int32[2m]: edge id (U-side slot) of each entry */
     BFC_CUT = 5,      /* int32[n]: |{y in N(x) : p(y) < p(x)}| per vertex of G* */
     BFC_WORK = 6,     /* uint64[n]: wedges Algorithm 2 processes from each start x of G* */
-    BFC_RETRIES = 7   /* int32[1]: starts whose hash table filled up in the last
+    BFC_RETRIES = 7,  /* int32[1]: starts whose hash table filled up in the last
                          count's first launch and went to the retry pass */
+    BFC_CORE_PRODUCT_U = 8, /* uint16[core_u * core_u] (bfc_info), row-major: for core U
+                         vertices u, w (G* ids num_l + num_u - core_u + i), entry
+                         (i_u, i_w) with i_w < i_u = the core middles v with p(v) < p(u)
+                         adjacent to both (the a of Lemma 1's split); entries with
+                         i_w >= i_u are unspecified.  Written by the last bfc_count
+                         of a graph prepared with core_vertices > 0 */
+    BFC_CORE_PRODUCT_L = 9  /* uint16[core_l * core_l]: the same for the L core (G* ids
+                         num_l - core_l + i) */
 } bfc_array;
 
 /* Fills *opt with the defaults listed above (NULL is ignored).  Library
@@ -170,14 +189,17 @@ int bfc_count_vertices(bfc_graph *g, void *stream, uint64_t *per_u_dev, uint64_t
 
 /* Step a9: per-edge counts ⋈_e (Eq. 7, Algorithm 4) indexed by edge id
  * (U-side slot): per_edge_dev[num_edges]; plus the total if total_dev !=
- * NULL.  Asynchronous; no allocation. */
+ * NULL.  Asynchronous; no host synchronisation.  The walks sum per slot of
+ * G* (two per edge): the first per-edge call on a graph takes that array,
+ * 16·num_edges bytes, from the library's pool (stream-ordered) and keeps it
+ * until bfc_release (BFC_ERR_OUT_OF_MEMORY if the pool cannot grow). */
 int bfc_count_edges(bfc_graph *g, void *stream, uint64_t *per_edge_dev, uint64_t *total_dev);
 
 /* Steps a8 and a9 together: the outputs of bfc_count_vertices and
  * bfc_count_edges from ONE first walk and ONE second walk (Algorithm 4's
  * pass attributes to vertices and edges at once).  per_u_dev / per_l_dev may
  * be NULL; per_edge_dev may be NULL only when num_edges is 0.  Asynchronous;
- * no allocation. */
+ * memory as bfc_count_edges. */
 int bfc_count_all(bfc_graph *g, void *stream, uint64_t *per_u_dev, uint64_t *per_l_dev,
                   uint64_t *per_edge_dev, uint64_t *total_dev);
 
@@ -247,9 +269,12 @@ typedef struct bfc_server_config {
 typedef struct bfc_server_stats {
     int64_t submitted, completed, failed, batches;
     int64_t max_batch_graphs;    /* largest batch formed */
-    int64_t peak_bytes_in_use;   /* largest admitted footprint (estimate) */
+    int64_t peak_bytes_in_use;   /* largest admitted footprint (the admission estimate) */
     int64_t bytes_in_use;        /* admitted footprint now */
     int64_t waiting;             /* requests not yet admitted */
+    int64_t pool_bytes_at_create; /* the library pool's bytes in use when the server was created */
+    int64_t pool_bytes_high;     /* the pool's measured high-water mark since then (all users of the
+                                    pool on this device, the server's batches included) */
 } bfc_server_stats;
 
 /* Fills *cfg with the defaults listed above (NULL is ignored). */
@@ -257,12 +282,21 @@ void bfc_server_config_init(bfc_server_config *cfg);
 
 /* Starts the workers on the current device.  *out is owned by the caller
  * until bfc_server_destroy.  BFC_ERR_INVALID_ARGUMENT for a configuration
- * outside the ranges above. */
+ * outside the ranges above (max_batch_edges at most 2^31 - 1, so a batch's
+ * CSR offsets fit int32); BFC_ERR_CUDA if a worker's stream cannot be created
+ * (no server is created then).  Resets the high-water mark of the library's
+ * device memory pool (see bfc_server_stats). */
 int bfc_server_create(const bfc_server_config *cfg, bfc_server **out);
 
 /* Queues one request.  off_u_host[num_u + 1] / adj_u_host[num_edges] must stay
  * valid until bfc_server_poll reports the request complete.  A request whose
- * footprint alone exceeds the budget returns BFC_ERR_OUT_OF_MEMORY. */
+ * footprint alone exceeds the budget returns BFC_ERR_OUT_OF_MEMORY; offsets
+ * that are not a CSR of num_edges entries, or an id outside [0, num_l),
+ * return BFC_ERR_INVALID_GRAPH (checked on the host here, so a bad request
+ * never joins a batch); |U| + |L| or num_edges above 2^31 - 1 return
+ * BFC_ERR_INVALID_ARGUMENT.  A duplicate edge is found on the device: the
+ * request completes with BFC_ERR_INVALID_GRAPH, and the other requests of its
+ * batch are counted again one by one, so their results are unchanged. */
 int bfc_server_submit(bfc_server *sv, int32_t num_u, int32_t num_l, int64_t num_edges,
                       const int32_t *off_u_host, const int32_t *adj_u_host, uint64_t *request_id);
 
@@ -310,11 +344,12 @@ int bfc_count_host(int32_t num_u, int32_t num_l, int64_t num_edges, const int32_
                    uint64_t *total_host, uint64_t *wedges_host);
 
 /* Allocation-free count for small graphs.  The paper has no counterpart: this
- * exists for callers that may not allocate device memory where they count --
- * code being recorded into a CUDA graph (allocation is illegal during stream
- * capture), code whose device memory is reserved up front by its own
- * allocator, or latency-bound loops that must not enter the driver's
- * allocator.  bfc_prepare cannot serve them because it allocates the
+ * exists for callers that may not allocate device memory where they count:
+ * code whose device memory is reserved up front by its own allocator (a
+ * caching allocator that already holds the whole budget, where one more
+ * cudaMalloc fails or fragments it), or latency-bound loops that must not
+ * enter the driver's allocator (cudaMalloc and cudaFree can synchronise the
+ * device).  bfc_prepare cannot serve them because it allocates the
  * renumbered graph.
  *
  * Computes ⋈_G of the U-side CSR (off_u_dev, adj_u_dev: device memory, the
@@ -363,6 +398,16 @@ long long bfc_kernel_launches(void);
  * written as one uint64 to caterpillars_dev (device).  Asynchronous on
  * `stream`; no allocation. */
 int bfc_caterpillars(bfc_graph *g, void *stream, uint64_t *caterpillars_dev);
+
+/* The bipartite clustering coefficient of Section 1's applications,
+ * 4·⋈_G / caterpillars (0 for a graph without three-paths), as one double
+ * in coefficient_dev (device).  butterflies_dev (device, one uint64) holds
+ * ⋈_G of this graph, for example written by bfc_count on the same stream
+ * before this call; the caterpillars are computed as by bfc_caterpillars
+ * into caterpillars_dev (device, one uint64).  Asynchronous on `stream`; no
+ * allocation.  BFC_ERR_INVALID_ARGUMENT for a null pointer. */
+int bfc_clustering_coefficient(bfc_graph *g, void *stream, const uint64_t *butterflies_dev,
+                               uint64_t *caterpillars_dev, double *coefficient_dev);
 
 /* Measurement aid (no counterpart in the paper): the throughput of the
  * count kernel's counter operation on the current device -- a returning

@@ -119,9 +119,17 @@ class ButterflyGraph:
         return int(out.item()) & ((1 << 64) - 1)
 
     def clustering_coefficient(self, stream=None) -> float:
-        """Bipartite clustering coefficient 4·⋈_G / caterpillars (0 without three-paths)."""
-        c = self.caterpillars(stream)
-        return 4.0 * self.count(stream) / c if c else 0.0
+        """Bipartite clustering coefficient 4·⋈_G / caterpillars (0 without
+        three-paths), computed by the library from a fresh count."""
+        import torch
+        tot = self.count_async(stream=stream)
+        cat = torch.zeros(1, dtype=torch.int64, device=self.device)
+        coef = torch.zeros(1, dtype=torch.float64, device=self.device)
+        sp, _ = _stream(stream)
+        bfc = _lib()
+        bfc.bfc_clustering_coefficient(self._h, sp, tot.data_ptr(), cat.data_ptr(), coef.data_ptr())
+        bfc.bfc_sync(self._h, sp)
+        return float(coef.item())
 
     def info(self) -> dict:
         return _lib().bfc_graph_info(self._h)
@@ -135,7 +143,11 @@ class ButterflyGraph:
         spec = {bfc.BFC_RANK_U: (self.num_u, torch.int32), bfc.BFC_RANK_L: (self.num_l, torch.int32),
                 bfc.BFC_PROJ_OFF: (n + 1, torch.int64), bfc.BFC_PROJ_ADJ: (2 * m, torch.int32),
                 bfc.BFC_PROJ_EID: (2 * m, torch.int32), bfc.BFC_CUT: (n, torch.int32),
-                bfc.BFC_WORK: (n, torch.int64), bfc.BFC_RETRIES: (1, torch.int32)}[which]
+                bfc.BFC_WORK: (n, torch.int64), bfc.BFC_RETRIES: (1, torch.int32)}
+        info = self.info()
+        spec[bfc.BFC_CORE_PRODUCT_U] = (info["core_u"] ** 2, torch.int16)
+        spec[bfc.BFC_CORE_PRODUCT_L] = (info["core_l"] ** 2, torch.int16)
+        spec = spec[which]
         t = torch.empty(max(spec[0], 1), dtype=spec[1], device=self.device)
         sp, _ = _stream(stream)
         bfc.bfc_export(self._h, which, t.data_ptr(), sp)

@@ -23,7 +23,8 @@ BFC_OK = 0
 STATUS = {0: "BFC_OK", 1: "BFC_ERR_INVALID_ARGUMENT", 2: "BFC_ERR_INVALID_GRAPH",
           3: "BFC_ERR_OUT_OF_MEMORY", 4: "BFC_ERR_CUDA", 5: "BFC_ERR_TIMEOUT",
           6: "BFC_ERR_INTERNAL"}
-BFC_RANK_U, BFC_RANK_L, BFC_PROJ_OFF, BFC_PROJ_ADJ, BFC_PROJ_EID, BFC_CUT, BFC_WORK, BFC_RETRIES = range(8)
+(BFC_RANK_U, BFC_RANK_L, BFC_PROJ_OFF, BFC_PROJ_ADJ, BFC_PROJ_EID, BFC_CUT, BFC_WORK, BFC_RETRIES,
+ BFC_CORE_PRODUCT_U, BFC_CORE_PRODUCT_L) = range(10)
 
 
 class bfc_csr(ctypes.Structure):
@@ -34,7 +35,7 @@ class bfc_csr(ctypes.Structure):
 class bfc_options(ctypes.Structure):
     _fields_ = [("validate", c_int32), ("warp_max_work", c_int32), ("hash_max_work", c_int32),
                 ("num_ctas", c_int32), ("wide_positions", c_int32), ("orientation", c_int32),
-                ("team_max_work", c_int32), ("reserved", c_int32 * 9)]
+                ("team_max_work", c_int32), ("core_vertices", c_int32), ("reserved", c_int32 * 8)]
 
 
 class bfc_info(ctypes.Structure):
@@ -42,7 +43,8 @@ class bfc_info(ctypes.Structure):
                 ("wedges", c_uint64), ("max_start_work", c_uint64),
                 ("starts_with_work", c_int64), ("warp_starts", c_int64), ("hash_starts", c_int64),
                 ("dense_starts", c_int64), ("dense_items", c_int64), ("device_bytes", c_int64),
-                ("max_deg_u", c_int32), ("max_deg_l", c_int32), ("team_starts", c_int64)]
+                ("max_deg_u", c_int32), ("max_deg_l", c_int32), ("team_starts", c_int64),
+                ("core_u", c_int32), ("core_l", c_int32)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -61,7 +63,7 @@ class bfc_server_config(ctypes.Structure):
 class bfc_server_stats(ctypes.Structure):
     _fields_ = [(k, c_int64) for k in ("submitted", "completed", "failed", "batches",
                                        "max_batch_graphs", "peak_bytes_in_use", "bytes_in_use",
-                                       "waiting")]
+                                       "waiting", "pool_bytes_at_create", "pool_bytes_high")]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -98,6 +100,7 @@ _SIGS = {
     "bfc_version": (c_int, []),
     "bfc_kernel_launches": (ctypes.c_longlong, []),
     "bfc_caterpillars": (c_int, [c_void_p, c_void_p, c_void_p]),
+    "bfc_clustering_coefficient": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "bfc_bench_smem_atomics": (c_int, [c_void_p, c_int32, ctypes.POINTER(ctypes.c_double),
                                        ctypes.POINTER(ctypes.c_double)]),
     "bfc_prepare_batch": (c_int, [ctypes.POINTER(bfc_csr), ctypes.POINTER(bfc_batch),
@@ -292,6 +295,12 @@ def bfc_version() -> int:
 
 def bfc_caterpillars(g: int, stream: int, out_dev: int):
     _check(_lib.bfc_caterpillars(g, stream, out_dev), "bfc_caterpillars")
+
+
+def bfc_clustering_coefficient(g: int, stream: int, butterflies_dev: int, caterpillars_dev: int,
+                               coefficient_dev: int):
+    _check(_lib.bfc_clustering_coefficient(g, stream, butterflies_dev, caterpillars_dev,
+                                           coefficient_dev), "bfc_clustering_coefficient")
 
 
 def bfc_kernel_launches() -> int:

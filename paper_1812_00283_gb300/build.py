@@ -16,7 +16,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libbfc.so")
-SOURCES = ["api.cu", "prepare.cu", "count.cu", "scan_sort.cu", "noalloc.cu", "server.cu", "microbench.cu", "derived.cu"]
+SOURCES = ["api.cu", "prepare.cu", "count.cu", "scan_sort.cu", "noalloc.cu", "server.cu", "microbench.cu",
+           "derived.cu", "core.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

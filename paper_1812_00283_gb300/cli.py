@@ -41,6 +41,8 @@ def main(argv=None):
     ap.add_argument("--hash-max-work", type=int, default=None)
     ap.add_argument("--team-max-work", type=int, default=None)
     ap.add_argument("--orientation", type=int, default=0, choices=[0, 1])
+    ap.add_argument("--core-vertices", type=int, default=0,
+                    help="top-K priority core counted by the tensor-core product (total counts)")
     args = ap.parse_args(argv)
 
     import torch
@@ -59,6 +61,7 @@ def main(argv=None):
     if args.team_max_work is not None:
         opts.team_max_work = args.team_max_work
     opts.orientation = args.orientation
+    opts.core_vertices = args.core_vertices
     s = torch.cuda.current_stream()
     sp = s.cuda_stream
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

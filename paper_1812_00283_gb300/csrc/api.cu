@@ -11,6 +11,7 @@
 namespace bfc {
 
 int gather_vertices(Graph *g, cudaStream_t s, uint64_t *per_u, uint64_t *per_l);
+int gather_edges(Graph *g, cudaStream_t s, uint64_t *per_edge);
 
 namespace {
 thread_local std::string g_last_error;
@@ -66,6 +67,23 @@ void pool_free(void *p, cudaStream_t s) {
     if (p) cudaFreeAsync(p, s);
 }
 
+cudaError_t pool_usage(int64_t *current, int64_t *high, bool reset_high) {
+    cudaMemPool_t pool;
+    cudaError_t e = get_pool(&pool);
+    if (e != cudaSuccess) return e;
+    if (reset_high) {
+        uint64_t zero = 0;   // the high-water mark can only be reset to zero
+        e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &zero);
+        if (e != cudaSuccess) return e;
+    }
+    uint64_t cur = 0, hi = 0;
+    e = cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &cur);
+    if (e == cudaSuccess) e = cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &hi);
+    if (current) *current = (int64_t)cur;
+    if (high) *high = (int64_t)hi;
+    return e;
+}
+
 }  // namespace bfc
 
 using bfc::Graph;
@@ -105,7 +123,11 @@ static int check_options(const bfc_options *o) {
         bfc::set_last_error("orientation must be 0 (Algorithm 2) or 1 (Algorithm 3)");
         return BFC_ERR_INVALID_ARGUMENT;
     }
-    for (int i = 0; i < 9; ++i)
+    if (o->core_vertices < 0) {
+        bfc::set_last_error("core_vertices must be >= 0");
+        return BFC_ERR_INVALID_ARGUMENT;
+    }
+    for (int i = 0; i < 8; ++i)
         if (o->reserved[i] != 0) {
             bfc::set_last_error("reserved option fields must be zero");
             return BFC_ERR_INVALID_ARGUMENT;
@@ -188,13 +210,23 @@ static int count_common(bfc_graph *h, void *stream, int mode, uint64_t *per_a, u
         BFC_CUDA(cudaMemsetAsync(pv, 0, sizeof(unsigned long long) * (size_t)(g->n > 0 ? g->n : 1), s));
     }
     if (bfc::wants_edges(mode)) {
-        pe = reinterpret_cast<unsigned long long *>(mode == bfc::kModeEdges ? per_a : per_edge);
-        if (g->m > 0) BFC_CUDA(cudaMemsetAsync(pe, 0, sizeof(uint64_t) * (size_t)g->m, s));
+        // the walks sum per G* slot (two per edge); the slot array is taken
+        // from the pool on the first per-edge count (stream-ordered) and kept
+        if (!g->pe_slot) {
+            g->mem.stream = s;
+            BFC_CUDA(g->mem.get(&g->pe_slot, (size_t)(2 * g->m > 0 ? 2 * g->m : 1)));
+        }
+        pe = g->pe_slot;
+        if (g->m > 0) BFC_CUDA(cudaMemsetAsync(pe, 0, sizeof(uint64_t) * (size_t)(2 * g->m), s));
     }
     int rc = bfc::launch_count(g, s, mode, pv, pe);
     if (rc) return rc;
     if (bfc::wants_vertices(mode)) {
         rc = bfc::gather_vertices(g, s, per_a, per_b);
+        if (rc) return rc;
+    }
+    if (bfc::wants_edges(mode)) {
+        rc = bfc::gather_edges(g, s, mode == bfc::kModeEdges ? per_a : per_edge);
         if (rc) return rc;
     }
     if (total_dev)
@@ -354,6 +386,11 @@ int bfc_sync(bfc_graph *h, void *stream) {
         BFC_CUDA(cudaMemsetAsync(g->err, 0, sizeof(int), s));
         BFC_CUDA(cudaStreamSynchronize(s));
         char buf[96];
+        if (herr & bfc::kErrTimeout) {
+            snprintf(buf, sizeof(buf), "a bounded device wait gave up (flags 0x%x)", herr);
+            bfc::set_last_error(buf);
+            return BFC_ERR_TIMEOUT;
+        }
         snprintf(buf, sizeof(buf), "kernel consistency check fired (flags 0x%x)", herr);
         bfc::set_last_error(buf);
         return BFC_ERR_INTERNAL;
@@ -382,6 +419,17 @@ int bfc_export(const bfc_graph *h, int which, void *dst, void *stream) {
         case BFC_CUT: src = g->cut; bytes = 4 * (size_t)g->n; break;
         case BFC_WORK: src = g->work; bytes = 8 * (size_t)g->n; break;
         case BFC_RETRIES: src = g->cursors + 2; bytes = 4; break;
+        case BFC_CORE_PRODUCT_U:
+        case BFC_CORE_PRODUCT_L: {
+            // rows of the padded product, core_u (core_l) columns each
+            const bool u = which == BFC_CORE_PRODUCT_U;
+            const int32_t k = u ? g->core_u : g->core_l;
+            if (k > 0)
+                BFC_CUDA(cudaMemcpy2DAsync(dst, 2 * (size_t)k, u ? g->core_au : g->core_al,
+                                           2 * (size_t)(u ? g->core_ld_u : g->core_ld_l), 2 * (size_t)k,
+                                           (size_t)k, cudaMemcpyDeviceToDevice, s));
+            return BFC_OK;
+        }
         default: bfc::set_last_error("unknown array"); return BFC_ERR_INVALID_ARGUMENT;
     }
     if (bytes) BFC_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, s));

@@ -41,6 +41,7 @@ constexpr int kErrBadId = 2;
 constexpr int kErrDuplicate = 4;
 constexpr int kErrHashFull = 8;
 constexpr int kErrBounds = 16;
+constexpr int kErrTimeout = 32;   // a bounded device wait gave up
 
 // ---------------------------------------------------------------------------
 // Host-side error reporting
@@ -61,6 +62,9 @@ int cuda_fail(cudaError_t e, const char *what);
 // ---------------------------------------------------------------------------
 cudaError_t pool_alloc(void **p, size_t bytes, cudaStream_t s);
 void pool_free(void *p, cudaStream_t s);
+// Bytes of the current device's pool in use now and its high-water mark
+// (reset to zero first when reset_high).
+cudaError_t pool_usage(int64_t *current, int64_t *high, bool reset_high);
 
 // A list of pool allocations released together.
 struct Allocs {
@@ -156,6 +160,21 @@ struct Graph {
     int64_t retry_static = 0;             // of which assigned there by prepare
     int64_t retry_cap = 0;
     unsigned long long *gwork = nullptr;  // [num_graphs] wedges per graph
+    // per-edge sums by G* slot [2m], taken from the pool by the first
+    // per-edge count and kept until release
+    unsigned long long *pe_slot = nullptr;
+    // dense high-priority core counted by a product (total counts only):
+    // core_u / core_l vertices at the top of each layer's ids, starting at
+    // core_lo_u / core_lo_l; ccut[x] = neighbours of core vertex x outside the
+    // other layer's core; B and Bm of both cores (bf16 bits, padded to
+    // core_ld_* = multiples of 128); the products a(u, w) as uint16; per row
+    // tile the contraction length in 64-column blocks; TMA maps of Bm and B
+    int32_t core_u = 0, core_l = 0, core_lo_u = 0, core_lo_l = 0, core_ld_u = 0, core_ld_l = 0;
+    int32_t *ccut = nullptr;
+    uint16_t *core_bu = nullptr, *core_bum = nullptr, *core_bl = nullptr, *core_blm = nullptr;
+    uint16_t *core_au = nullptr, *core_al = nullptr;
+    int32_t *core_kb_u = nullptr, *core_kb_l = nullptr;
+    alignas(64) unsigned char core_map_bytes[4][128];
 };
 
 // ---------------------------------------------------------------------------
@@ -202,6 +221,10 @@ int launch_count(Graph *g, cudaStream_t s, int mode, unsigned long long *pv_proj
 int rebin_graph(Graph *g, cudaStream_t s, int32_t warp_max_work, int32_t team_max_work,
                 int32_t hash_max_work);
 int count_smem_setup(int device);
+// the dense-core hybrid (core.cu): core choice and matrices in prepare, the
+// masked products before a total count
+int core_prepare(Graph *g, cudaStream_t s, const int32_t *deg_star);
+int core_product(Graph *g, cudaStream_t s);
 
 // small helpers
 inline int bits_for(uint64_t x) {  // bits needed to represent x (0 for x = 0)

@@ -33,6 +33,7 @@
 // needed with dense chunks of its end range.
 #include "bfc_internal.cuh"
 
+#include <algorithm>
 #include <type_traits>
 
 namespace bfc {
@@ -59,7 +60,7 @@ struct CountParams {
     int *cursors;                      // [0] CTA, [1] warp, [2] retry pushes, [3] retry, [4] team
     unsigned long long *acc;
     unsigned long long *pv;            // [n] in G* ids
-    unsigned long long *pe;            // [m] by edge id
+    unsigned long long *pe;            // [2m] by G* slot (each edge has two)
     const int32_t *__restrict__ coff;  // chunk-boundary table (nullable; Algorithm 2 only)
     const int32_t *__restrict__ gstar; // graph of each G* vertex (batch mode)
     const int32_t *__restrict__ vbase; // first id of x's graph in x's layer (batch mode)
@@ -76,6 +77,14 @@ struct CountParams {
     int64_t adj_len;
     int32_t l;
     int *err;
+    // dense-core hybrid (total counts): core starts skip core middles' core
+    // ends and add a·b + C(a, 2) per core pair after their walk
+    int32_t core_on;
+    int32_t core_lo_u, core_lo_l;          // first core id of each layer (n when none)
+    int32_t core_ld_u, core_ld_l;          // row pitch of the products
+    const int32_t *__restrict__ ccut;      // neighbours outside the other layer's core
+    const uint16_t *__restrict__ core_au;  // a(u, w) of the U core
+    const uint16_t *__restrict__ core_al;  // a(v, x) of the L core
 };
 
 // The threads that walk one start together: the whole CTA (barrier 0) or one
@@ -270,7 +279,9 @@ __device__ __forceinline__ unsigned long long wedge_op(const CountParams &p, int
     }
     // δ = count − 1 for the edge (middle, w); the caller sums it per middle
     const unsigned long long delta = (unsigned long long)c - 1ull;
-    if (wants_edges(MODE) && delta) atomicAdd(p.pe + __ldg(p.eid + pos), delta);
+    // per-edge sums are kept by G* slot: the ends of one run are consecutive
+    // slots, so a window's atomics fall on a few consecutive sectors
+    if (wants_edges(MODE) && delta) atomicAdd(p.pe + pos, delta);
     return delta;
 }
 
@@ -313,7 +324,8 @@ __device__ __forceinline__ void batch_runs(const CountParams &p, int64_t e0, int
                                            int32_t lb, int32_t lo, int32_t hi, int flags,
                                            unsigned char *ctr, int zero_bytes, SH &sh,
                                            const Team<kThreads> &t, BatchSlots<Pos, kThreads> &bs,
-                                           int32_t *total_out, int *nnz_out) {
+                                           int32_t *total_out, int *nnz_out,
+                                           int32_t core_lo_v = 0x7fffffff) {
     constexpr int kPer = Batch<Pos, kThreads>::kPer;
     const int tid = t.tid;
     int32_t pl[kPer];
@@ -333,6 +345,13 @@ __device__ __forceinline__ void batch_runs(const CountParams &p, int64_t e0, int
         // suffix above both x and v (Algorithm 3)
         b[i] = has[i] ? __ldg(p.sbeg + bs.e[i]) : 0;
     }
+    // a core start: a core middle's run stops before its core ends (they are
+    // the top of the run, and the product counts those wedges)
+    if (core_lo_v != 0x7fffffff) {
+#pragma unroll
+        for (int i = 0; i < kPer; ++i)
+            if (has[i] && bs.v[i] >= core_lo_v) pl[i] = min(pl[i], __ldg(p.ccut + bs.v[i]));
+    }
     int32_t s0[kPer], s1[kPer];
 #pragma unroll
     for (int i = 0; i < kPer; ++i) {
@@ -345,6 +364,10 @@ __device__ __forceinline__ void batch_runs(const CountParams &p, int64_t e0, int
                                            : (int64_t)p.l * p.coff_u1 + (int64_t)(v - p.l) * p.coff_l1;
                 if (flags & 1) s0[i] = __ldg(p.coff + tb + lo / kChunkUnit);
                 if (flags & 2) s1[i] = __ldg(p.coff + tb + hi / kChunkUnit);
+                if (core_lo_v != 0x7fffffff) {   // chunk bounds past a shortened run
+                    s1[i] = min(s1[i], pl[i]);
+                    s0[i] = min(s0[i], s1[i]);
+                }
             } else {
                 if (flags & 1) s0[i] = lower_bound_g(p.adj + b[i], pl[i], lb + lo);
                 if (flags & 2) s1[i] = lower_bound_g(p.adj + b[i], pl[i], lb + hi);
@@ -547,7 +570,7 @@ __device__ unsigned long long team_walk(const CountParams &p, int32_t x, int32_t
                     const unsigned long long dsum = sh.msum[bs.nzs[i]];
                     if (dsum) {
                         if (wants_vertices(MODE)) atomicAdd(p.pv + bs.v[i], dsum);
-                        if (wants_edges(MODE)) atomicAdd(p.pe + __ldg(p.eid + bs.e[i]), dsum);
+                        if (wants_edges(MODE)) atomicAdd(p.pe + bs.e[i], dsum);
                     }
                 }
             }
@@ -746,6 +769,10 @@ __device__ unsigned long long dense_stream(const CountParams &p, int64_t &it, un
         const int flags = (lo > 0 ? 1 : 0) | (hi < R ? 2 : 0);
         const int64_t e0 = p.off[x];
         const int32_t nmid = p.cut[x];
+        // dense-core hybrid: x in its layer's core (uniform over the item)
+        const int32_t clo_x = x >= p.l ? p.core_lo_u : p.core_lo_l;
+        const bool core_x = p.core_on && x >= clo_x;
+        const int32_t core_lo_v = core_x ? (x >= p.l ? p.core_lo_l : p.core_lo_u) : 0x7fffffff;
         unsigned long long item_acc = 0;
         int32_t mb = 0;
         do {
@@ -758,7 +785,7 @@ __device__ unsigned long long dense_stream(const CountParams &p, int64_t &it, un
             int nnz;
             const int zero_bytes = mb > 0 ? 0 : (wide ? span * 4 : ((span + 1) >> 1) * 4);
             batch_runs<true, false, Pos>(p, e0, nmid, mb, lb, lo, hi, flags, ctr, zero_bytes, sh, t, bs,
-                                         &total, &nnz);
+                                         &total, &nnz, core_lo_v);
             t.sync();
             item_acc += wide ? batch_windows<MODE, kDenseWide, false, Pos>(p, lb, lo, span, 0, ctr, total,
                                                                           nnz, nullptr, sh, t)
@@ -766,6 +793,27 @@ __device__ unsigned long long dense_stream(const CountParams &p, int64_t &it, un
                                                                             nnz, nullptr, sh, t);
             mb += kB;
         } while (mb < nmid);
+        if (core_x) {
+            // every core end w of this chunk: count_wedge(w) = b (the walk's
+            // middles outside the core) + a (the product's core middles), and
+            // C(a + b, 2) - C(b, 2) = a·b + C(a, 2) (Lemma 1).  The next
+            // item's scan clears the counters after its first barrier, so
+            // the reads below come before it.
+            t.sync();
+            const bool in_u = x >= p.l;
+            const uint16_t *arow = (in_u ? p.core_au : p.core_al) +
+                                   (int64_t)(x - clo_x) * (in_u ? p.core_ld_u : p.core_ld_l);
+            const uint32_t *w32 = reinterpret_cast<const uint32_t *>(ctr);
+            const int32_t w_hi = lb + hi;
+            unsigned long long e = 0;
+            for (int32_t w = max(lb + lo, clo_x) + t.tid; w < w_hi; w += kCountThreads) {
+                const unsigned long long a = __ldg(arow + (w - clo_x));
+                const int idx = w - lb - lo;
+                const unsigned long long b = wide ? w32[idx] : get16(w32, idx);
+                e += a * b + (a * (a - 1)) / 2;   // a = 0 gives 0
+            }
+            item_acc += e;
+        }
         if (MODE == kModeBatch) {
             // this warp's share of x's butterflies goes to x's graph
             unsigned long long w = item_acc;
@@ -861,7 +909,7 @@ __device__ unsigned long long warp_walk(const CountParams &p, int32_t x, int32_t
                         acc += atomicAdd(cnt + slot, 1u);
                     } else {
                         delta = cnt[slot] - 1u;   // below 384
-                        if (wants_edges(MODE) && delta) atomicAdd(p.pe + __ldg(p.eid + pos), (unsigned long long)delta);
+                        if (wants_edges(MODE) && delta) atomicAdd(p.pe + pos, (unsigned long long)delta);
                     }
                 }
             }
@@ -872,7 +920,7 @@ __device__ unsigned long long warp_walk(const CountParams &p, int32_t x, int32_t
             const unsigned long long dsum = msum[nz];
             if (dsum) {
                 if (wants_vertices(MODE)) atomicAdd(p.pv + v, dsum);
-                if (wants_edges(MODE)) atomicAdd(p.pe + __ldg(p.eid + e), dsum);
+                if (wants_edges(MODE)) atomicAdd(p.pe + e, dsum);
             }
         }
         __syncwarp();
@@ -1033,6 +1081,26 @@ __global__ void k_gather_vertices(const unsigned long long *__restrict__ pv,
     if (i < l && per_l) per_l[i] = pv[rank_l[i]];
 }
 
+// ⋈_e from the two G* slots of every edge: the U-side slots [m, 2m) hold
+// each edge once, in rows that are permutations of the caller's rows (so
+// the stores stay inside one row), then the L-side slots [0, m) add theirs.
+// Every edge id occurs once per side, so neither pass needs atomics; the
+// second runs after the first on the same stream.
+__global__ void k_edges_from_slots_u(const unsigned long long *__restrict__ pe_slot,
+                                     const int32_t *__restrict__ eid, int64_t m, uint64_t *per_edge) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride)
+        per_edge[__ldg(eid + m + i)] = pe_slot[m + i];
+}
+__global__ void k_edges_from_slots_l(const unsigned long long *__restrict__ pe_slot,
+                                     const int32_t *__restrict__ eid, int64_t m, uint64_t *per_edge) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
+        const unsigned long long x = pe_slot[i];
+        if (x) per_edge[__ldg(eid + i)] += x;
+    }
+}
+
 template <int MODE, typename Pos>
 cudaError_t setup_one() {
     cudaError_t e = cudaFuncSetAttribute(k_count<MODE, Pos>,
@@ -1106,6 +1174,16 @@ int launch_count(Graph *g, cudaStream_t s, int mode, unsigned long long *pv_proj
     p.retry_on = g->may_retry ? 1 : 0;
     p.orient = g->opt.orientation; p.n = g->n;
     p.adj_len = 2 * g->m; p.l = g->l; p.err = g->err;
+    p.core_on = (mode == kModeTotal && g->core_u + g->core_l > 0) ? 1 : 0;
+    p.core_lo_u = g->core_u > 0 ? g->core_lo_u : g->n;
+    p.core_lo_l = g->core_l > 0 ? g->core_lo_l : g->n;
+    p.core_ld_u = g->core_ld_u; p.core_ld_l = g->core_ld_l;
+    p.ccut = g->ccut; p.core_au = g->core_au; p.core_al = g->core_al;
+    if (p.core_on) {
+        // the core pairs' a(u, w), on the same stream before the walk
+        int rc2 = core_product(g, s);
+        if (rc2) return rc2;
+    }
     BFC_CUDA(cudaMemsetAsync(g->cursors, 0, 8 * sizeof(int), s));
     BFC_CUDA(cudaMemsetAsync(g->acc, 0, sizeof(unsigned long long), s));
     const int grid = g->grid;
@@ -1122,6 +1200,18 @@ int launch_count(Graph *g, cudaStream_t s, int mode, unsigned long long *pv_proj
         note_launch();
         BFC_CUDA(cudaGetLastError());
     }
+    return BFC_OK;
+}
+
+int gather_edges(Graph *g, cudaStream_t s, uint64_t *per_edge) {
+    if (g->m == 0) return BFC_OK;
+    const unsigned blocks = (unsigned)std::min<int64_t>((g->m + 255) / 256, (int64_t)g->num_sms * 16);
+    k_edges_from_slots_u<<<blocks, 256, 0, s>>>(g->pe_slot, g->eid, g->m, per_edge);
+    note_launch();
+    BFC_CUDA(cudaGetLastError());
+    k_edges_from_slots_l<<<blocks, 256, 0, s>>>(g->pe_slot, g->eid, g->m, per_edge);
+    note_launch();
+    BFC_CUDA(cudaGetLastError());
     return BFC_OK;
 }
 

@@ -32,8 +32,31 @@ __global__ void k_caterpillars(const int64_t *__restrict__ off, const int32_t *_
     if (lane == 0 && sum) atomicAdd(out, sum);
 }
 
+// coefficient = 4·⋈_G / caterpillars, 0 when the graph has no three-path
+__global__ void k_clustering(const unsigned long long *butterflies,
+                             const unsigned long long *caterpillars, double *coefficient) {
+    const unsigned long long c = *caterpillars;
+    *coefficient = c ? 4.0 * (double)*butterflies / (double)c : 0.0;
+}
+
 }  // namespace
 }  // namespace bfc
+
+extern "C" int bfc_clustering_coefficient(bfc_graph *h, void *stream, const uint64_t *butterflies_dev,
+                                          uint64_t *caterpillars_dev, double *coefficient_dev) {
+    if (!h || !butterflies_dev || !caterpillars_dev || !coefficient_dev) {
+        bfc::set_last_error("null argument");
+        return BFC_ERR_INVALID_ARGUMENT;
+    }
+    const int rc = bfc_caterpillars(h, stream, caterpillars_dev);
+    if (rc) return rc;
+    bfc::k_clustering<<<1, 1, 0, static_cast<cudaStream_t>(stream)>>>(
+        reinterpret_cast<const unsigned long long *>(butterflies_dev),
+        reinterpret_cast<const unsigned long long *>(caterpillars_dev), coefficient_dev);
+    bfc::note_launch();
+    BFC_CUDA(cudaGetLastError());
+    return BFC_OK;
+}
 
 extern "C" int bfc_caterpillars(bfc_graph *h, void *stream, uint64_t *caterpillars_dev) {
     bfc::set_last_error("");

@@ -2,11 +2,10 @@
 // allocates nothing.
 //
 // Who needs it: code that may not call cudaMalloc or any allocating routine
-// at the point where it counts -- for example a caller that records its work
-// into a CUDA graph (allocation is not allowed while a stream is being
-// captured), a caller whose memory is fully reserved up front by its own
-// allocator and that may not grow the device footprint, or a real-time loop
-// that must not hit the driver's allocator.  The regular entry points
+// at the point where it counts -- for example a caller whose memory is fully
+// reserved up front by its own allocator and that may not grow the device
+// footprint, or a real-time loop that must not hit the driver's allocator
+// (which can synchronise the device).  The regular entry points
 // (bfc_prepare and friends) allocate the renumbered graph from a pool, so
 // they are not usable there.
 //

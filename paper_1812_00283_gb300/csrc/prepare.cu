@@ -412,11 +412,20 @@ __global__ void k_work(const int64_t *__restrict__ off, const int32_t *__restric
 }
 
 // ----- a5: bins and schedule ---------------------------------------------------
+// a core start (dense-core hybrid) with wedges is always a dense item: the
+// count kernel adds its core pairs after the item's walk
+__device__ __forceinline__ bool forced_dense(int32_t x, int32_t l, int32_t core_lo_u, int32_t core_lo_l,
+                                             uint64_t w) {
+    return w > 0 && (x >= l ? x >= core_lo_u : x >= core_lo_l);
+}
+
 __global__ void k_sched_keys(const uint64_t *__restrict__ work, int32_t n, uint64_t maxw,
-                             uint64_t *keys, int32_t *vals) {
+                             int32_t l, int32_t core_lo_u, int32_t core_lo_l, uint64_t *keys,
+                             int32_t *vals) {
     int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= n) return;
-    keys[x] = maxw - work[x];   // ascending key = descending work; zero work last
+    // ascending key = descending work; zero work last; forced dense starts first
+    keys[x] = forced_dense((int32_t)x, l, core_lo_u, core_lo_l, work[x]) ? 0 : maxw - work[x];
     vals[x] = (int32_t)x;
 }
 
@@ -424,12 +433,13 @@ __global__ void k_sched_keys(const uint64_t *__restrict__ work, int32_t n, uint6
 // Bins of a6: [0] dense (work > hash_max), [1] CTA hash (team_max < work <=
 // hash_max), [2] team (warp_max < work <= team_max), [3] warp (0 < work <= warp_max).
 __global__ void k_classify(const uint64_t *__restrict__ work, int32_t n, uint64_t warp_max,
-                           uint64_t team_max, uint64_t hash_max, unsigned long long *counts) {
+                           uint64_t team_max, uint64_t hash_max, int32_t l, int32_t core_lo_u,
+                           int32_t core_lo_l, unsigned long long *counts) {
     unsigned long long c[4] = {0, 0, 0, 0};
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
          x += (int64_t)gridDim.x * blockDim.x) {
         uint64_t w = work[x];
-        if (w > hash_max) ++c[0];
+        if (w > hash_max || forced_dense((int32_t)x, l, core_lo_u, core_lo_l, w)) ++c[0];
         else if (w > team_max) ++c[1];
         else if (w > warp_max) ++c[2];
         else if (w > 0) ++c[3];
@@ -642,11 +652,14 @@ static int schedule_graph(Graph *g, cudaStream_t s, int32_t warp_max_work, int32
         GET(tmp, red, 4);
         BFC_CUDA(cudaMemsetAsync(red, 0, 4 * sizeof(unsigned long long), s));
         int which = 0;
-        k_sched_keys<<<blocks_for(n), kT, 0, s>>>(g->work, n, maxw, k0, v0); note_launch();
+        // without a core the bounds lie past every id
+        const int32_t clo_u = g->core_u > 0 ? g->core_lo_u : n, clo_l = g->core_l > 0 ? g->core_lo_l : n;
+        k_sched_keys<<<blocks_for(n), kT, 0, s>>>(g->work, n, maxw, l, clo_u, clo_l, k0, v0); note_launch();
         BFC_CUDA(cudaGetLastError());
         BFC_CUDA(radix_sort_pairs(k0, v0, k1, v1, n, 0, bits_for(maxw), hist, hist_tmp, s, &which));
         const int32_t *order = which ? v1 : v0;
-        k_classify<<<grid_stride_blocks(n), kT, 0, s>>>(g->work, n, warp_max, team_max, hash_max, red); note_launch();
+        k_classify<<<grid_stride_blocks(n), kT, 0, s>>>(g->work, n, warp_max, team_max, hash_max, l, clo_u,
+                                                        clo_l, red); note_launch();
         BFC_CUDA(cudaGetLastError());
         unsigned long long hc[4];
         BFC_CUDA(cudaMemcpyAsync(hc, red, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
@@ -1024,6 +1037,14 @@ int prepare_graph(const bfc_csr *csr, const bfc_options *opt, cudaStream_t s, Gr
     BFC_CUDA(cudaStreamSynchronize(s));
     g->info.wedges = hred[0];
     g->info.max_start_work = hred[1];
+
+    // ---- dense-core hybrid (Algorithm 2 single graphs with core_vertices > 0)
+    if (opt->core_vertices > 0 && opt->orientation == 0 && num_graphs == 0) {
+        int rc = core_prepare(g, s, deg_star);
+        if (rc) return rc;
+    }
+    g->info.core_u = g->core_u;
+    g->info.core_l = g->core_l;
 
     // ---- a5: heaviest-first order and bins
     {

@@ -30,6 +30,21 @@ int64_t batch_bytes(int64_t r, int64_t l, int64_t m) {
     return 112 * m + 64 * (r + l) + (4 << 20);
 }
 
+// The graph contract's cheap host-side part, checked at submission so that a
+// malformed request fails alone instead of failing the batch it would join:
+// off_u is a CSR of num_edges entries and every id lies in [0, num_l).
+bool host_csr_ok(int32_t r, int32_t l, int64_t m, const int32_t *off, const int32_t *adj) {
+    if (off[0] != 0 || (int64_t)off[r] != m) return false;
+    for (int32_t u = 0; u < r; ++u)
+        if (off[u + 1] < off[u]) return false;
+    for (int64_t k = 0; k < m; ++k)
+        if (adj[k] < 0 || adj[k] >= l) return false;
+    return true;
+}
+
+// a union of graphs keeps its vertex ids and its CSR offsets in int32
+constexpr int64_t kUnionMax = 0x7fffffffll;
+
 // offsets and ids of each graph shifted into the union's id space
 __global__ void k_union_fixup(int32_t *off, int32_t *adj, const int64_t *__restrict__ e_start,
                               const int32_t *__restrict__ u_start,
@@ -78,6 +93,7 @@ struct bfc_server {
     std::deque<bfc::Request *> waiting;
     std::unordered_map<uint64_t, bfc::Request *> all;
     std::vector<std::thread> workers;
+    std::vector<cudaStream_t> streams;   // one per worker, created before any worker starts
     uint64_t next_id = 1;
     int64_t bytes_in_use = 0;
     bool stop = false;
@@ -87,14 +103,16 @@ struct bfc_server {
 namespace bfc {
 namespace {
 
-void complete(bfc_server *sv, std::vector<Request *> &batch, int status, const uint64_t *totals) {
+void complete(bfc_server *sv, std::vector<Request *> &batch, const std::vector<int> &status,
+              const std::vector<uint64_t> &totals) {
     const auto now = std::chrono::steady_clock::now();
     std::lock_guard<std::mutex> lk(sv->mu);
     for (size_t i = 0; i < batch.size(); ++i) {
-        batch[i]->status = status;
-        batch[i]->total = (status == BFC_OK && totals) ? totals[i] : 0;
+        const int st = status[i];
+        batch[i]->status = st;
+        batch[i]->total = (st == BFC_OK && i < totals.size()) ? totals[i] : 0;
         batch[i]->t_done = now;
-        if (status == BFC_OK) sv->stats.completed += 1; else sv->stats.failed += 1;
+        if (st == BFC_OK) sv->stats.completed += 1; else sv->stats.failed += 1;
     }
     sv->cv_done.notify_all();
 }
@@ -103,13 +121,19 @@ void complete(bfc_server *sv, std::vector<Request *> &batch, int status, const u
 int run_batch(bfc_server *sv, std::vector<Request *> &batch, cudaStream_t s,
               std::vector<uint64_t> &totals) {
     const int32_t G = (int32_t)batch.size();
-    std::vector<int32_t> us(G + 1, 0), ls(G + 1, 0);
-    std::vector<int64_t> es(G + 1, 0);
+    std::vector<int64_t> us64(G + 1, 0), ls64(G + 1, 0), es(G + 1, 0);
     for (int32_t g = 0; g < G; ++g) {
-        us[g + 1] = us[g] + batch[g]->r;
-        ls[g + 1] = ls[g] + batch[g]->l;
+        us64[g + 1] = us64[g] + batch[g]->r;
+        ls64[g + 1] = ls64[g] + batch[g]->l;
         es[g + 1] = es[g] + batch[g]->m;
     }
+    // admission keeps a batch inside int32 ids and slots (kUnionMax)
+    if (us64[G] + ls64[G] > kUnionMax || es[G] > kUnionMax) {
+        set_last_error("batch exceeds the int32 range of a union");
+        return BFC_ERR_INTERNAL;
+    }
+    std::vector<int32_t> us(G + 1), ls(G + 1);
+    for (int32_t g = 0; g <= G; ++g) { us[g] = (int32_t)us64[g]; ls[g] = (int32_t)ls64[g]; }
     Allocs in;
     in.stream = s;
     struct Guard { Allocs *a; ~Guard() { a->release(); } } guard{&in};
@@ -161,11 +185,28 @@ int run_batch(bfc_server *sv, std::vector<Request *> &batch, cudaStream_t s,
     return rc;
 }
 
-void worker_main(bfc_server *sv) {
+// A batch that failed as a whole because one graph broke the contract (a
+// duplicate edge, found by prepare's validation) is counted again graph by
+// graph, so that only the offending request fails.
+int run_batch_or_each(bfc_server *sv, std::vector<Request *> &batch, cudaStream_t s,
+                      std::vector<uint64_t> &totals, std::vector<int> &status) {
+    int rc = run_batch(sv, batch, s, totals);
+    status.assign(batch.size(), rc);
+    if (rc != BFC_ERR_INVALID_GRAPH || batch.size() < 2) return rc;
+    totals.assign(batch.size(), 0);
+    std::vector<uint64_t> one;
+    for (size_t i = 0; i < batch.size(); ++i) {
+        std::vector<Request *> single{batch[i]};
+        status[i] = run_batch(sv, single, s, one);
+        if (status[i] == BFC_OK) totals[i] = one[0];
+    }
+    return BFC_OK;
+}
+
+void worker_main(bfc_server *sv, cudaStream_t s) {
     cudaSetDevice(sv->device);
-    cudaStream_t s;
-    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return;
     std::vector<uint64_t> totals;
+    std::vector<int> status;
     for (;;) {
         std::vector<Request *> batch;
         int64_t bytes = 0;
@@ -181,30 +222,33 @@ void worker_main(bfc_server *sv) {
             }
             if (sv->stop && sv->waiting.empty()) break;
             if (sv->stop && sv->bytes_in_use + sv->waiting.front()->bytes > sv->cfg.memory_budget_bytes) break;
-            int64_t edges = 0;
+            int64_t edges = 0, verts = 0;
             while (!sv->waiting.empty() && (int32_t)batch.size() < sv->cfg.max_batch_graphs) {
                 Request *q = sv->waiting.front();
                 if (sv->bytes_in_use + bytes + q->bytes > sv->cfg.memory_budget_bytes) break;
                 if (!batch.empty() && edges + q->m > sv->cfg.max_batch_edges) break;
+                // the union's ids and CSR offsets stay in int32 (each request alone does)
+                if (!batch.empty() && (verts + q->r + q->l > kUnionMax || edges + q->m > kUnionMax))
+                    break;
                 sv->waiting.pop_front();
                 batch.push_back(q);
                 bytes += q->bytes;
                 edges += q->m;
+                verts += q->r + q->l;
             }
             sv->bytes_in_use += bytes;
             if (sv->bytes_in_use > sv->stats.peak_bytes_in_use) sv->stats.peak_bytes_in_use = sv->bytes_in_use;
             sv->stats.batches += 1;
             if ((int64_t)batch.size() > sv->stats.max_batch_graphs) sv->stats.max_batch_graphs = (int64_t)batch.size();
         }
-        int rc = run_batch(sv, batch, s, totals);
+        run_batch_or_each(sv, batch, s, totals, status);
         {
             std::lock_guard<std::mutex> lk(sv->mu);
             sv->bytes_in_use -= bytes;
         }
         sv->cv_work.notify_all();
-        complete(sv, batch, rc, rc == BFC_OK ? totals.data() : nullptr);
+        complete(sv, batch, status, totals);
     }
-    cudaStreamDestroy(s);
 }
 
 }  // namespace
@@ -228,7 +272,7 @@ int bfc_server_create(const bfc_server_config *cfg, bfc_server **out) {
     bfc_server_config c;
     if (cfg) c = *cfg; else bfc_server_config_init(&c);
     if (c.workers < 1 || c.workers > 16 || c.max_batch_graphs < 1 || c.memory_budget_bytes <= 0 ||
-        c.max_batch_edges < 1) {
+        c.max_batch_edges < 1 || c.max_batch_edges > bfc::kUnionMax) {
         bfc::set_last_error("invalid server configuration");
         return BFC_ERR_INVALID_ARGUMENT;
     }
@@ -239,7 +283,29 @@ int bfc_server_create(const bfc_server_config *cfg, bfc_server **out) {
     if (e != cudaSuccess) { delete sv; return bfc::cuda_fail(e, "cudaGetDevice"); }
     int rc = bfc::count_smem_setup(sv->device);   // before any worker launches
     if (rc) { delete sv; return rc; }
-    for (int i = 0; i < c.workers; ++i) sv->workers.emplace_back(bfc::worker_main, sv);
+    // every worker's stream exists before any worker starts: a server that
+    // could not start all its workers is not created, so no request can wait
+    // for a worker that is not there
+    for (int i = 0; i < c.workers; ++i) {
+        cudaStream_t st = nullptr;
+        e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            for (cudaStream_t x : sv->streams) cudaStreamDestroy(x);
+            delete sv;
+            return bfc::cuda_fail(e, "cudaStreamCreateWithFlags");
+        }
+        sv->streams.push_back(st);
+    }
+    // the pool's real high-water mark is tracked from here (stats)
+    int64_t cur = 0;
+    e = bfc::pool_usage(&cur, nullptr, true);
+    if (e != cudaSuccess) {
+        for (cudaStream_t x : sv->streams) cudaStreamDestroy(x);
+        delete sv;
+        return bfc::cuda_fail(e, "cudaMemPoolSetAttribute(UsedMemHigh)");
+    }
+    sv->stats.pool_bytes_at_create = cur;
+    for (int i = 0; i < c.workers; ++i) sv->workers.emplace_back(bfc::worker_main, sv, sv->streams[i]);
     *out = sv;
     return BFC_OK;
 }
@@ -250,6 +316,14 @@ int bfc_server_submit(bfc_server *sv, int32_t num_u, int32_t num_l, int64_t num_
     if (!sv || !off_u_host || (num_edges > 0 && !adj_u_host) || !request_id || num_u < 0 ||
         num_l < 0 || num_edges < 0 || num_edges > 2147483647LL) {
         bfc::set_last_error("invalid request");
+        return BFC_ERR_INVALID_ARGUMENT;
+    }
+    if (!bfc::host_csr_ok(num_u, num_l, num_edges, off_u_host, adj_u_host)) {
+        bfc::set_last_error("request is not a CSR of num_edges entries with ids in [0, num_l)");
+        return BFC_ERR_INVALID_GRAPH;
+    }
+    if ((int64_t)num_u + num_l > bfc::kUnionMax) {
+        bfc::set_last_error("request too large for int32 vertex ids");
         return BFC_ERR_INVALID_ARGUMENT;
     }
     bfc::Request *q = new (std::nothrow) bfc::Request();
@@ -293,10 +367,14 @@ int bfc_server_poll(bfc_server *sv, uint64_t request_id, int wait, uint64_t *tot
 
 int bfc_server_get_stats(bfc_server *sv, bfc_server_stats *out) {
     if (!sv || !out) { bfc::set_last_error("null argument"); return BFC_ERR_INVALID_ARGUMENT; }
+    int64_t cur = 0, high = 0;
+    cudaError_t e = bfc::pool_usage(&cur, &high, false);
+    if (e != cudaSuccess) return bfc::cuda_fail(e, "cudaMemPoolGetAttribute");
     std::lock_guard<std::mutex> lk(sv->mu);
     *out = sv->stats;
     out->bytes_in_use = sv->bytes_in_use;
     out->waiting = (int64_t)sv->waiting.size();
+    out->pool_bytes_high = high;
     return BFC_OK;
 }
 
@@ -308,6 +386,7 @@ void bfc_server_destroy(bfc_server *sv) {
     }
     sv->cv_work.notify_all();
     for (auto &t : sv->workers) t.join();
+    for (cudaStream_t x : sv->streams) cudaStreamDestroy(x);
     {
         // requests never admitted are cancelled
         std::lock_guard<std::mutex> lk(sv->mu);

@@ -14,11 +14,12 @@ from bfc_inputs import generators as G
 
 
 def test_algorithmic_bytes_formula():
-    # 4 B per wedge, 12 B per oriented edge and per start; all outputs add
-    # 8 B per wedge, per edge and per vertex
+    # 4 B per wedge, 12 B per oriented edge and per start; all outputs read
+    # the same again in the second walk, write and read 2m slot sums of 8 B,
+    # read 2m edge ids of 4 B and write 8 B per edge and per vertex
     W, m, n = 3_286_555_729, 20_000_000, 1_500_000
     assert bench.algorithmic_bytes(W, m, n) == 13_404_222_916
-    assert bench.algorithmic_bytes(W, m, n, "all") == 13_404_222_916 + 8 * (W + m + n)
+    assert bench.algorithmic_bytes(W, m, n, "all") == 2 * 13_404_222_916 + 48 * m + 8 * n
     assert bench.algorithmic_bytes(0, 0, 0) == 0
 
 

@@ -2,13 +2,17 @@
 times (default options, Algorithm 2, one CTA per SM).
 
 * The 20M-edge power-law graph: every output against the full oracle.
-* The 300M-edge shopping graph (10M users, 100k items): the oracle cannot run
-  there in test time, so the check is (a) identities that hold at any size
-  (Σ per-vertex over each layer = 2⋈, Σ per-edge = 4⋈, the combined pass
-  equals the total-only pass, Algorithm 3 gives the same ⋈ and W by Lemma 4)
-  and (b) sampled vertices and edges, including the heaviest of each kind,
-  that the oracle computes one by one from Eq. 1 and Eq. 7.
+* The 300M-edge shopping graph (10M users, 100k items): every output
+  (⋈_G, W, per-vertex of both layers, per-edge) against the full oracle run
+  on the host cores, which works while the GPU counts.  Two checks that do
+  not go through the oracle's Algorithm 2 stand beside it: identities that
+  hold at any size (Σ per-vertex over each layer = 2⋈, Σ per-edge = 4⋈,
+  Algorithm 3 gives the same ⋈ and W by Lemma 4) and sampled vertices and
+  edges, including the heaviest of each kind, computed one by one from
+  Eq. 1 and Eq. 7.
 """
+import threading
+
 import numpy as np
 import pytest
 
@@ -47,30 +51,53 @@ def _sample(rng, n, k, must):
     return np.array(sorted(pick), dtype=np.int64)
 
 
-def test_shopping_300m_identities_and_samples():
+def test_shopping_300m_all_outputs_against_oracle():
     from paper_1812_00283_gb300 import ButterflyGraph, bfc
     g = G.shopping_300m(device="cuda")
-    off = torch.from_numpy(g.off_u).cuda()
-    adj = torch.from_numpy(g.adj_u).cuda()
-    bg = ButterflyGraph(off, adj, g.num_u, g.num_l)
+    # the oracle (Algorithm 2 with the two-walk attribution, all host cores)
+    # runs in a thread while the GPU counts; ctypes releases the GIL
+    ref, failure = {}, []
+
+    def run_oracle():
+        try:
+            ref.update(oracle.vp(g, vertices=True, edges=True))
+        except Exception as e:   # re-raised in the test thread
+            failure.append(e)
+    th = threading.Thread(target=run_oracle)
+    th.start()
     try:
-        tot = bg.count()
-        W = bg.info()["wedges"]
-        pu, pl, pe, t_all = bg.count_all()
-        pu, pl, pe = as_u64(pu), as_u64(pl), as_u64(pe)
+        off = torch.from_numpy(g.off_u).cuda()
+        adj = torch.from_numpy(g.adj_u).cuda()
+        bg = ButterflyGraph(off, adj, g.num_u, g.num_l)
+        try:
+            tot = bg.count()
+            W = bg.info()["wedges"]
+            pu, pl, pe, t_all = bg.count_all()
+            pu, pl, pe = as_u64(pu), as_u64(pl), as_u64(pe)
+            pe2, t_e = bg.count_edges()
+            pe2 = as_u64(pe2)
+        finally:
+            bg.release()
+        del off, adj
+        torch.cuda.empty_cache()
+        # Lemma 4: Algorithm 3 processes the same wedges and finds the same total
+        alt = run_gpu(g, options=bfc.bfc_options_init(orientation=1))
+        torch.cuda.empty_cache()
     finally:
-        bg.release()
-    del off, adj
-    torch.cuda.empty_cache()
-    assert tot > 0 and t_all == tot
-    # uint64 sums wrap like the counts themselves; the totals stay far below 2^64
+        th.join()
+    if failure:
+        raise failure[0]
+    assert tot > 0 and t_all == tot and t_e == tot
+    assert alt["total"] == tot and alt["info"]["wedges"] == W
+    # element by element against the oracle
+    assert tot == ref["total"] and W == ref["wedges"]
+    assert np.array_equal(pu, ref["pv_u"]) and np.array_equal(pl, ref["pv_l"])
+    assert np.array_equal(pe, ref["pe"]) and np.array_equal(pe2, ref["pe"])
+    # identities (uint64 sums wrap like the counts; the totals stay far below 2^64)
     assert int(pu.sum(dtype=np.uint64)) == 2 * tot
     assert int(pl.sum(dtype=np.uint64)) == 2 * tot
     assert int(pe.sum(dtype=np.uint64)) == 4 * tot
-    # Lemma 4: Algorithm 3 processes the same wedges and finds the same total
-    alt = run_gpu(g, options=bfc.bfc_options_init(orientation=1))
-    assert alt["total"] == tot and alt["info"]["wedges"] == W
-    # sampled outputs, one by one from the definitions
+    # sampled outputs, one by one from the definitions (Eq. 1, Eq. 7)
     deg_u = np.diff(g.off_u.astype(np.int64))
     deg_l = np.bincount(g.adj_u, minlength=g.num_l)
     rng = np.random.default_rng(7)

@@ -73,7 +73,8 @@ def test_server_results_equal_alone_results():
     graphs = _pool()
     alone = [_alone(g) for g in graphs]
     assert alone[:4] == [15 * 36, 0, 999_000, 1]
-    assert alone[10] == oracle.vp(graphs[10])["total"]
+    # every graph counted alone on the GPU equals the oracle's count
+    assert alone == [oracle.vp(g)["total"] for g in graphs]
     rng = random.Random(3)
     order = [rng.randrange(len(graphs)) for _ in range(300)]
     delays = [rng.expovariate(20000.0) for _ in order]     # ~50 us apart: requests overlap
@@ -86,6 +87,9 @@ def test_server_results_equal_alone_results():
         assert [tot for _, tot, _ in res] == [alone[gi] for gi in order]
         assert stats["submitted"] == stats["completed"] == len(order) and stats["failed"] == 0
         assert stats["peak_bytes_in_use"] <= cfg.memory_budget_bytes
+        # the admission estimate bounds the memory the batches really took
+        # from the library's pool (its measured high-water mark)
+        assert stats["pool_bytes_high"] <= stats["pool_bytes_at_create"] + stats["peak_bytes_in_use"]
         if cfg.max_batch_graphs == 1:
             assert stats["batches"] == len(order)
 
@@ -101,3 +105,47 @@ def test_server_rejects_request_over_budget():
         assert ei.value.status == 3
     finally:
         bfc.bfc_server_destroy(sv)
+
+
+def test_server_bad_request_fails_alone():
+    """A malformed request fails on its own; the requests batched with it
+    get the oracle's counts."""
+    from paper_1812_00283_gb300 import BfcError, bfc
+    graphs = [G.chung_lu_bipartite(40000, 20000, 400000, 2.1, 2.1, 17)] + _pool(k=16, seed=9)
+    expect = [oracle.vp(g)["total"] for g in graphs]
+    arrays = [(np.ascontiguousarray(g.off_u), np.ascontiguousarray(g.adj_u if g.num_edges else
+                                                                  np.zeros(1, np.int32)))
+              for g in graphs]
+    sv = bfc.bfc_server_create(bfc.bfc_server_config_init(workers=1))
+    try:
+        # not a CSR, and an id out of range: refused at submission
+        for off, adj in [(np.array([0, 3, 2], np.int32), np.array([0, 1, 0], np.int32)),
+                         (np.array([0, 1, 3], np.int32), np.array([0, 1, 5], np.int32))]:
+            with pytest.raises(BfcError) as ei:
+                bfc.bfc_server_submit(sv, 2, 2, 3, off.ctypes.data, adj.ctypes.data)
+            assert ei.value.status == 2
+        # a duplicate edge is found on the device while the large first graph
+        # keeps the worker busy, so it meets the others in one batch
+        dup_off, dup_adj = np.array([0, 2, 3], np.int32), np.array([1, 1, 0], np.int32)
+        ids = []
+        for i, (g, (off, adj)) in enumerate(zip(graphs, arrays)):
+            ids.append(bfc.bfc_server_submit(sv, g.num_u, g.num_l, g.num_edges, off.ctypes.data,
+                                             adj.ctypes.data))
+            if i == 5:
+                dup_id = bfc.bfc_server_submit(sv, 2, 2, 3, dup_off.ctypes.data, dup_adj.ctypes.data)
+        res = [bfc.bfc_server_poll(sv, rid, True) for rid in ids]
+        dup = bfc.bfc_server_poll(sv, dup_id, True)
+        stats = bfc.bfc_server_get_stats(sv)
+    finally:
+        bfc.bfc_server_destroy(sv)
+    assert dup[0] == 2
+    assert [st for st, _, _ in res] == [0] * len(graphs)
+    assert [tot for _, tot, _ in res] == expect
+    assert stats["failed"] == 1 and stats["completed"] == len(graphs)
+
+
+def test_server_rejects_batch_limit_beyond_int32_offsets():
+    from paper_1812_00283_gb300 import BfcError, bfc
+    with pytest.raises(BfcError) as ei:
+        bfc.bfc_server_create(bfc.bfc_server_config_init(max_batch_edges=1 << 31))
+    assert ei.value.status == 1

@@ -480,6 +480,36 @@ def test_identities(gi):
     assert np.array_equal(oracle.brute_edges(g), r["pe"])
 
 
+@pytest.mark.parametrize("a,b", [(1, 1), (1, 6), (3, 7), (6, 4), (5, 5)])
+def test_degree_stats_closed_forms_complete_bipartite(a, b):
+    # K_{a,b}: every U vertex has degree b, every L vertex degree a, so each of
+    # the a·b edges has min(deg) = min(a, b); Σ_U deg² = a·b², Σ_L deg² = b·a²
+    tc, du2, dl2 = oracle.degree_stats(G.complete_bipartite(a, b))
+    assert tc == a * b * min(a, b)
+    assert du2 == a * b * b and dl2 == b * a * a
+
+
+def test_degree_stats_closed_forms_sparse_shapes():
+    # star with k leaves, centre in U: every edge has min(deg) = 1
+    k = 9
+    assert oracle.degree_stats(G.star(k)) == (k, k * k, k)
+    assert oracle.degree_stats(G.star(k, center_in_u=False)) == (k, k, k * k)
+    # C_{2k}: every vertex has degree 2
+    for k in (2, 3, 8):
+        assert oracle.degree_stats(G.cycle(k)) == (4 * k, 4 * k, 4 * k)
+    # path with e >= 2 edges: the two end edges have min(deg) = 1, the rest 2;
+    # U holds the even path positions (degrees 1, 2, ..., ending in 1 or 2)
+    for e in (2, 5, 8):
+        tc, du2, dl2 = oracle.degree_stats(G.path(e))
+        assert tc == 2 + 2 * (e - 2)
+        degs = [1] + [2] * (e - 1) + [1]     # degree of path position 0..e
+        assert du2 == sum(d * d for d in degs[0::2]) and dl2 == sum(d * d for d in degs[1::2])
+    # disjoint unions add
+    a, b = G.complete_bipartite(3, 7), G.cycle(4)
+    sa, sb = oracle.degree_stats(a), oracle.degree_stats(b)
+    assert oracle.degree_stats(G.disjoint_union(a, b)) == tuple(x + y for x, y in zip(sa, sb))
+
+
 @pytest.mark.parametrize("gi", range(5))
 def test_relabel_and_list_order_invariance(gi):
     g = _graphs()[gi]

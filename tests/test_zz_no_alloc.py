@@ -1,8 +1,9 @@
 """bfc_count_small_noalloc: the allocation-free entry point for callers that
-may not allocate device memory where they count (stream capture, fixed
-up-front memory budgets).  Its result must equal the regular entry point's
-(bfc_prepare + bfc_count) bit for bit, on consecutive calls that share the
-library's fixed scratch array.
+may not allocate device memory where they count (their device memory is
+reserved up front by their own allocator, or they run in a loop that must
+not enter the driver's allocator).  Its result must equal the regular entry
+point's (bfc_prepare + bfc_count) and the oracle's bit for bit, on
+consecutive calls that share the library's fixed scratch array.
 
 This file is collected last on purpose: a failure here leaves every other
 test already run.
@@ -12,6 +13,7 @@ import ctypes
 import numpy as np
 import pytest
 
+import oracle
 from bfc_inputs import generators as G
 
 torch = pytest.importorskip("torch")
@@ -48,6 +50,7 @@ def test_no_alloc_matches_regular_entry_point():
         bg = ButterflyGraph(off, adj[:g.num_edges], g.num_u, g.num_l)
         expect = bg.count()
         bg.release()
+        assert expect == oracle.vp(g)["total"], g.name
         for _ in range(2):   # two calls in a row on the shared scratch
             total.fill_(-1)
             status.fill_(-1)
