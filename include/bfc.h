@@ -110,16 +110,24 @@ typedef struct bfc_options {
                                Algorithm 2 caps it at hash_max_work; above 3072
                                a start whose team table fills up goes to the
                                retry pass. */
-    int32_t core_vertices;  /* Algorithm 2 total counts (bfc_count) only: the
-                               K vertices of highest priority (Definition 3)
-                               form a core whose pairs are counted by a masked
-                               0/1 matrix product on the tensor cores (the
-                               walk skips every wedge with start, middle and
-                               end in the core and adds a·b + C(a, 2) per core
-                               pair, Lemma 1).  0 (default) = off; at most
-                               65,535 core vertices per layer.  Per-vertex and
+    int32_t core_vertices;  /* Algorithm 2 total counts (bfc_count) of single
+                               graphs only: the K vertices of highest priority
+                               (Definition 3) form a core whose pairs are
+                               counted by a masked 0/1 matrix product on the
+                               tensor cores (the walk of every core start skips
+                               the wedges with middle and end in the core too
+                               and adds a·b + C(a, 2) per core pair, Lemma 1;
+                               core starts are always counted with dense
+                               counters).  -1 (default) = automatic: K = the
+                               number of starts with more than hash_max_work
+                               wedges, at most 8,192, and no core unless each
+                               layer holds at least 1,024 of its vertices;
+                               0 = off; K > 0: that many (at most 65,535 core
+                               vertices per layer, else
+                               BFC_ERR_INVALID_ARGUMENT).  Per-vertex and
                                per-edge counts of the same graph walk every
-                               wedge as usual. */
+                               wedge as usual.  Costs 8·K_U·K_L bytes of bf16
+                               operands and 2·(K_U² + K_L²) bytes of products. */
     int32_t reserved[8];    /* must be zero */
 } bfc_options;
 

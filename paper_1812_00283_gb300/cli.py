@@ -41,7 +41,7 @@ def main(argv=None):
     ap.add_argument("--hash-max-work", type=int, default=None)
     ap.add_argument("--team-max-work", type=int, default=None)
     ap.add_argument("--orientation", type=int, default=0, choices=[0, 1])
-    ap.add_argument("--core-vertices", type=int, default=0,
+    ap.add_argument("--core-vertices", type=int, default=-1,
                     help="top-K priority core counted by the tensor-core product (total counts)")
     args = ap.parse_args(argv)
 

@@ -123,8 +123,8 @@ static int check_options(const bfc_options *o) {
         bfc::set_last_error("orientation must be 0 (Algorithm 2) or 1 (Algorithm 3)");
         return BFC_ERR_INVALID_ARGUMENT;
     }
-    if (o->core_vertices < 0) {
-        bfc::set_last_error("core_vertices must be >= 0");
+    if (o->core_vertices < -1) {
+        bfc::set_last_error("core_vertices must be -1 (automatic), 0 (off) or a core size");
         return BFC_ERR_INVALID_ARGUMENT;
     }
     for (int i = 0; i < 8; ++i)
@@ -145,6 +145,7 @@ void bfc_options_init(bfc_options *opt) {
     opt->hash_max_work = bfc::kHashMaxWork;
     opt->team_max_work = -1;
     opt->num_ctas = 0;
+    opt->core_vertices = -1;
 }
 
 int bfc_prepare(const bfc_csr *csr, const bfc_options *opt_in, void *stream, bfc_graph **out) {

@@ -223,7 +223,12 @@ int rebin_graph(Graph *g, cudaStream_t s, int32_t warp_max_work, int32_t team_ma
 int count_smem_setup(int device);
 // the dense-core hybrid (core.cu): core choice and matrices in prepare, the
 // masked products before a total count
-int core_prepare(Graph *g, cudaStream_t s, const int32_t *deg_star);
+int core_prepare(Graph *g, cudaStream_t s, const int32_t *deg_star, int32_t core_vertices,
+                 bool automatic);
+// the automatic core size is at most this many vertices (the product grows as
+// K^3), and is used only when each layer holds at least kCoreAutoMinLayer
+constexpr int32_t kCoreAutoMax = 8192;
+constexpr int32_t kCoreAutoMinLayer = 1024;
 int core_product(Graph *g, cudaStream_t s);
 
 // small helpers

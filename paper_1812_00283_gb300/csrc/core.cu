@@ -104,11 +104,13 @@ __global__ void k_core_ccut(const int64_t *__restrict__ off, const int32_t *__re
 
 // Rows of B and Bm for one layer's core, one warp per core vertex x: its core
 // neighbours are list positions [ccut[x], deg); those below cut[x] have lower
-// priority than x.  The matrices are zeroed before.
+// priority than x.  The matrices are zeroed before.  Each row also raises its
+// row tile's contraction limit (in 64-column blocks, zeroed before) to cover
+// its last lower-priority core neighbour, at list position cut[x] - 1.
 __global__ void k_core_rows(const int64_t *__restrict__ off, const int32_t *__restrict__ adj,
                             const int32_t *__restrict__ cut, const int32_t *__restrict__ ccut,
                             int32_t row_lo, int32_t rows, int32_t col_lo, int32_t ld,
-                            uint16_t *bmat, uint16_t *bmask) {
+                            uint16_t *bmat, uint16_t *bmask, int32_t *kb) {
     const int lane = threadIdx.x & 31;
     const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -116,36 +118,15 @@ __global__ void k_core_rows(const int64_t *__restrict__ off, const int32_t *__re
     for (int64_t i = w0; i < rows; i += nw) {
         const int32_t x = row_lo + (int32_t)i;
         const int64_t b = off[x], d = off[x + 1] - b;
-        const int32_t c = cut[x];
-        for (int64_t k = ccut[x] + lane; k < d; k += 32) {
+        const int32_t c = cut[x], cc = ccut[x];
+        for (int64_t k = cc + lane; k < d; k += 32) {
             const int32_t col = adj[b + k] - col_lo;
             bmat[i * ld + col] = one;
             if (k < c) bmask[i * ld + col] = one;
         }
+        if (lane == 0 && c > cc)
+            atomicMax(kb + i / kTile, (adj[b + c - 1] - col_lo + kKBlock) / kKBlock);
     }
-}
-
-// The contraction limit of every row tile of Bm, in 64-column blocks: the
-// last valid row of the tile has the most core neighbours below it in
-// priority (cL grows with priority), and its last one is at list position
-// cut - 1.
-__global__ void k_core_kblocks(const int64_t *__restrict__ off, const int32_t *__restrict__ adj,
-                               const int32_t *__restrict__ cut, const int32_t *__restrict__ ccut,
-                               int32_t row_lo, int32_t rows, int32_t col_lo, int32_t tiles,
-                               int32_t *kb) {
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= tiles) return;
-    const int64_t end = (t + 1) * kTile < rows ? (t + 1) * kTile : rows;
-    const int32_t last = (int32_t)end - 1;
-    int32_t cols = 0;
-    // any row of the tile could reach further than the last one only if cL
-    // decreased, which it cannot; scan the tile's rows anyway (cheap, exact)
-    for (int32_t i = (int32_t)(t * kTile); i <= last; ++i) {
-        const int32_t x = row_lo + i;
-        const int32_t c = cut[x];
-        if (c > ccut[x]) cols = max(cols, adj[off[x] + c - 1] - col_lo + 1);
-    }
-    kb[t] = (int32_t)((cols + kKBlock - 1) / kKBlock);
 }
 
 // ---------------------------------------------------------------------------
@@ -440,8 +421,8 @@ CUtensorMap *map_of(Graph *g, int i) {
 // Chooses the core (top core_vertices of Definition 3's order, split between
 // the layers), builds B and Bm of both layers' cores and the tile limits.
 // Called by prepare while the G* degrees are still at hand; synchronises s.
-int core_prepare(Graph *g, cudaStream_t s, const int32_t *deg_star) {
-    const int32_t k = std::min<int32_t>(g->opt.core_vertices, g->n);
+int core_prepare(Graph *g, cudaStream_t s, const int32_t *deg_star, int32_t core_vertices, bool automatic) {
+    const int32_t k = std::min<int32_t>(core_vertices, g->n);
     if (k <= 0 || g->m == 0) return BFC_OK;
     int32_t *split = nullptr;
     Allocs tmp;
@@ -455,6 +436,9 @@ int core_prepare(Graph *g, cudaStream_t s, const int32_t *deg_star) {
     BFC_CUDA(cudaMemcpyAsync(h, split, sizeof(h), cudaMemcpyDeviceToHost, s));
     BFC_CUDA(cudaStreamSynchronize(s));
     const int32_t ku = h[0], kl = h[1];
+    // the automatic core needs both layers in it: with a thin side the core
+    // block holds few wedges and the product would be pure overhead
+    if (automatic && (ku < kCoreAutoMinLayer || kl < kCoreAutoMinLayer)) return BFC_OK;
     if (ku > 65535 || kl > 65535) {
         set_last_error("core_vertices too large: a layer's core holds at most 65,535 vertices");
         return BFC_ERR_INVALID_ARGUMENT;
@@ -481,29 +465,19 @@ int core_prepare(Graph *g, cudaStream_t s, const int32_t *deg_star) {
                                                         g->core_lo_l, g->ccut);
     note_launch();
     BFC_CUDA(cudaGetLastError());
+    BFC_CUDA(cudaMemsetAsync(g->core_kb_u, 0, sizeof(int32_t) * (size_t)(pu / kTile), s));
+    BFC_CUDA(cudaMemsetAsync(g->core_kb_l, 0, sizeof(int32_t) * (size_t)(pl / kTile), s));
     if (ku > 0) {
         k_core_rows<<<blocks((int64_t)ku * 32), kT, 0, s>>>(g->off, g->adj, g->cut, g->ccut, g->core_lo_u, ku,
-                                                             g->core_lo_l, (int32_t)pl, g->core_bu, g->core_bum);
+                                                             g->core_lo_l, (int32_t)pl, g->core_bu, g->core_bum,
+                                                             g->core_kb_u);
         note_launch();
         BFC_CUDA(cudaGetLastError());
     }
     if (kl > 0) {
         k_core_rows<<<blocks((int64_t)kl * 32), kT, 0, s>>>(g->off, g->adj, g->cut, g->ccut, g->core_lo_l, kl,
-                                                             g->core_lo_u, (int32_t)pu, g->core_bl, g->core_blm);
-        note_launch();
-        BFC_CUDA(cudaGetLastError());
-    }
-    BFC_CUDA(cudaMemsetAsync(g->core_kb_u, 0, sizeof(int32_t) * (size_t)(pu / kTile), s));
-    BFC_CUDA(cudaMemsetAsync(g->core_kb_l, 0, sizeof(int32_t) * (size_t)(pl / kTile), s));
-    if (ku > 0) {
-        k_core_kblocks<<<blocks(pu / kTile), kT, 0, s>>>(g->off, g->adj, g->cut, g->ccut, g->core_lo_u, ku,
-                                                          g->core_lo_l, (int32_t)cdiv(ku, kTile), g->core_kb_u);
-        note_launch();
-        BFC_CUDA(cudaGetLastError());
-    }
-    if (kl > 0) {
-        k_core_kblocks<<<blocks(pl / kTile), kT, 0, s>>>(g->off, g->adj, g->cut, g->ccut, g->core_lo_l, kl,
-                                                          g->core_lo_u, (int32_t)cdiv(kl, kTile), g->core_kb_l);
+                                                             g->core_lo_u, (int32_t)pu, g->core_bl, g->core_blm,
+                                                             g->core_kb_l);
         note_launch();
         BFC_CUDA(cudaGetLastError());
     }

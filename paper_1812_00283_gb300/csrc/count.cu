@@ -769,7 +769,9 @@ __device__ unsigned long long dense_stream(const CountParams &p, int64_t &it, un
         const int flags = (lo > 0 ? 1 : 0) | (hi < R ? 2 : 0);
         const int64_t e0 = p.off[x];
         const int32_t nmid = p.cut[x];
-        // dense-core hybrid: x in its layer's core (uniform over the item)
+        // dense-core hybrid: x in its layer's core (uniform over the item).  Only
+        // dense items split: a core start in a hash bin walks all its wedges
+        // and its row of the product is not used.
         const int32_t clo_x = x >= p.l ? p.core_lo_u : p.core_lo_l;
         const bool core_x = p.core_on && x >= clo_x;
         const int32_t core_lo_v = core_x ? (x >= p.l ? p.core_lo_l : p.core_lo_u) : 0x7fffffff;

@@ -412,8 +412,8 @@ __global__ void k_work(const int64_t *__restrict__ off, const int32_t *__restric
 }
 
 // ----- a5: bins and schedule ---------------------------------------------------
-// a core start (dense-core hybrid) with wedges is always a dense item: the
-// count kernel adds its core pairs after the item's walk
+// A core start (dense-core hybrid) with wedges is always a dense item: only
+// dense items skip the core wedges and add the core pairs after the walk.
 __device__ __forceinline__ bool forced_dense(int32_t x, int32_t l, int32_t core_lo_u, int32_t core_lo_l,
                                              uint64_t w) {
     return w > 0 && (x >= l ? x >= core_lo_u : x >= core_lo_l);
@@ -427,6 +427,18 @@ __global__ void k_sched_keys(const uint64_t *__restrict__ work, int32_t n, uint6
     // ascending key = descending work; zero work last; forced dense starts first
     keys[x] = forced_dense((int32_t)x, l, core_lo_u, core_lo_l, work[x]) ? 0 : maxw - work[x];
     vals[x] = (int32_t)x;
+}
+
+// starts with more than `bound` wedges (the dense bin's size before any core)
+__global__ void k_count_heavy(const uint64_t *__restrict__ work, int32_t n, uint64_t bound,
+                              unsigned long long *count) {
+    unsigned long long c = 0;
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
+         x += (int64_t)gridDim.x * blockDim.x)
+        c += work[x] > bound ? 1 : 0;
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) c += __shfl_xor_sync(0xffffffffu, c, d);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, c);
 }
 
 // counts[0] = dense starts, [1] = hash starts, [2] = warp starts
@@ -1032,15 +1044,24 @@ int prepare_graph(const bfc_csr *csr, const bfc_options *opt, cudaStream_t s, Gr
         k_graph_work<<<grid_stride_blocks(n), kT, 0, s>>>(g->work, g->gstar, n, g->gwork); note_launch();
         BFC_CUDA(cudaGetLastError());
     }
-    unsigned long long hred[2] = {0, 0};
-    BFC_CUDA(cudaMemcpyAsync(hred, red, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    const bool core_auto = opt->core_vertices < 0 && opt->orientation == 0 && num_graphs == 0;
+    if (core_auto && n > 0) {
+        k_count_heavy<<<grid_stride_blocks(n), kT, 0, s>>>(g->work, n, (uint64_t)opt->hash_max_work, red + 2); note_launch();
+        BFC_CUDA(cudaGetLastError());
+    }
+    unsigned long long hred[3] = {0, 0, 0};
+    BFC_CUDA(cudaMemcpyAsync(hred, red, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
     BFC_CUDA(cudaStreamSynchronize(s));
     g->info.wedges = hred[0];
     g->info.max_start_work = hred[1];
 
-    // ---- dense-core hybrid (Algorithm 2 single graphs with core_vertices > 0)
-    if (opt->core_vertices > 0 && opt->orientation == 0 && num_graphs == 0) {
-        int rc = core_prepare(g, s, deg_star);
+    // ---- dense-core hybrid (Algorithm 2 single graphs): the requested core
+    // size, or (core_vertices = -1) as many vertices as starts heavier than
+    // the CTA-hash bin, at most kCoreAutoMax
+    if (opt->core_vertices != 0 && opt->orientation == 0 && num_graphs == 0) {
+        const int32_t k = core_auto ? (int32_t)std::min<unsigned long long>(hred[2], (unsigned long long)kCoreAutoMax)
+                                    : opt->core_vertices;
+        int rc = core_prepare(g, s, deg_star, k, core_auto);
         if (rc) return rc;
     }
     g->info.core_u = g->core_u;

@@ -138,9 +138,37 @@ def test_core_graph_keeps_other_outputs_and_repeats():
         bg.release()
 
 
+@pytest.mark.parametrize("gi", range(6))
+@pytest.mark.parametrize("hash_max", [None, 0])
+def test_core_automatic_size(gi, hash_max):
+    # -1 (the default): as many core vertices as starts heavier than the
+    # CTA-hash bin (at most 8,192), if each layer then holds 1,024 of them
+    from paper_1812_00283_gb300 import ButterflyGraph, bfc
+    g = _graphs()[gi]
+    opts = bfc.bfc_options_init() if hash_max is None else \
+        bfc.bfc_options_init(warp_max_work=0, hash_max_work=hash_max)
+    assert opts.core_vertices == -1
+    bg = ButterflyGraph(torch.from_numpy(g.off_u).cuda(), torch.from_numpy(g.adj_u).cuda(),
+                        g.num_u, g.num_l, opts)
+    try:
+        total, info, work = bg.count(), bg.info(), as_u64(bg.export(bfc.BFC_WORK))
+    finally:
+        bg.release()
+    assert total == oracle.vp(g)["total"]
+    K = min(int((work > opts.hash_max_work).sum()), 8192)
+    _, _, p = oracle.priority(g)
+    n, l = g.num_u + g.num_l, g.num_l
+    top = p > n - K
+    ku, kl = int(top[l:].sum()), int(top[:l].sum())
+    if ku >= 1024 and kl >= 1024:
+        assert (info["core_u"], info["core_l"]) == (ku, kl)
+    else:
+        assert (info["core_u"], info["core_l"]) == (0, 0)
+
+
 def test_core_powerlaw_20m_against_oracle():
     g = G.powerlaw_20m(device="cuda")
     ref = oracle.vp(g)["total"]
-    for K in (4096, 16384):
+    for K in (-1, 4096, 16384):
         got = _core_count(g, K, repeat=2, products=False)
         assert got["totals"] == [ref, ref]
