@@ -310,6 +310,23 @@ struct BatchSlots {
     int nzs[kPer];
 };
 
+// The per-middle sums of a second-walk batch: Σ δ over each middle's ends
+// goes to the middle (per-vertex) and to the edge (x, v) at its slot.
+template <int MODE, typename Pos, int kThreads, class SH>
+__device__ __forceinline__ void middle_sums(const CountParams &p, const BatchSlots<Pos, kThreads> &bs,
+                                            const SH &sh) {
+#pragma unroll
+    for (int i = 0; i < Batch<Pos, kThreads>::kPer; ++i) {
+        if (bs.len[i] > 0) {
+            const unsigned long long dsum = sh.msum[bs.nzs[i]];
+            if (dsum) {
+                if (wants_vertices(MODE)) atomicAdd(p.pv + bs.v[i], dsum);
+                if (wants_edges(MODE)) atomicAdd(p.pe + bs.e[i], dsum);
+            }
+        }
+    }
+}
+
 // Sets up one batch of the middles of x (those with index mb .. mb+kB-1):
 // the run of ends in range for each middle comes from the slot arrays (plus
 // the chunk-boundary table or a binary search for dense chunks); non-empty
@@ -563,18 +580,7 @@ __device__ unsigned long long team_walk(const CountParams &p, int32_t x, int32_t
         // finish their windows early already load the next batch's slots.
         if (KIND == kHash || kSecond) t.sync();
         if (KIND == kHash && !kSecond && sh.overflow) break;   // uniform: read after the barrier
-        if (kSecond) {
-#pragma unroll
-            for (int i = 0; i < kPer; ++i) {
-                if (bs.len[i] > 0) {
-                    const unsigned long long dsum = sh.msum[bs.nzs[i]];
-                    if (dsum) {
-                        if (wants_vertices(MODE)) atomicAdd(p.pv + bs.v[i], dsum);
-                        if (wants_edges(MODE)) atomicAdd(p.pe + bs.e[i], dsum);
-                    }
-                }
-            }
-        }
+        if (kSecond) middle_sums<MODE, Pos>(p, bs, sh);
     }
     return acc;
 }
@@ -582,10 +588,52 @@ __device__ unsigned long long team_walk(const CountParams &p, int32_t x, int32_t
 // First walk, then (per-vertex / per-edge) the end contributions and the
 // second walk.  Returns Σ C(count, 2) over the pairs of this item, or 0 with
 // sh.overflow set when a hash table filled up (nothing is attributed then).
+// The per-vertex end contributions of one item: each pair (x, w) of the
+// item adds C(count, 2) to ⋈_w.  Called after the first walk, with its
+// counters final.
+template <int MODE, int KIND, int kThreads>
+__device__ __forceinline__ void end_contributions(const CountParams &p, int32_t lb, int32_t lo,
+                                                  int32_t hi, uint32_t hmask, const unsigned char *ctr,
+                                                  const Team<kThreads> &t);
+
 template <int MODE, int KIND, typename Pos, int kThreads, class SH>
 __device__ unsigned long long item_body(const CountParams &p, int32_t x, int32_t lb, int32_t lo,
                                         int32_t hi, int flags, uint32_t hmask, unsigned char *ctr,
                                         SH &sh, const Team<kThreads> &t) {
+    constexpr int kB = Batch<Pos, kThreads>::kSize;
+    if (has_second_walk(MODE)) {
+        const int32_t nmid = p.orient ? (int32_t)(p.off[x + 1] - p.off[x]) : p.cut[x];
+        if (nmid <= kB) {
+            // One batch of middles: the second walk reuses the first walk's
+            // compacted runs (shared arrays and each thread's slots), so the
+            // slot loads and the scan happen once.
+            BatchSlots<Pos, kThreads> bs;
+            int32_t total;
+            int nnz;
+            batch_runs<KIND != kHash, false, Pos>(p, p.off[x], nmid, 0, lb, lo, hi, flags, ctr, 0, sh, t, bs,
+                                                  &total, &nnz);
+            t.sync();
+            int *const ins = (KIND == kHash && sh.track) ? &sh.inserts : nullptr;
+            const int32_t span = hi - lo;
+            const unsigned long long acc =
+                batch_windows<MODE, KIND, false, Pos>(p, lb, lo, span, hmask, ctr, total, nnz, ins, sh, t);
+            t.sync();   // counters final
+            if (KIND == kHash && sh.overflow) return 0;   // the caller re-queues x
+            if (wants_vertices(MODE)) end_contributions<MODE, KIND>(p, lb, lo, hi, hmask, ctr, t);
+#pragma unroll
+            for (int i = 0; i < Batch<Pos, kThreads>::kPer; ++i)
+                if (bs.len[i] > 0) sh.msum[bs.nzs[i]] = 0;
+            t.sync();
+            batch_windows<MODE, KIND, true, Pos>(p, lb, lo, span, hmask, ctr, total, nnz, nullptr, sh, t);
+            t.sync();
+            middle_sums<MODE, Pos>(p, bs, sh);
+            if (wants_vertices(MODE)) {
+                const unsigned long long s = team_sum(acc, sh, t);
+                if (t.tid == 0 && s) atomicAdd(p.pv + x, s);
+            }
+            return acc;
+        }
+    }
     unsigned long long acc = team_walk<MODE, KIND, false, Pos>(p, x, lb, lo, hi, flags, hmask, ctr, sh, t);
     if (KIND == kHash) {
         t.sync();
@@ -593,26 +641,7 @@ __device__ unsigned long long item_body(const CountParams &p, int32_t x, int32_t
     }
     if (has_second_walk(MODE)) {
         t.sync();
-        if (wants_vertices(MODE)) {
-            // ends: each pair (x, w) adds C(count, 2) to ⋈_w
-            if (KIND == kHash) {
-                const int32_t *hkeys = reinterpret_cast<const int32_t *>(ctr);
-                const uint32_t *hcnt = reinterpret_cast<const uint32_t *>(ctr + (size_t)(hmask + 1) * 4);
-                for (uint32_t s = t.tid; s <= hmask; s += kThreads) {
-                    const int32_t k = hkeys[s];
-                    if (k >= 0) {
-                        const unsigned long long b = c2(get16(hcnt, (int)s));
-                        if (b) atomicAdd(p.pv + lb + k, b);
-                    }
-                }
-            } else {
-                const uint32_t *w32 = reinterpret_cast<const uint32_t *>(ctr);
-                for (int32_t i = t.tid; i < hi - lo; i += kThreads) {
-                    const uint32_t c = (KIND == kDenseWide) ? w32[i] : get16(w32, i);
-                    if (c >= 2) atomicAdd(p.pv + lb + lo + i, c2(c));
-                }
-            }
-        }
+        if (wants_vertices(MODE)) end_contributions<MODE, KIND>(p, lb, lo, hi, hmask, ctr, t);
         team_walk<MODE, KIND, true, Pos>(p, x, lb, lo, hi, flags, hmask, ctr, sh, t);
         if (wants_vertices(MODE)) {
             const unsigned long long s = team_sum(acc, sh, t);
@@ -620,6 +649,49 @@ __device__ unsigned long long item_body(const CountParams &p, int32_t x, int32_t
         }
     }
     return acc;
+}
+
+template <int MODE, int KIND, int kThreads>
+__device__ __forceinline__ void end_contributions(const CountParams &p, int32_t lb, int32_t lo,
+                                                  int32_t hi, uint32_t hmask, const unsigned char *ctr,
+                                                  const Team<kThreads> &t) {
+    if (KIND == kHash) {
+        const int32_t *hkeys = reinterpret_cast<const int32_t *>(ctr);
+        const uint32_t *hcnt = reinterpret_cast<const uint32_t *>(ctr + (size_t)(hmask + 1) * 4);
+        for (uint32_t s = t.tid; s <= hmask; s += kThreads) {
+            const int32_t k = hkeys[s];
+            if (k >= 0) {
+                const unsigned long long b = c2(get16(hcnt, (int)s));
+                if (b) atomicAdd(p.pv + lb + k, b);
+            }
+        }
+    } else {
+        // 16 bytes per thread and step (8 narrow or 4 wide counters);
+        // a word whose counts are all below 2 adds nothing.  The
+        // clear before the walk covered whole 16-byte words.
+        const uint4 *q4 = reinterpret_cast<const uint4 *>(ctr);
+        constexpr int kPerQ = (KIND == kDenseWide) ? 4 : 8;
+        constexpr uint32_t kAtLeast2 = (KIND == kDenseWide) ? 0xFFFFFFFEu : 0xFFFEFFFEu;
+        const int32_t span = hi - lo;
+        unsigned long long *pvb = p.pv + lb + lo;
+        for (int32_t j = t.tid; j * kPerQ < span; j += kThreads) {
+            const uint4 q = q4[j];
+            if (((q.x | q.y | q.z | q.w) & kAtLeast2) == 0) continue;
+            const uint32_t wv[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if (KIND == kDenseWide) {
+                    const int32_t i = j * 4 + k;
+                    if (wv[k] >= 2 && i < span) atomicAdd(pvb + i, c2(wv[k]));
+                } else {
+                    const int32_t i = j * 8 + 2 * k;
+                    const uint32_t c0 = wv[k] & 0xFFFFu, c1 = wv[k] >> 16;
+                    if (c0 >= 2 && i < span) atomicAdd(pvb + i, c2(c0));
+                    if (c1 >= 2 && i + 1 < span) atomicAdd(pvb + i + 1, c2(c1));
+                }
+            }
+        }
+    }
 }
 
 // first id of x's part of its layer, and one past its last
