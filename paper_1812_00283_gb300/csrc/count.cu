@@ -286,18 +286,23 @@ __device__ __forceinline__ unsigned long long wedge_op(const CountParams &p, int
 }
 
 // Adds each lane's x to msum[q], where equal q occupy consecutive lanes (the
-// runs of a window are contiguous): a segmented scan over the warp leaves
-// each run's sum in its last lane, which makes the one shared atomic.
+// runs of a window are contiguous): the last lane of each run takes the
+// difference of an inclusive warp scan at its lane and at the previous run's
+// last lane (found from a ballot of run ends), and makes the one shared atomic.
 template <typename T>
 __device__ __forceinline__ void run_add(unsigned long long *msum, int q, T x, int lane) {
+    T sc = x;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        const T t = __shfl_up_sync(0xffffffffu, x, o);
-        const int qq = __shfl_up_sync(0xffffffffu, q, o);
-        if (lane >= o && qq == q) x += t;
+        const T t = __shfl_up_sync(0xffffffffu, sc, o);
+        if (lane >= o) sc += t;
     }
     const int qn = __shfl_down_sync(0xffffffffu, q, 1);
-    if ((lane == 31 || qn != q) && x) atomicAdd(msum + q, (unsigned long long)x);
+    const bool last = lane == 31 || qn != q;
+    const uint32_t below = __ballot_sync(0xffffffffu, last) & ((1u << lane) - 1u);
+    const T prev = __shfl_sync(0xffffffffu, sc, below ? 31 - __clz(below) : 0);
+    const T sum = below ? sc - prev : sc;
+    if (last && sum) atomicAdd(msum + q, (unsigned long long)sum);
 }
 
 // The per-thread state of one batch of middles that the second walk needs

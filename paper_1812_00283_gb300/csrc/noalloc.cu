@@ -152,12 +152,18 @@ k_count_noalloc(int32_t r, int32_t l, int32_t m, const int32_t *__restrict__ off
         for (int32_t x = blockIdx.x; x < n; x += gridDim.x) {
             const bool in_u = x >= l;
             const int32_t layer = in_u ? r : l;
+            const int32_t mb = in_u ? off_u[x - l] : loff[x];
+            const int32_t me = in_u ? off_u[x - l + 1] : loff[x + 1];
+            // a start none of whose neighbours has lower priority has no
+            // wedges: skip its clear and its walk (most light starts)
+            bool any = false;
+            for (int32_t j = mb + threadIdx.x; j < me && !any; j += kNaThreads)
+                any = lower_priority(deg, in_u ? adj_u[j] : l + ladj[j], x);
+            if (!__syncthreads_or(any)) continue;
             uint4 *c4 = reinterpret_cast<uint4 *>(cnt);
             for (int32_t i = threadIdx.x; i < (layer + 3) / 4; i += kNaThreads)
                 c4[i] = make_uint4(0, 0, 0, 0);
             __syncthreads();
-            const int32_t mb = in_u ? off_u[x - l] : loff[x];
-            const int32_t me = in_u ? off_u[x - l + 1] : loff[x + 1];
             for (int32_t j = mb + warp; j < me; j += kNaWarps) {
                 const int32_t v = in_u ? adj_u[j] : l + ladj[j];       // middle, global id
                 if (!lower_priority(deg, v, x)) continue;
