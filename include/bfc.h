@@ -252,6 +252,61 @@ int bfc_batch_wedges(const bfc_graph *g, void *stream, uint64_t *wedges_dev);
  * allocates only the schedule arrays. */
 int bfc_autotune(bfc_graph *g, void *stream, int iters, bfc_options *chosen);
 
+/* ---- Batches of a fixed shape, counted with no host synchronisation -------
+ * A batch plan prepares and counts batches (bfc_batch) whose union always has
+ * the same shape, with every step on the stream and every array allocated
+ * once: steps a1-a5 (Definition 3's ranks of every graph, Definition 4's
+ * projection, the cut and exact work of Section 4 / Eq. 5, Section 6.2's
+ * heaviest-first bins) and a6-a7 (Algorithm 2 for every start of every
+ * graph in one persistent launch).  No call of bfc_batch_plan_run
+ * synchronises or allocates, so a caller can record a whole step in a CUDA
+ * graph and replay it after writing new contents of the same shape into the
+ * same input buffers.  The library has no counterpart in the paper for this
+ * plumbing; the counts are those of bfc_prepare_batch + bfc_count_batch. */
+typedef struct bfc_batch_plan bfc_batch_plan;
+typedef struct bfc_batch_shape {
+    int32_t num_u, num_l;   /* layer sizes of the union (all graphs together) */
+    int64_t num_edges;      /* edges of the union, at most 2^31 - 1 */
+    int32_t num_graphs;     /* graphs per batch, at least 1 */
+    int32_t max_layer;      /* the largest layer of any one graph, 1 .. 65,535: a
+                               degree stays below 2^16, and each dense start's
+                               end range is one chunk of counters */
+    int32_t reserved[6];    /* must be zero */
+} bfc_batch_shape;
+
+/* Allocates a plan for batches of this shape on the current device (library
+ * pool) and sets up the kernels it uses, on `stream`; synchronises it.  The
+ * options must choose Algorithm 2 (orientation 0) and a team bound of at most
+ * 3,072 wedges (team_max_work -1 or <= 3072: every team table fits, so no
+ * retry pass is needed); core_vertices is ignored (batches have no core).
+ * BFC_ERR_INVALID_ARGUMENT for a shape or options outside these ranges,
+ * BFC_ERR_OUT_OF_MEMORY if the pool cannot hold the plan.  Create the plan
+ * before any stream capture. */
+int bfc_batch_plan_create(const bfc_batch_shape *shape, const bfc_options *opt, void *stream,
+                          bfc_batch_plan **out);
+
+/* One batch of the plan's shape: off_u_dev[num_u + 1] / adj_u_dev[num_edges]
+ * (the union's U-side CSR, L ids global) and graph_u_start_dev /
+ * graph_l_start_dev [num_graphs + 1] (as in bfc_batch), all device memory
+ * that the caller owns.  Writes totals_dev[g] = ⋈ of graph g (uint64
+ * [num_graphs], device) and, if status_dev is not NULL, one int32 status
+ * (device): BFC_OK; BFC_ERR_INVALID_GRAPH for offsets that are not a CSR, an
+ * id out of range, start arrays that are not prefix sums of the layer sizes,
+ * an edge across graphs, a graph layer above max_layer, or (validate) a
+ * duplicate edge; BFC_ERR_INTERNAL for a failed consistency check.  The
+ * totals are defined only when the status is BFC_OK (they are 0 when the
+ * input failed its checks: no kernel after the checks indexes with it).
+ * Asynchronous on `stream`: no host synchronisation, no allocation; the
+ * return value reports launch errors only.  Runs of one plan share its
+ * arrays: issue them on one stream. */
+int bfc_batch_plan_run(bfc_batch_plan *plan, const int32_t *off_u_dev, const int32_t *adj_u_dev,
+                       const int32_t *graph_u_start_dev, const int32_t *graph_l_start_dev,
+                       void *stream, uint64_t *totals_dev, int32_t *status_dev);
+
+/* Frees the plan (stream-ordered on the stream of its last run, then waits
+ * for it).  NULL is ignored. */
+void bfc_batch_plan_destroy(bfc_batch_plan *plan);
+
 /* ---- Serving: continuous batching of counting requests -------------------
  * Requests (one graph each, U-side CSR in HOST memory) may arrive at any time
  * from any thread.  Worker threads (one CUDA stream each) take the oldest

@@ -54,6 +54,11 @@ class bfc_batch(ctypes.Structure):
     _fields_ = [("num_graphs", c_int32), ("graph_u_start", c_void_p), ("graph_l_start", c_void_p)]
 
 
+class bfc_batch_shape(ctypes.Structure):
+    _fields_ = [("num_u", c_int32), ("num_l", c_int32), ("num_edges", c_int64), ("num_graphs", c_int32),
+                ("max_layer", c_int32), ("reserved", c_int32 * 6)]
+
+
 class bfc_server_config(ctypes.Structure):
     _fields_ = [("memory_budget_bytes", c_int64), ("workers", c_int32), ("max_batch_graphs", c_int32),
                 ("max_batch_edges", c_int64), ("warp_max_work", c_int32), ("hash_max_work", c_int32),
@@ -108,6 +113,11 @@ _SIGS = {
     "bfc_count_batch": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "bfc_batch_wedges": (c_int, [c_void_p, c_void_p, c_void_p]),
     "bfc_autotune": (c_int, [c_void_p, c_void_p, c_int, ctypes.POINTER(bfc_options)]),
+    "bfc_batch_plan_create": (c_int, [ctypes.POINTER(bfc_batch_shape), ctypes.POINTER(bfc_options), c_void_p,
+                                      ctypes.POINTER(c_void_p)]),
+    "bfc_batch_plan_run": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                   c_void_p]),
+    "bfc_batch_plan_destroy": (None, [c_void_p]),
     "bfc_server_config_init": (None, [ctypes.POINTER(bfc_server_config)]),
     "bfc_server_create": (c_int, [ctypes.POINTER(bfc_server_config), ctypes.POINTER(c_void_p)]),
     "bfc_server_submit": (c_int, [c_void_p, c_int32, c_int32, c_int64, c_void_p, c_void_p,
@@ -210,6 +220,26 @@ def bfc_prepare_batch(num_u: int, num_l: int, num_edges: int, off_u: int, adj_u:
                                   ctypes.byref(options) if options else None, stream,
                                   ctypes.byref(h)), "bfc_prepare_batch")
     return h.value
+
+
+def bfc_batch_plan_create(num_u: int, num_l: int, num_edges: int, num_graphs: int, max_layer: int,
+                          options: bfc_options | None = None, stream: int = 0) -> int:
+    """A plan for batches of this union shape; returns its handle."""
+    shape = bfc_batch_shape(num_u, num_l, num_edges, num_graphs, max_layer)
+    h = c_void_p()
+    _check(_lib.bfc_batch_plan_create(ctypes.byref(shape), ctypes.byref(options) if options else None,
+                                      stream, ctypes.byref(h)), "bfc_batch_plan_create")
+    return h.value
+
+
+def bfc_batch_plan_run(plan: int, off_u: int, adj_u: int, graph_u_start: int, graph_l_start: int,
+                       stream: int, totals_dev: int, status_dev: int | None = None):
+    _check(_lib.bfc_batch_plan_run(plan, off_u, adj_u, graph_u_start, graph_l_start, stream, totals_dev,
+                                   status_dev), "bfc_batch_plan_run")
+
+
+def bfc_batch_plan_destroy(plan: int):
+    _lib.bfc_batch_plan_destroy(plan)
 
 
 def bfc_count_batch(g: int, stream: int, totals_dev: int, total_dev: int | None = None):

@@ -1,4 +1,5 @@
 // C-ABI entry points of libbfc (declared in include/bfc.h).
+#include <algorithm>
 #include <cstdio>
 #include <atomic>
 #include <cstring>
@@ -296,6 +297,81 @@ int bfc_batch_wedges(const bfc_graph *h, void *stream, uint64_t *wedges_dev) {
     BFC_CUDA(cudaMemcpyAsync(wedges_dev, g->gwork, sizeof(uint64_t) * (size_t)g->num_graphs,
                              cudaMemcpyDeviceToDevice, static_cast<cudaStream_t>(stream)));
     return BFC_OK;
+}
+
+struct bfc_batch_plan {
+    bfc::BatchPlan p;
+};
+
+int bfc_batch_plan_create(const bfc_batch_shape *shape, const bfc_options *opt_in, void *stream,
+                          bfc_batch_plan **out) {
+    bfc::set_last_error("");
+    if (!shape || !out) { bfc::set_last_error("null argument"); return BFC_ERR_INVALID_ARGUMENT; }
+    *out = nullptr;
+    bfc_options opt;
+    if (opt_in) opt = *opt_in; else bfc_options_init(&opt);
+    int rc = check_options(&opt);
+    if (rc) return rc;
+    bool reserved_zero = true;
+    for (int i = 0; i < 6; ++i) reserved_zero = reserved_zero && shape->reserved[i] == 0;
+    if (shape->num_u < 0 || shape->num_l < 0 || shape->num_edges < 0 || shape->num_edges > 2147483647LL ||
+        (int64_t)shape->num_u + shape->num_l > 2147483646LL || shape->num_graphs < 1 ||
+        shape->max_layer < 1 || shape->max_layer > 65535 || !reserved_zero) {
+        bfc::set_last_error("batch shape outside its ranges (max_layer in [1, 65535], num_graphs >= 1, "
+                            "reserved fields zero)");
+        return BFC_ERR_INVALID_ARGUMENT;
+    }
+    if (opt.orientation != 0 || opt.team_max_work > bfc::kTeamFitWork) {
+        bfc::set_last_error("a batch plan counts with Algorithm 2 and team_max_work <= 3072");
+        return BFC_ERR_INVALID_ARGUMENT;
+    }
+    bfc_batch_plan *h = new (std::nothrow) bfc_batch_plan();
+    if (!h) { bfc::set_last_error("host allocation failed"); return BFC_ERR_OUT_OF_MEMORY; }
+    bfc::BatchPlan &pl = h->p;
+    Graph *g = &pl.g;
+    cudaError_t e = cudaGetDevice(&g->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device);
+    if (e != cudaSuccess) { delete h; return bfc::cuda_fail(e, "cudaGetDevice"); }
+    g->grid = opt.num_ctas > 0 ? opt.num_ctas : g->num_sms * bfc::kCountCtasPerSm;
+    opt.core_vertices = 0;
+    g->opt = opt;
+    pl.r = shape->num_u; pl.l = shape->num_l; pl.m = shape->num_edges;
+    pl.num_graphs = shape->num_graphs; pl.max_layer = shape->max_layer;
+    // the team bin as schedule_graph sets it for Algorithm 2
+    const uint64_t team_req = opt.team_max_work >= 0 ? (uint64_t)opt.team_max_work : (uint64_t)bfc::kTeamFitWork;
+    pl.team_max = std::min<uint64_t>(std::max<uint64_t>(team_req, (uint64_t)opt.warp_max_work),
+                                     (uint64_t)opt.hash_max_work);
+    g->team_max = (int32_t)pl.team_max;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    rc = bfc::batch_plan_create(&pl, s);
+    if (rc) {
+        g->mem.release();
+        cudaStreamSynchronize(s);
+        delete h;
+        return rc;
+    }
+    *out = h;
+    return BFC_OK;
+}
+
+int bfc_batch_plan_run(bfc_batch_plan *h, const int32_t *off_u, const int32_t *adj_u, const int32_t *gu,
+                       const int32_t *gl, void *stream, uint64_t *totals_dev, int32_t *status_dev) {
+    bfc::set_last_error("");
+    if (!h || !off_u || (h->p.m > 0 && !adj_u) || !gu || !gl || !totals_dev) {
+        bfc::set_last_error("null argument");
+        return BFC_ERR_INVALID_ARGUMENT;
+    }
+    return bfc::batch_plan_run(&h->p, off_u, adj_u, gu, gl, static_cast<cudaStream_t>(stream),
+                               reinterpret_cast<unsigned long long *>(totals_dev), status_dev);
+}
+
+void bfc_batch_plan_destroy(bfc_batch_plan *h) {
+    if (!h) return;
+    Graph *g = &h->p.g;
+    g->mem.stream = g->stream;
+    g->mem.release();
+    cudaStreamSynchronize(g->stream);
+    delete h;
 }
 
 int bfc_autotune(bfc_graph *h, void *stream, int iters, bfc_options *chosen) {

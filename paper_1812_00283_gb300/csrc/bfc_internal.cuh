@@ -175,6 +175,9 @@ struct Graph {
     uint16_t *core_au = nullptr, *core_al = nullptr;
     int32_t *core_kb_u = nullptr, *core_kb_l = nullptr;
     alignas(64) unsigned char core_map_bytes[4][128];
+    // batch plan: the bin sizes in device memory ([0] dense, [1] hash,
+    // [2] team, [3] warp starts; null for graphs prepared by prepare_graph)
+    unsigned long long *item_counts = nullptr;
 };
 
 // ---------------------------------------------------------------------------
@@ -221,6 +224,24 @@ int launch_count(Graph *g, cudaStream_t s, int mode, unsigned long long *pv_proj
 int rebin_graph(Graph *g, cudaStream_t s, int32_t warp_max_work, int32_t team_max_work,
                 int32_t hash_max_work);
 int count_smem_setup(int device);
+
+// A batch of a fixed shape prepared and counted without host synchronisation
+// or allocation (prepare.cu): every array is allocated by batch_plan_create.
+struct BatchPlan {
+    Graph g;                       // the prepared arrays, rewritten by every run
+    int32_t r = 0, l = 0, num_graphs = 0, max_layer = 0;
+    int64_t m = 0;
+    uint64_t team_max = 0;         // team bin bound (at most 3,072: no retry pass)
+    uint64_t *k0 = nullptr, *k1 = nullptr;
+    int32_t *v0 = nullptr, *v1 = nullptr, *deg_u = nullptr, *deg_l = nullptr, *deg_star = nullptr;
+    int32_t *rows = nullptr, *heads = nullptr, *rows_star = nullptr, *tier_rows = nullptr, *tier_n = nullptr;
+    uint32_t *hist = nullptr, *hist_tmp = nullptr;
+    int64_t *scan64_tmp = nullptr, *deg64 = nullptr;
+    unsigned long long *red = nullptr;   // [0] W, [4..8) bin sizes
+};
+int batch_plan_create(BatchPlan *pl, cudaStream_t s);
+int batch_plan_run(BatchPlan *pl, const int32_t *off_u, const int32_t *adj_u, const int32_t *gu,
+                   const int32_t *gl, cudaStream_t s, unsigned long long *totals, int32_t *status);
 // the dense-core hybrid (core.cu): core choice and matrices in prepare, the
 // masked products before a total count
 int core_prepare(Graph *g, cudaStream_t s, const int32_t *deg_star, int32_t core_vertices,

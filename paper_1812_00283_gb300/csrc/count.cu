@@ -85,7 +85,23 @@ struct CountParams {
     const int32_t *__restrict__ ccut;      // neighbours outside the other layer's core
     const uint16_t *__restrict__ core_au;  // a(u, w) of the U core
     const uint16_t *__restrict__ core_al;  // a(v, x) of the L core
+    // batch plan: bin sizes in device memory (dense, hash, team, warp
+    // starts; a dense start is one item), and the error word whose check
+    // failures stop the launch (null otherwise)
+    const unsigned long long *__restrict__ item_counts;
+    const int *guard;
 };
+
+// item queue lengths: from the host, or from a batch plan's device counts
+__device__ __forceinline__ int64_t n_cta_items(const CountParams &p) {
+    return p.item_counts ? (int64_t)(p.item_counts[0] + p.item_counts[1]) : p.n_cta;
+}
+__device__ __forceinline__ int64_t n_team_items(const CountParams &p) {
+    return p.item_counts ? (int64_t)p.item_counts[2] : p.n_team;
+}
+__device__ __forceinline__ int64_t n_warp_items(const CountParams &p) {
+    return p.item_counts ? (int64_t)p.item_counts[3] : p.n_warp;
+}
 
 // The threads that walk one start together: the whole CTA (barrier 0) or one
 // of its four 256-thread teams (hardware barriers 1..4).
@@ -903,7 +919,7 @@ __device__ unsigned long long dense_stream(const CountParams &p, int64_t &it, un
         acc += item_acc;
         it = sh.next[par];
         par ^= 1;
-        if (it >= p.n_cta) return acc;
+        if (it >= n_cta_items(p)) return acc;
         item = p.cta_items[it];
         if (item.y < 0) return acc;
     }
@@ -1060,13 +1076,16 @@ __global__ void __launch_bounds__(kCountThreads, kCountCtasPerSm) k_count(CountP
     extern __shared__ __align__(16) unsigned char ctr[];
     __shared__ SharedTeam<MODE, Pos, kCountThreads> sh;
     const Team<kCountThreads> cta{(int)threadIdx.x, 0};
+    // a batch plan whose input failed the checks counts nothing (uniform)
+    if (p.guard && (*(volatile const int *)p.guard & (kErrBadOffsets | kErrBadId))) return;
     unsigned long long acc = 0;
     // phase A: CTA items, heaviest first (the dense items, then the hash items)
     if (threadIdx.x == 0) sh.item = atomicAdd(p.cursors, 1);
     __syncthreads();
     int64_t it = sh.item;
     __syncthreads();
-    while (it < p.n_cta) {
+    const int64_t n_cta = n_cta_items(p);
+    while (it < n_cta) {
         if (!has_second_walk(MODE) && p.cta_items[it].y >= 0) {
             acc += dense_stream<MODE, Pos>(p, it, ctr, sh, cta);
             __syncthreads();   // join: the last item's slowest warps
@@ -1083,7 +1102,8 @@ __global__ void __launch_bounds__(kCountThreads, kCountCtasPerSm) k_count(CountP
     // arrays.  A team leaves together (its item index is read before its
     // barrier), so none of its warps is still using the region when the
     // first one starts phase C in its own part of it.
-    if (p.n_team > 0) {
+    const int64_t n_team = n_team_items(p);
+    if (n_team > 0) {
         typedef SharedTeam<MODE, Pos, kTeamThreads> TS;
         static_assert(kTeamTableBytes + sizeof(TS) <= kTeamRegion, "team region overflow");
         const int k = threadIdx.x / kTeamThreads;
@@ -1095,7 +1115,7 @@ __global__ void __launch_bounds__(kCountThreads, kCountCtasPerSm) k_count(CountP
             team.sync();
             const int64_t it = tsh.item;
             team.sync();
-            if (it >= p.n_team) break;
+            if (it >= n_team) break;
             acc += team_item<MODE, Pos>(p, p.team_items[it], table, tsh, team);
         }
     }
@@ -1103,11 +1123,12 @@ __global__ void __launch_bounds__(kCountThreads, kCountCtasPerSm) k_count(CountP
     {
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
         unsigned char *region = ctr + (size_t)warp * kWarpRegion;
+        const int64_t n_warp = n_warp_items(p);
         for (;;) {
             int it = 0;
             if (lane == 0) it = atomicAdd(p.cursors + 1, 1);
             it = __shfl_sync(0xffffffffu, it, 0);
-            if (it >= p.n_warp) break;
+            if (it >= n_warp) break;
             acc += warp_item<MODE>(p, p.warp_items[it], region);
         }
     }
@@ -1258,6 +1279,8 @@ int launch_count(Graph *g, cudaStream_t s, int mode, unsigned long long *pv_proj
     p.core_lo_l = g->core_l > 0 ? g->core_lo_l : g->n;
     p.core_ld_u = g->core_ld_u; p.core_ld_l = g->core_ld_l;
     p.ccut = g->ccut; p.core_au = g->core_au; p.core_al = g->core_al;
+    p.item_counts = g->item_counts;
+    p.guard = g->item_counts ? g->err : nullptr;
     if (p.core_on) {
         // the core pairs' a(u, w), on the same stream before the walk
         int rc2 = core_product(g, s);

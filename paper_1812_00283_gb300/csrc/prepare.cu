@@ -23,6 +23,14 @@ inline unsigned blocks_for(int64_t n, int t = kT) {
     return (unsigned)b;
 }
 
+// A prepared batch run without host synchronisation (the batch plan) checks
+// the caller's CSR on the device; every later kernel of that run is given
+// the error word and returns at once when the CSR failed the checks, so no
+// kernel indexes with unchecked input.  Elsewhere the word is null.
+__device__ __forceinline__ bool aborted(const int *guard) {
+    return guard && (*(volatile const int *)guard & (kErrBadOffsets | kErrBadId));
+}
+
 // ----- validation (always on: every later index depends on it) -------------
 __global__ void k_check_offsets(const int32_t *__restrict__ off, int32_t r, int64_t m, int *err) {
     int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -42,7 +50,9 @@ __global__ void k_check_ids(const int32_t *__restrict__ adj, int64_t m, int32_t 
 
 // ----- a1: degrees -----------------------------------------------------------
 __global__ void k_deg_u(const int32_t *__restrict__ off, int32_t r, int32_t *deg_u,
-                        int32_t *heads) {
+                        int32_t *heads,
+    const int *guard = nullptr) {
+    if (aborted(guard)) return;
     int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (u >= r) return;
     int32_t d = off[u + 1] - off[u];
@@ -50,7 +60,9 @@ __global__ void k_deg_u(const int32_t *__restrict__ off, int32_t r, int32_t *deg
     if (heads && d > 0) heads[off[u]] = (int32_t)u;   // row owning slot off[u]; rows via max-scan
 }
 
-__global__ void k_deg_l(const int32_t *__restrict__ adj, int64_t m, int32_t *deg_l) {
+__global__ void k_deg_l(const int32_t *__restrict__ adj, int64_t m, int32_t *deg_l,
+    const int *guard = nullptr) {
+    if (aborted(guard)) return;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < m;
          k += (int64_t)gridDim.x * blockDim.x)
         atomicAdd(&deg_l[adj[k]], 1);
@@ -72,7 +84,9 @@ __global__ void k_iota_keys(const int32_t *__restrict__ deg, int32_t n, uint64_t
 // contiguous rank range [start[g], start[g+1]) of their layer
 __global__ void k_iota_keys_batch(const int32_t *__restrict__ deg, int32_t n,
                                   const int32_t *__restrict__ start, int32_t num_graphs, int bdeg,
-                                  uint64_t *keys, int32_t *vals) {
+                                  uint64_t *keys, int32_t *vals,
+    const int *guard = nullptr) {
+    if (aborted(guard)) return;
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int32_t lo = 0, hi = num_graphs;
@@ -86,7 +100,9 @@ __global__ void k_iota_keys_batch(const int32_t *__restrict__ deg, int32_t n,
 
 // rank[order[i]] = i; degree of G* vertex (base + i) = sorted key
 __global__ void k_ranks(const uint64_t *__restrict__ sorted_deg, const int32_t *__restrict__ order,
-                        int32_t n, int32_t *rank, int32_t *deg_star, int32_t base, uint64_t deg_mask) {
+                        int32_t n, int32_t *rank, int32_t *deg_star, int32_t base, uint64_t deg_mask,
+    const int *guard = nullptr) {
+    if (aborted(guard)) return;
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     rank[order[i]] = (int32_t)i;
@@ -132,7 +148,9 @@ struct URowOut {
 
 __global__ void k_u_rows_warp(const int32_t *__restrict__ off_u, const int32_t *__restrict__ adj_u,
                               const int32_t *__restrict__ rank_u, const int32_t *__restrict__ rank_l,
-                              int32_t r, URowOut o) {
+                              int32_t r, URowOut o,
+    const int *guard = nullptr) {
+    if (aborted(guard)) return;
     const int lane = threadIdx.x & 31;
     const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -174,7 +192,10 @@ __device__ __forceinline__ void warp_bitonic(uint64_t *buf, int np, int lane) {
 __global__ void __launch_bounds__(kRowCtaThreads) k_u_rows_warp_sort(
     const int32_t *__restrict__ off_u, const int32_t *__restrict__ adj_u,
     const int32_t *__restrict__ rank_u, const int32_t *__restrict__ rank_l,
-    const int32_t *__restrict__ rows, int32_t nrows, URowOut o) {
+    const int32_t *__restrict__ rows, int32_t nrows, URowOut o,
+    const int *guard = nullptr, const int32_t *nrows_dev = nullptr) {
+    if (aborted(guard)) return;
+    if (nrows_dev) nrows = *nrows_dev;
     __shared__ uint64_t buf[kRowCtaThreads / 32][kRowWarpSortMax];
     const int lane = threadIdx.x & 31;
     uint64_t *wb = buf[threadIdx.x >> 5];
@@ -203,7 +224,10 @@ __global__ void __launch_bounds__(kRowCtaThreads) k_u_rows_warp_sort(
 __global__ void __launch_bounds__(kRowCtaThreads) k_u_rows_cta(
     const int32_t *__restrict__ off_u, const int32_t *__restrict__ adj_u,
     const int32_t *__restrict__ rank_u, const int32_t *__restrict__ rank_l,
-    const int32_t *__restrict__ rows, int32_t nrows, URowOut o) {
+    const int32_t *__restrict__ rows, int32_t nrows, URowOut o,
+    const int *guard = nullptr, const int32_t *nrows_dev = nullptr) {
+    if (aborted(guard)) return;
+    if (nrows_dev) nrows = *nrows_dev;
     __shared__ uint64_t buf[kRowCtaMax];
     for (int64_t i0 = blockIdx.x; i0 < nrows; i0 += gridDim.x) {
         const int32_t u = rows[i0];
@@ -240,7 +264,9 @@ __global__ void __launch_bounds__(kRowCtaThreads) k_u_rows_cta(
 // lists of the rows of the CTA tier and of the largest rows (any order: every
 // row is written to its own slots); one atomic per warp and list
 __global__ void k_row_tiers(const int32_t *__restrict__ off_u, int32_t r, int32_t *lists,
-                            int32_t *counts) {
+                            int32_t *counts,
+    const int *guard = nullptr) {
+    if (aborted(guard)) return;
     // lists[t * r ...]: rows of tier t (0: warp sort, 1: CTA sort, 2: radix)
     const int lane = threadIdx.x & 31;
     const uint32_t lt = (1u << lane) - 1u;
@@ -302,7 +328,9 @@ __global__ void k_large_emit(const uint64_t *__restrict__ keys, const int32_t *_
 
 __global__ void k_emit_l_side(const uint64_t *__restrict__ keys2, const int32_t *__restrict__ vals2,
                               int64_t m, int bu, int32_t l, int32_t *adj_star, int32_t *eid_star,
-                              int32_t *rows_star) {
+                              int32_t *rows_star,
+    const int *guard = nullptr) {
+    if (aborted(guard)) return;
     const uint64_t mask_u = (1ull << bu) - 1ull;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < m;
          k += (int64_t)gridDim.x * blockDim.x) {
@@ -313,7 +341,9 @@ __global__ void k_emit_l_side(const uint64_t *__restrict__ keys2, const int32_t 
     }
 }
 
-__global__ void k_deg_to_i64(const int32_t *__restrict__ d, int32_t n, int64_t *out) {
+__global__ void k_deg_to_i64(const int32_t *__restrict__ d, int32_t n, int64_t *out,
+    const int *guard = nullptr) {
+    if (aborted(guard)) return;
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) out[i] = d[i];
 }
@@ -324,7 +354,9 @@ __global__ void k_deg_to_i64(const int32_t *__restrict__ d, int32_t n, int64_t *
 // lower bound on degree: for x in L a U neighbour of equal degree has higher
 // priority (U ids > L ids); for x in U an L neighbour of equal degree is lower.
 __global__ void k_cut(const int64_t *__restrict__ off, const int32_t *__restrict__ adj,
-                      const int32_t *__restrict__ deg_star, int32_t n, int32_t l, int32_t *cut) {
+                      const int32_t *__restrict__ deg_star, int32_t n, int32_t l, int32_t *cut,
+    const int *guard = nullptr) {
+    if (aborted(guard)) return;
     int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= n) return;
     const int64_t b = off[x];
@@ -346,7 +378,9 @@ __global__ void k_cut(const int64_t *__restrict__ off, const int32_t *__restrict
 // with the slot instead of after the slot's neighbour id.
 __global__ void k_plen(const int64_t *__restrict__ off, const int32_t *__restrict__ adj,
                        const int32_t *__restrict__ rows, const int32_t *__restrict__ cut,
-                       int64_t slots, int32_t *plen, int64_t *sbeg) {
+                       int64_t slots, int32_t *plen, int64_t *sbeg,
+    const int *guard = nullptr) {
+    if (aborted(guard)) return;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < slots;
          e += (int64_t)gridDim.x * blockDim.x) {
         const int32_t x = rows[e];
@@ -393,7 +427,9 @@ __global__ void k_slen(const int64_t *__restrict__ off, const int32_t *__restric
 // Algorithm 2, every slot for Algorithm 3); one warp per start.
 __global__ void k_work(const int64_t *__restrict__ off, const int32_t *__restrict__ cut,
                        const int32_t *__restrict__ plen, int32_t n, int all_slots, uint64_t *work,
-                       unsigned long long *total) {
+                       unsigned long long *total,
+    const int *guard = nullptr) {
+    if (aborted(guard)) return;
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -421,7 +457,9 @@ __device__ __forceinline__ bool forced_dense(int32_t x, int32_t l, int32_t core_
 
 __global__ void k_sched_keys(const uint64_t *__restrict__ work, int32_t n, uint64_t maxw,
                              int32_t l, int32_t core_lo_u, int32_t core_lo_l, uint64_t *keys,
-                             int32_t *vals) {
+                             int32_t *vals,
+    const int *guard = nullptr) {
+    if (aborted(guard)) return;
     int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= n) return;
     // ascending key = descending work; zero work last; forced dense starts first
@@ -446,7 +484,9 @@ __global__ void k_count_heavy(const uint64_t *__restrict__ work, int32_t n, uint
 // hash_max), [2] team (warp_max < work <= team_max), [3] warp (0 < work <= warp_max).
 __global__ void k_classify(const uint64_t *__restrict__ work, int32_t n, uint64_t warp_max,
                            uint64_t team_max, uint64_t hash_max, int32_t l, int32_t core_lo_u,
-                           int32_t core_lo_l, unsigned long long *counts) {
+                           int32_t core_lo_l, unsigned long long *counts,
+    const int *guard = nullptr) {
+    if (aborted(guard)) return;
     unsigned long long c[4] = {0, 0, 0, 0};
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
          x += (int64_t)gridDim.x * blockDim.x) {
@@ -560,11 +600,12 @@ __device__ __forceinline__ int32_t graph_of(const int32_t *start, int32_t num_gr
 }
 
 __global__ void k_check_starts(const int32_t *__restrict__ start, int32_t num_graphs,
-                               int32_t total, int *err) {
+                               int32_t total, int *err, int32_t max_len = 0x7fffffff) {
     for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g <= num_graphs;
          g += (int64_t)gridDim.x * blockDim.x) {
         if (g == 0 && start[0] != 0) atomicOr(err, kErrBadOffsets);
-        if (g < num_graphs && start[g + 1] < start[g]) atomicOr(err, kErrBadOffsets);
+        if (g < num_graphs && (start[g + 1] < start[g] || start[g + 1] - start[g] > max_len))
+            atomicOr(err, kErrBadOffsets);
         if (g == num_graphs && start[g] != total) atomicOr(err, kErrBadOffsets);
     }
 }
@@ -572,7 +613,9 @@ __global__ void k_check_starts(const int32_t *__restrict__ start, int32_t num_gr
 // every edge must join a U and an L vertex of the same graph
 __global__ void k_check_batch_edges(const int32_t *__restrict__ rows, const int32_t *__restrict__ adj,
                                     int64_t m, const int32_t *__restrict__ gu,
-                                    const int32_t *__restrict__ gl, int32_t num_graphs, int *err) {
+                                    const int32_t *__restrict__ gl, int32_t num_graphs, int *err,
+    const int *guard = nullptr) {
+    if (aborted(guard)) return;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < m;
          k += (int64_t)gridDim.x * blockDim.x)
         if (graph_of(gu, num_graphs, rows[k]) != graph_of(gl, num_graphs, adj[k]))
@@ -583,7 +626,9 @@ __global__ void k_check_batch_edges(const int32_t *__restrict__ rows, const int3
 // holds it; vbase[x] = the first G* id of that graph in x's layer
 __global__ void k_graph_star(int32_t r, int32_t l, const int32_t *__restrict__ gu,
                              const int32_t *__restrict__ gl, int32_t num_graphs, int32_t *gstar,
-                             int32_t *vbase, int32_t *vend) {
+                             int32_t *vbase, int32_t *vend,
+    const int *guard = nullptr) {
+    if (aborted(guard)) return;
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < (int64_t)r + l;
          x += (int64_t)gridDim.x * blockDim.x) {
         if (x < l) {
@@ -601,7 +646,9 @@ __global__ void k_graph_star(int32_t r, int32_t l, const int32_t *__restrict__ g
 }
 
 __global__ void k_graph_work(const uint64_t *__restrict__ work, const int32_t *__restrict__ gstar,
-                             int32_t n, unsigned long long *gwork) {
+                             int32_t n, unsigned long long *gwork,
+    const int *guard = nullptr) {
+    if (aborted(guard)) return;
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
          x += (int64_t)gridDim.x * blockDim.x)
         if (work[x]) atomicAdd(gwork + gstar[x], (unsigned long long)work[x]);
@@ -1076,6 +1123,290 @@ int prepare_graph(const bfc_csr *csr, const bfc_options *opt, cudaStream_t s, Gr
     g->info.device_bytes = (int64_t)g->mem.total;
     BFC_CUDA(cudaStreamSynchronize(s));
 #undef GET
+    return BFC_OK;
+}
+
+// ----------------------------------------------------------------------------
+// Batch plan: a batch of a fixed shape prepared and counted with no host
+// synchronisation and no allocation, so the whole step can be captured in a
+// CUDA graph and replayed on new contents.  Sizes that prepare_graph reads
+// back to the host come from the shape instead: the degree bits of the rank
+// keys from the largest layer of one graph, the row tiers and the bin sizes
+// from counts in device memory that the kernels read themselves, and every
+// dense start is one end-range chunk (a graph's layer holds at most 65,535
+// vertices, so counts fit 16 bits and the end range one chunk).
+// ----------------------------------------------------------------------------
+namespace {
+
+constexpr int32_t kPlanMaxLayer = 65535;
+constexpr int kBitmapWords = (kPlanMaxLayer + 1) / 32;   // 2,048 words, 8 KB
+
+// U rows of more than 4,096 neighbours, one CTA per row.  The row's L ranks
+// are distinct and lie in its graph's L rank range, so a bitmap of that range
+// gives every neighbour its position: the number of set bits below its rank.
+// A bit that is already set is a duplicate edge.
+__global__ void __launch_bounds__(kRowCtaThreads) k_u_rows_bitmap(
+    const int32_t *__restrict__ off_u, const int32_t *__restrict__ adj_u,
+    const int32_t *__restrict__ rank_u, const int32_t *__restrict__ rank_l,
+    const int32_t *__restrict__ rows, const int32_t *__restrict__ nrows_dev,
+    const int32_t *__restrict__ gl, const int32_t *__restrict__ gu, int32_t num_graphs, URowOut o,
+    const int *guard) {
+    if (aborted(guard)) return;
+    __shared__ uint32_t bits[kBitmapWords];
+    __shared__ int32_t wpre[kBitmapWords];
+    __shared__ int32_t part[kRowCtaThreads / 32];
+    constexpr int kPerThread = kBitmapWords / kRowCtaThreads;   // 8 words
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int32_t nrows = *nrows_dev;
+    for (int64_t i0 = blockIdx.x; i0 < nrows; i0 += gridDim.x) {
+        const int32_t u = rows[i0];
+        const int32_t b = off_u[u], d = off_u[u + 1] - b;
+        const int32_t g = graph_of(gu, num_graphs, u);
+        const int32_t base = gl[g];   // the graph's L ranks: [gl[g], gl[g + 1])
+        for (int i = tid; i < kBitmapWords; i += kRowCtaThreads) bits[i] = 0;
+        __syncthreads();
+        for (int32_t i = tid; i < d; i += kRowCtaThreads) {
+            // every edge stays inside its graph (checked), so 0 <= k < 65,536
+            const int32_t k = rank_l[adj_u[b + i]] - base;
+            const uint32_t bit = 1u << (k & 31);
+            const uint32_t old = atomicOr(&bits[k >> 5], bit);
+            if ((old & bit) && o.check_dup) atomicOr(o.err, kErrDuplicate);
+        }
+        __syncthreads();
+        // exclusive prefix of the words' popcounts: 8 words per thread
+        int32_t loc[kPerThread], sum = 0;
+#pragma unroll
+        for (int j = 0; j < kPerThread; ++j) {
+            loc[j] = sum;
+            sum += __popc(bits[tid * kPerThread + j]);
+        }
+        int32_t incl = sum;
+#pragma unroll
+        for (int dd = 1; dd < 32; dd <<= 1) {
+            const int32_t t = __shfl_up_sync(0xffffffffu, incl, dd);
+            if (lane >= dd) incl += t;
+        }
+        if (lane == 31) part[warp] = incl;
+        __syncthreads();
+        int32_t before = 0;
+        for (int w = 0; w < warp; ++w) before += part[w];
+        before += incl - sum;
+#pragma unroll
+        for (int j = 0; j < kPerThread; ++j) wpre[tid * kPerThread + j] = before + loc[j];
+        __syncthreads();
+        const int32_t ru = rank_u[u];
+        for (int32_t i = tid; i < d; i += kRowCtaThreads) {
+            const int32_t rl = rank_l[adj_u[b + i]];
+            const int32_t k = rl - base;
+            const int32_t pos = wpre[k >> 5] + __popc(bits[k >> 5] & ((1u << (k & 31)) - 1u));
+            o.put(ru, pos, rl, b + i);
+        }
+        __syncthreads();   // the bitmap is reused by the next row
+    }
+}
+
+// heaviest first by exact work, 32 key bits (work saturated at 2^32 - 1)
+__global__ void k_sched_keys_plan(const uint64_t *__restrict__ work, int32_t n, uint64_t *keys,
+                                  int32_t *vals, const int *guard) {
+    if (aborted(guard)) return;
+    const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= n) return;
+    const uint64_t w = work[x];
+    keys[x] = 0xFFFFFFFFull - (w < 0xFFFFFFFFull ? w : 0xFFFFFFFFull);
+    vals[x] = (int32_t)x;
+}
+
+// the item lists from the sorted order and the bin sizes on the device: a
+// dense start is one chunk, so the lists follow the order directly
+__global__ void k_emit_items_plan(const int32_t *__restrict__ order,
+                                  const unsigned long long *__restrict__ counts, int2 *cta_items,
+                                  int32_t *team_items, int32_t *warp_items, const int *guard) {
+    if (aborted(guard)) return;
+    const int64_t nd = (int64_t)counts[0], nh = (int64_t)counts[1], nt = (int64_t)counts[2],
+                  nw = (int64_t)counts[3];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nd + nh + nt + nw;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t x = order[i];
+        if (i < nd) cta_items[i] = make_int2(x, 0);
+        else if (i < nd + nh) cta_items[i] = make_int2(x, -1);
+        else if (i < nd + nh + nt) team_items[i - nd - nh] = x;
+        else warp_items[i - nd - nh - nt] = x;
+    }
+}
+
+__global__ void k_plan_status(const int *__restrict__ err, int check_dup, int32_t *status) {
+    const int e = *err;
+    int32_t st = BFC_OK;
+    if (e & (kErrBadOffsets | kErrBadId)) st = BFC_ERR_INVALID_GRAPH;
+    else if ((e & kErrDuplicate) && check_dup) st = BFC_ERR_INVALID_GRAPH;
+    else if (e & kErrTimeout) st = BFC_ERR_TIMEOUT;
+    else if (e & (kErrHashFull | kErrBounds)) st = BFC_ERR_INTERNAL;
+    *status = st;
+}
+
+}  // namespace
+
+int batch_plan_create(BatchPlan *pl, cudaStream_t s) {
+    Graph *g = &pl->g;
+    const int32_t r = pl->r, l = pl->l, n = r + l, G = pl->num_graphs;
+    const int64_t m = pl->m;
+    g->r = r; g->l = l; g->n = n; g->m = m;
+    g->num_graphs = G;
+    g->stream = s;
+    g->mem.stream = s;
+#define GET(ptr, cnt)                                                                 \
+    do {                                                                              \
+        cudaError_t e_ = g->mem.get(&(ptr), (size_t)std::max<int64_t>((int64_t)(cnt), 1)); \
+        if (e_ != cudaSuccess) {                                                      \
+            set_last_error(std::string("device allocation failed: ") + #ptr);         \
+            return BFC_ERR_OUT_OF_MEMORY;                                             \
+        }                                                                             \
+    } while (0)
+    // kept arrays (those of prepare_graph for a batch)
+    GET(g->err, 4); GET(g->rank_u, r); GET(g->rank_l, l); GET(g->off, (int64_t)n + 1);
+    GET(g->adj, 2 * m); GET(g->eid, 2 * m); GET(g->plen, 2 * m); GET(g->cut, n); GET(g->work, n);
+    GET(g->cursors, 8); GET(g->acc, 2); GET(g->pv, 1); GET(g->sbeg, 2 * m);
+    GET(g->gstar, n); GET(g->vbase, n); GET(g->vend, n); GET(g->gwork, G);
+    GET(g->cta_items, n); GET(g->team_items, n); GET(g->warp_items, n); GET(g->retry, 1);
+    // temporaries, kept with the plan
+    const int64_t nsort = std::max<int64_t>({(int64_t)r, (int64_t)l, m, (int64_t)n, 1});
+    GET(pl->k0, nsort + 1); GET(pl->k1, nsort + 1); GET(pl->v0, nsort); GET(pl->v1, nsort);
+    GET(pl->deg_u, r); GET(pl->deg_l, l); GET(pl->deg_star, n);
+    GET(pl->rows, m); GET(pl->heads, m); GET(pl->rows_star, 2 * m);
+    GET(pl->tier_rows, 3 * (int64_t)std::max(r, 1)); GET(pl->tier_n, 4);
+    GET(pl->hist, radix_hist_elems(nsort));
+    GET(pl->hist_tmp, scan_tmp_elems<uint32_t>((int64_t)radix_hist_elems(nsort)));
+    GET(pl->scan64_tmp, std::max(scan_tmp_elems<int64_t>((int64_t)n + 1), max_scan_tmp_elems(m)));
+    GET(pl->deg64, (int64_t)n + 1); GET(pl->red, 8);
+#undef GET
+    // every kept array starts zeroed: a run that stops at the checks leaves
+    // arrays that later kernels can still index safely
+    for (int i = 0; i < g->mem.n; ++i) BFC_CUDA(cudaMemsetAsync(g->mem.ptr[i], 0, g->mem.bytes[i], s));
+    g->n_cta_items = 0; g->n_team_items = 0; g->n_warp_items = 0;
+    g->retry_static = 0; g->retry_cap = 1; g->may_retry = false;
+    g->info.num_u = r; g->info.num_l = l; g->info.num_edges = m;
+    g->info.device_bytes = (int64_t)g->mem.total;
+    // the radix sort's and the count's kernel attributes are set here, outside
+    // any capture: a two-key sort and the count's per-device setup
+    int which = 0;
+    BFC_CUDA(radix_sort_pairs(pl->k0, pl->v0, pl->k1, pl->v1, 2, 0, 8, pl->hist, pl->hist_tmp, s, &which));
+    int rc = count_smem_setup(g->device);
+    if (rc) return rc;
+    BFC_CUDA(cudaStreamSynchronize(s));
+    return BFC_OK;
+}
+
+int batch_plan_run(BatchPlan *pl, const int32_t *off_u, const int32_t *adj_u, const int32_t *gu,
+                   const int32_t *gl, cudaStream_t s, unsigned long long *totals, int32_t *status) {
+    Graph *g = &pl->g;
+    const int32_t r = pl->r, l = pl->l, n = r + l, G = pl->num_graphs;
+    const int64_t m = pl->m;
+    const int *guard = g->err;
+    g->stream = s;
+    const bfc_options *opt = &g->opt;
+    BFC_CUDA(cudaMemsetAsync(g->err, 0, 4 * sizeof(int), s));
+    // ---- checks: the CSR, the graph start arrays, edges inside their graph
+    k_check_offsets<<<blocks_for((int64_t)r + 1), kT, 0, s>>>(off_u, r, m, g->err); note_launch();
+    if (m > 0) { k_check_ids<<<grid_stride_blocks(m), kT, 0, s>>>(adj_u, m, l, g->err); note_launch(); }
+    k_check_starts<<<blocks_for((int64_t)G + 1), kT, 0, s>>>(gu, G, r, g->err, pl->max_layer); note_launch();
+    k_check_starts<<<blocks_for((int64_t)G + 1), kT, 0, s>>>(gl, G, l, g->err, pl->max_layer); note_launch();
+    BFC_CUDA(cudaGetLastError());
+    // ---- a1: degrees
+    BFC_CUDA(cudaMemsetAsync(pl->deg_l, 0, sizeof(int32_t) * std::max<int64_t>(l, 1), s));
+    BFC_CUDA(cudaMemsetAsync(pl->heads, 0, sizeof(int32_t) * std::max<int64_t>(m, 1), s));
+    if (r > 0) { k_deg_u<<<blocks_for(r), kT, 0, s>>>(off_u, r, pl->deg_u, pl->heads, guard); note_launch(); }
+    if (m > 0) { k_deg_l<<<grid_stride_blocks(m), kT, 0, s>>>(adj_u, m, pl->deg_l, guard); note_launch(); }
+    BFC_CUDA(cudaGetLastError());
+    // ---- a2: graph-major ranks; a degree is below 2^bdeg (at most the other layer)
+    const int bdeg = bits_for((uint64_t)pl->max_layer);
+    const int bkey = bdeg + bits_for((uint64_t)(G - 1));
+    const uint64_t dmask = (1ull << bdeg) - 1;
+    int which = 0;
+    for (int side = 0; side < 2; ++side) {
+        const int32_t cnt = side == 0 ? r : l;
+        if (cnt == 0) continue;
+        const int32_t *deg = side == 0 ? pl->deg_u : pl->deg_l;
+        const int32_t *start = side == 0 ? gu : gl;
+        k_iota_keys_batch<<<blocks_for(cnt), kT, 0, s>>>(deg, cnt, start, G, bdeg, pl->k0, pl->v0, guard); note_launch();
+        BFC_CUDA(cudaGetLastError());
+        BFC_CUDA(radix_sort_pairs(pl->k0, pl->v0, pl->k1, pl->v1, cnt, 0, bkey, pl->hist, pl->hist_tmp, s, &which));
+        const uint64_t *ks = which ? pl->k1 : pl->k0;
+        const int32_t *vs = which ? pl->v1 : pl->v0;
+        k_ranks<<<blocks_for(cnt), kT, 0, s>>>(ks, vs, cnt, side == 0 ? g->rank_u : g->rank_l, pl->deg_star,
+                                               side == 0 ? l : 0, dmask, guard); note_launch();
+        BFC_CUDA(cudaGetLastError());
+    }
+    if (n > 0) {
+        k_graph_star<<<grid_stride_blocks(n), kT, 0, s>>>(r, l, gu, gl, G, g->gstar, g->vbase, g->vend, guard); note_launch();
+        k_deg_to_i64<<<blocks_for(n), kT, 0, s>>>(pl->deg_star, n, pl->deg64, guard); note_launch();
+        BFC_CUDA(cudaGetLastError());
+    }
+    BFC_CUDA(scan_exclusive<int64_t>(pl->deg64, g->off, n, pl->scan64_tmp, s));
+    // ---- a3: G*
+    const int bu = bits_for(r > 0 ? (uint64_t)(r - 1) : 0);
+    const int bl = bits_for(l > 0 ? (uint64_t)(l - 1) : 0);
+    if (m > 0) {
+        BFC_CUDA(max_scan_inclusive(pl->heads, pl->rows, m, (int32_t *)pl->scan64_tmp, s));
+        k_check_batch_edges<<<grid_stride_blocks(m), kT, 0, s>>>(pl->rows, adj_u, m, gu, gl, G, g->err, guard); note_launch();
+        const URowOut uo{m, l, bu, g->off, g->adj, g->eid, pl->rows_star, pl->k1, pl->v1, g->err, opt->validate};
+        k_u_rows_warp<<<grid_stride_blocks((int64_t)r * 32), kT, 0, s>>>(off_u, adj_u, g->rank_u, g->rank_l, r, uo,
+                                                                         guard); note_launch();
+        BFC_CUDA(cudaMemsetAsync(pl->tier_n, 0, 4 * sizeof(int32_t), s));
+        k_row_tiers<<<grid_stride_blocks(r), kT, 0, s>>>(off_u, r, pl->tier_rows, pl->tier_n, guard); note_launch();
+        k_u_rows_warp_sort<<<152 * 8, kRowCtaThreads, 0, s>>>(off_u, adj_u, g->rank_u, g->rank_l, pl->tier_rows, 0,
+                                                              uo, guard, pl->tier_n); note_launch();
+        k_u_rows_cta<<<152 * 16, kRowCtaThreads, 0, s>>>(off_u, adj_u, g->rank_u, g->rank_l, pl->tier_rows + r, 0,
+                                                         uo, guard, pl->tier_n + 1); note_launch();
+        k_u_rows_bitmap<<<152 * 4, kRowCtaThreads, 0, s>>>(off_u, adj_u, g->rank_u, g->rank_l,
+                                                           pl->tier_rows + 2 * (int64_t)r, pl->tier_n + 2, gl, gu,
+                                                           G, uo, guard); note_launch();
+        BFC_CUDA(cudaGetLastError());
+        // L side: stable sort of the swapped keys on their rank_l bits
+        int which2 = 0;
+        BFC_CUDA(radix_sort_pairs(pl->k1, pl->v1, pl->k0, pl->v0, m, bu, bu + bl, pl->hist, pl->hist_tmp, s, &which2));
+        const uint64_t *k2 = which2 ? pl->k0 : pl->k1;
+        const int32_t *v2 = which2 ? pl->v0 : pl->v1;
+        k_emit_l_side<<<grid_stride_blocks(m), kT, 0, s>>>(k2, v2, m, bu, l, g->adj, g->eid, pl->rows_star,
+                                                            guard); note_launch();
+        BFC_CUDA(cudaGetLastError());
+    }
+    // ---- a4: cut, runs, work
+    BFC_CUDA(cudaMemsetAsync(pl->red, 0, 8 * sizeof(unsigned long long), s));
+    if (n > 0) { k_cut<<<blocks_for(n), kT, 0, s>>>(g->off, g->adj, pl->deg_star, n, l, g->cut, guard); note_launch(); }
+    if (m > 0) {
+        k_plen<<<grid_stride_blocks(2 * m), kT, 0, s>>>(g->off, g->adj, pl->rows_star, g->cut, 2 * m, g->plen,
+                                                         g->sbeg, guard); note_launch();
+    }
+    if (n > 0) {
+        k_work<<<grid_stride_blocks((int64_t)n * 32), kT, 0, s>>>(g->off, g->cut, g->plen, n, 0, g->work, pl->red,
+                                                                   guard); note_launch();
+        BFC_CUDA(cudaMemsetAsync(g->gwork, 0, sizeof(unsigned long long) * G, s));
+        k_graph_work<<<grid_stride_blocks(n), kT, 0, s>>>(g->work, g->gstar, n, g->gwork, guard); note_launch();
+        BFC_CUDA(cudaGetLastError());
+    }
+    // ---- a5: heaviest first, bins from device counts
+    unsigned long long *bins = pl->red + 4;
+    if (n > 0) {
+        k_sched_keys_plan<<<blocks_for(n), kT, 0, s>>>(g->work, n, pl->k0, pl->v0, guard); note_launch();
+        BFC_CUDA(cudaGetLastError());
+        BFC_CUDA(radix_sort_pairs(pl->k0, pl->v0, pl->k1, pl->v1, n, 0, 32, pl->hist, pl->hist_tmp, s, &which));
+        const int32_t *order = which ? pl->v1 : pl->v0;
+        k_classify<<<grid_stride_blocks(n), kT, 0, s>>>(g->work, n, (uint64_t)opt->warp_max_work,
+                                                        (uint64_t)pl->team_max, (uint64_t)opt->hash_max_work, l, n, n,
+                                                        bins, guard); note_launch();
+        k_emit_items_plan<<<grid_stride_blocks(n), kT, 0, s>>>(order, bins, g->cta_items, g->team_items,
+                                                               g->warp_items, guard); note_launch();
+        BFC_CUDA(cudaGetLastError());
+    }
+    // ---- a6-a7: one persistent count; per-graph totals
+    BFC_CUDA(cudaMemsetAsync(totals, 0, sizeof(unsigned long long) * G, s));
+    g->item_counts = bins;
+    int rc = launch_count(g, s, kModeBatch, nullptr, nullptr, totals);
+    if (rc) return rc;
+    if (status) {
+        k_plan_status<<<1, 1, 0, s>>>(g->err, opt->validate, status); note_launch();
+        BFC_CUDA(cudaGetLastError());
+    }
     return BFC_OK;
 }
 

@@ -57,6 +57,7 @@ int main(void) {
   printf("%zu %zu %zu\\n", offsetof(bfc_options, team_max_work), offsetof(bfc_info, team_starts),
          sizeof(bfc_server_config));
   printf("%zu %zu\\n", offsetof(bfc_server_config, team_max_work), sizeof(bfc_server_stats));
+  printf("%zu %zu\\n", sizeof(bfc_batch_shape), offsetof(bfc_batch_shape, max_layer));
   return 0;
 }
 ''')
@@ -68,9 +69,10 @@ int main(void) {
                          ctypes.sizeof(bfc.bfc_info)]
     assert sizes[3:6] == [bfc.bfc_csr.adj_u.offset, bfc.bfc_options.reserved.offset,
                           bfc.bfc_info.max_deg_l.offset]
-    assert sizes[6:] == [bfc.bfc_options.team_max_work.offset, bfc.bfc_info.team_starts.offset,
-                         ctypes.sizeof(bfc.bfc_server_config), bfc.bfc_server_config.team_max_work.offset,
-                         ctypes.sizeof(bfc.bfc_server_stats)]
+    assert sizes[6:11] == [bfc.bfc_options.team_max_work.offset, bfc.bfc_info.team_starts.offset,
+                           ctypes.sizeof(bfc.bfc_server_config), bfc.bfc_server_config.team_max_work.offset,
+                           ctypes.sizeof(bfc.bfc_server_stats)]
+    assert sizes[11:] == [ctypes.sizeof(bfc.bfc_batch_shape), bfc.bfc_batch_shape.max_layer.offset]
 
 
 @pytest.mark.parametrize("case", ["null", "negative", "too_many_edges", "bad_option", "null_ptr"])
@@ -100,3 +102,25 @@ def test_null_graph_calls(bfc):
     assert lib.bfc_count(None, None, None) == 1
     assert lib.bfc_sync(None, None) == 1
     lib.bfc_release(None)
+
+
+@pytest.mark.parametrize("case", ["max_layer", "graphs", "orientation", "team", "reserved"])
+def test_batch_plan_argument_errors_before_cuda(bfc, case):
+    # shape and option checks come before any device work
+    lib = bfc.library()
+    h = ctypes.c_void_p()
+    shape = bfc.bfc_batch_shape(100, 100, 500, 4, 50)
+    opts = bfc.bfc_options_init()
+    if case == "max_layer":
+        shape.max_layer = 65536
+    elif case == "graphs":
+        shape.num_graphs = 0
+    elif case == "orientation":
+        opts.orientation = 1
+    elif case == "team":
+        opts.team_max_work = 4096
+    else:
+        shape.reserved[2] = 1
+    rc = lib.bfc_batch_plan_create(ctypes.byref(shape), ctypes.byref(opts), None, ctypes.byref(h))
+    assert rc == 1 and h.value is None
+    assert bfc.bfc_last_error()
