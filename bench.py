@@ -148,6 +148,40 @@ def run_batch(args, rank, world):
     _, W_all, _ = reduce_over_ranks(world, dev, 0.0, W * args.steps)
     value = graphs_all / (t_total / 1e3)
 
+    # the whole step (a1-a7: checks, ranks, projection, cut/work, bins, the
+    # persistent count, per-graph totals) recorded once as a CUDA graph on a
+    # batch plan and replayed: no host synchronisation and no allocation per
+    # step (tuned bounds as above)
+    max_layer = max(max(g.num_u, g.num_l) for g in graphs)
+    plan = bfc.bfc_batch_plan_create(r, l, m, num, max_layer, opts, sp)
+    ptot = torch.zeros(num, dtype=torch.int64, device=dev)
+    pst = torch.zeros(1, dtype=torch.int32, device=dev)
+    bfc.bfc_batch_plan_run(plan, off.data_ptr(), adj.data_ptr(), us.data_ptr(), ls.data_ptr(), sp,
+                           ptot.data_ptr(), pst.data_ptr())
+    torch.cuda.synchronize()
+    pg = torch.cuda.CUDAGraph()
+    cap = torch.cuda.Stream()
+    cap.wait_stream(s)
+    with torch.cuda.graph(pg, stream=cap):
+        bfc.bfc_batch_plan_run(plan, off.data_ptr(), adj.data_ptr(), us.data_ptr(), ls.data_ptr(),
+                               cap.cuda_stream, ptot.data_ptr(), pst.data_ptr())
+    for _ in range(args.warmup):
+        flush.fill_(1)
+        pg.replay()
+    pevs = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        flush.fill_(i & 0xff)
+        pevs[i][0].record(s)
+        pg.replay()
+        pevs[i][1].record(s)
+    torch.cuda.synchronize()
+    if int(pst.item()) != 0 or not torch.equal(ptot, expect):
+        raise SystemExit("the batch plan's replayed step disagrees with the batched path")
+    plan_ms = [e[0].elapsed_time(e[1]) for e in pevs]
+    bfc.bfc_batch_plan_destroy(plan)
+    del pg
+
     # the per-graph path: one prepare + one count launch per graph, in turn
     lat = []
     done_at = []
@@ -186,6 +220,11 @@ def run_batch(args, rank, world):
                                    hash_max_work=chosen.hash_max_work),
                     parallelism=f"replicas x{world} (each rank its own batch, no collective)",
                     generation_s=gen_s),
+        plan_graph_replay=dict(graphs_per_s=num / (statistics.median(plan_ms) / 1e3),
+                               ms_per_step_median=statistics.median(plan_ms), ms_per_step_max=max(plan_ms),
+                               note="the whole step (checks, ranks, projection, cut/work, bins, count, "
+                                    "per-graph totals) as one CUDA graph replay of a batch plan: no host "
+                                    "synchronisation, no allocation; totals equal the batched path's"),
         batched=dict(graphs_per_s=value, wedges_per_s=W_all / (t_total / 1e3),
                      latency_ms_p50=p50_all, latency_ms_p99=p99_all,
                      request_completion_ms_p50=p50_all, request_completion_ms_p99=p99_all,

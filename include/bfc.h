@@ -128,7 +128,14 @@ typedef struct bfc_options {
                                per-edge counts of the same graph walk every
                                wedge as usual.  Costs 8·K_U·K_L bytes of bf16
                                operands and 2·(K_U² + K_L²) bytes of products. */
-    int32_t reserved[8];    /* must be zero */
+    int32_t use_tuned;      /* 1: if bfc_autotune has tuned a graph of the same
+                               size class in this process (same orientation,
+                               single graph or batch, and the same
+                               floor(log2) of the edge count and of the vertex
+                               count), prepare with the bin bounds it chose
+                               instead of warp/team/hash_max_work; 0 (default):
+                               use the bounds given here */
+    int32_t reserved[7];    /* must be zero */
 } bfc_options;
 
 /* Figures of a prepared graph (host values). */
@@ -248,8 +255,12 @@ int bfc_batch_wedges(const bfc_graph *g, void *stream, uint64_t *wedges_dev);
  * team_max_work in {512, 3072} x hash_max_work in {4096, 24576}; Algorithm 3:
  * warp_max_work in {32, 128, 384} x team_max_work in {2048, 16384}), times
  * `iters` count launches of each with CUDA events on `stream`, keeps the
- * fastest and writes it to *chosen (nullable).  Synchronises `stream`;
- * allocates only the schedule arrays. */
+ * fastest and writes it to *chosen (nullable).  The choice is also kept for
+ * the graph's size class for the rest of the process (see use_tuned; a later
+ * tuning of the same class replaces it).  The CTA shape of the count (1,024
+ * threads per SM, four 256-thread teams, 2,048 middles per batch) is fixed
+ * at compile time.  Synchronises `stream`; allocates only the schedule
+ * arrays. */
 int bfc_autotune(bfc_graph *g, void *stream, int iters, bfc_options *chosen);
 
 /* ---- Batches of a fixed shape, counted with no host synchronisation -------

@@ -35,7 +35,8 @@ class bfc_csr(ctypes.Structure):
 class bfc_options(ctypes.Structure):
     _fields_ = [("validate", c_int32), ("warp_max_work", c_int32), ("hash_max_work", c_int32),
                 ("num_ctas", c_int32), ("wide_positions", c_int32), ("orientation", c_int32),
-                ("team_max_work", c_int32), ("core_vertices", c_int32), ("reserved", c_int32 * 8)]
+                ("team_max_work", c_int32), ("core_vertices", c_int32), ("use_tuned", c_int32),
+                ("reserved", c_int32 * 7)]
 
 
 class bfc_info(ctypes.Structure):

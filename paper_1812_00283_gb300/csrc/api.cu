@@ -6,6 +6,7 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "bfc_internal.cuh"
 
@@ -98,6 +99,39 @@ namespace bfc {
 const Graph *graph_of_handle(const bfc_graph *h) { return &h->g; }
 }  // namespace bfc
 
+// Bin bounds chosen by bfc_autotune, per size class, for the rest of the
+// process: key = (orientation, batch or single graph, floor(log2) of the edge
+// count, floor(log2) of the vertex count).
+namespace {
+struct TunedKey {
+    int orient, batch, le, ln;
+    bool operator==(const TunedKey &o) const {
+        return orient == o.orient && batch == o.batch && le == o.le && ln == o.ln;
+    }
+};
+struct Tuned { TunedKey k; int32_t w, t, h; };
+std::mutex g_tuned_mutex;
+std::vector<Tuned> g_tuned;
+
+TunedKey tuned_key(int orient, bool batch, int64_t m, int64_t n) {
+    return TunedKey{orient, batch ? 1 : 0, bfc::bits_for((uint64_t)m), bfc::bits_for((uint64_t)n)};
+}
+void tuned_store(const TunedKey &k, int32_t w, int32_t t, int32_t h) {
+    std::lock_guard<std::mutex> lk(g_tuned_mutex);
+    for (auto &e : g_tuned)
+        if (e.k == k) { e.w = w; e.t = t; e.h = h; return; }
+    g_tuned.push_back(Tuned{k, w, t, h});
+}
+// applies a stored choice to *o when use_tuned asks for it
+void tuned_apply(bfc_options *o, bool batch, int64_t m, int64_t n) {
+    if (!o->use_tuned) return;
+    const TunedKey k = tuned_key(o->orientation, batch, m, n);
+    std::lock_guard<std::mutex> lk(g_tuned_mutex);
+    for (const auto &e : g_tuned)
+        if (e.k == k) { o->warp_max_work = e.w; o->team_max_work = e.t; o->hash_max_work = e.h; return; }
+}
+}  // namespace
+
 static int check_options(const bfc_options *o) {
     if (o->warp_max_work < 0 || o->warp_max_work > bfc::kWarpMaxWork) {
         bfc::set_last_error("warp_max_work must lie in [0, " + std::to_string(bfc::kWarpMaxWork) + "]");
@@ -128,7 +162,11 @@ static int check_options(const bfc_options *o) {
         bfc::set_last_error("core_vertices must be -1 (automatic), 0 (off) or a core size");
         return BFC_ERR_INVALID_ARGUMENT;
     }
-    for (int i = 0; i < 8; ++i)
+    if (o->use_tuned != 0 && o->use_tuned != 1) {
+        bfc::set_last_error("use_tuned must be 0 or 1");
+        return BFC_ERR_INVALID_ARGUMENT;
+    }
+    for (int i = 0; i < 7; ++i)
         if (o->reserved[i] != 0) {
             bfc::set_last_error("reserved option fields must be zero");
             return BFC_ERR_INVALID_ARGUMENT;
@@ -172,6 +210,7 @@ int bfc_prepare(const bfc_csr *csr, const bfc_options *opt_in, void *stream, bfc
     if (csr->num_edges > 0 && csr->num_l == 0) {
         bfc::set_last_error("edges with an empty L layer"); return BFC_ERR_INVALID_GRAPH;
     }
+    tuned_apply(&opt, false, csr->num_edges, (int64_t)csr->num_u + csr->num_l);
     bfc_graph *h = new (std::nothrow) bfc_graph();
     if (!h) { bfc::set_last_error("host allocation failed"); return BFC_ERR_OUT_OF_MEMORY; }
     Graph *g = &h->g;
@@ -255,6 +294,7 @@ int bfc_prepare_batch(const bfc_csr *csr, const bfc_batch *batch, const bfc_opti
         bfc::set_last_error("invalid union CSR arguments");
         return BFC_ERR_INVALID_ARGUMENT;
     }
+    tuned_apply(&opt, true, csr->num_edges, (int64_t)csr->num_u + csr->num_l);
     bfc_graph *h = new (std::nothrow) bfc_graph();
     if (!h) { bfc::set_last_error("host allocation failed"); return BFC_ERR_OUT_OF_MEMORY; }
     Graph *g = &h->g;
@@ -420,6 +460,7 @@ int bfc_autotune(bfc_graph *h, void *stream, int iters, bfc_options *chosen) {
     if (rc) return rc;
     rc = bfc::rebin_graph(g, s, bw, bt, bh);
     if (rc) return rc;
+    tuned_store(tuned_key(g->opt.orientation, g->num_graphs > 0, g->m, (int64_t)g->n), bw, bt, bh);
     if (chosen) *chosen = g->opt;
     return BFC_OK;
 }

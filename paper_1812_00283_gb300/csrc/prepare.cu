@@ -1105,7 +1105,10 @@ int prepare_graph(const bfc_csr *csr, const bfc_options *opt, cudaStream_t s, Gr
     // ---- dense-core hybrid (Algorithm 2 single graphs): the requested core
     // size, or (core_vertices = -1) as many vertices as starts heavier than
     // the CTA-hash bin, at most kCoreAutoMax
-    if (opt->core_vertices != 0 && opt->orientation == 0 && num_graphs == 0) {
+    // (an automatic core below 2 x kCoreAutoMinLayer vertices cannot hold
+    // both layers: nothing is launched for it)
+    if (opt->core_vertices != 0 && opt->orientation == 0 && num_graphs == 0 &&
+        !(core_auto && hred[2] < 2ull * kCoreAutoMinLayer)) {
         const int32_t k = core_auto ? (int32_t)std::min<unsigned long long>(hred[2], (unsigned long long)kCoreAutoMax)
                                     : opt->core_vertices;
         int rc = core_prepare(g, s, deg_star, k, core_auto);

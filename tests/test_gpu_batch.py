@@ -105,3 +105,32 @@ def test_batch_rejects_cross_graph_edge():
     with pytest.raises(BfcError) as ei:
         _prepare(b)
     assert ei.value.status == 2
+
+
+def test_tuned_bounds_kept_per_size_class():
+    # bfc_autotune keeps its choice for the size class; a later batch of the
+    # same class prepared with use_tuned gets the same bins as one prepared
+    # with the chosen bounds given explicitly, and counts exactly
+    from paper_1812_00283_gb300 import bfc
+    graphs = _batch_graphs(k=50, seed=3)
+    b = G.union_batch(graphs)
+    h, keep = _prepare(b)
+    try:
+        chosen = bfc.bfc_autotune(h, torch.cuda.current_stream().cuda_stream, 1)
+    finally:
+        bfc.bfc_release(h)
+    other = [G.relabel(g, 40 + i) for i, g in enumerate(graphs)]   # same sizes
+    b2 = G.union_batch(other)
+    h1, k1 = _prepare(b2, bfc.bfc_options_init(use_tuned=1))
+    h2, k2 = _prepare(b2, bfc.bfc_options_init(warp_max_work=chosen.warp_max_work,
+                                               team_max_work=chosen.team_max_work,
+                                               hash_max_work=chosen.hash_max_work))
+    try:
+        i1, i2 = bfc.bfc_graph_info(h1), bfc.bfc_graph_info(h2)
+        for key in ("warp_starts", "team_starts", "hash_starts", "dense_starts", "dense_items"):
+            assert i1[key] == i2[key], key
+        tot, _ = _count(h1, b2.num_graphs)
+    finally:
+        bfc.bfc_release(h1)
+        bfc.bfc_release(h2)
+    assert [int(x) for x in tot] == [oracle.vp(g)["total"] for g in other]
