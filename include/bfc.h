@@ -210,6 +210,19 @@ int bfc_count_vertices(bfc_graph *g, void *stream, uint64_t *per_u_dev, uint64_t
  * until bfc_release (BFC_ERR_OUT_OF_MEMORY if the pool cannot grow). */
 int bfc_count_edges(bfc_graph *g, void *stream, uint64_t *per_edge_dev, uint64_t *total_dev);
 
+/* ⋈_G by the pair formulation of Section 6.3 (Algorithm 6's wedge pairs,
+ * run in device memory instead of on disk): every wedge (x, v, w) of the
+ * prepared orientation becomes the key (x, w); a radix sort groups equal
+ * keys, and a run of c equal keys adds C(c, 2) (Lemma 1; each butterfly is
+ * counted by one pair, Lemma 4).  A second exact path beside the counter
+ * walk of bfc_count (which reads each end once, where this one writes and
+ * sorts 8·W bytes of keys).  Writes one uint64 to total_dev.  Takes 24·W
+ * bytes plus the sort's histograms from the library's pool and frees them,
+ * stream-ordered; no host synchronisation.  BFC_ERR_INVALID_ARGUMENT for a
+ * batch or for W >= 2^32 - 1 (the sort's offsets are 32-bit),
+ * BFC_ERR_OUT_OF_MEMORY if the pool cannot grow. */
+int bfc_count_pairs(bfc_graph *g, void *stream, uint64_t *total_dev);
+
 /* Steps a8 and a9 together: the outputs of bfc_count_vertices and
  * bfc_count_edges from ONE first walk and ONE second walk (Algorithm 4's
  * pass attributes to vertices and edges at once).  per_u_dev / per_l_dev may

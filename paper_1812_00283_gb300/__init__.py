@@ -107,6 +107,16 @@ class ButterflyGraph:
         return (pu[:self.num_u], pl[:self.num_l], pe[:self.num_edges],
                 int(self._total.item()) & ((1 << 64) - 1))
 
+    def count_pairs(self, stream=None) -> int:
+        """⋈_G by Section 6.3's pair formulation (sort of the wedge pairs)."""
+        import torch
+        out = torch.zeros(1, dtype=torch.int64, device=self.device)
+        sp, _ = _stream(stream)
+        bfc = _lib()
+        bfc.bfc_count_pairs(self._h, sp, out.data_ptr())
+        bfc.bfc_sync(self._h, sp)
+        return int(out.item()) & ((1 << 64) - 1)
+
     # -- derived statistics (Section 1) ----------------------------------------
     def caterpillars(self, stream=None) -> int:
         """Three-paths: Σ over edges (deg u − 1)(deg v − 1)."""

@@ -94,6 +94,7 @@ _SIGS = {
     "bfc_count_vertices": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "bfc_count_edges": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "bfc_count_all": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "bfc_count_pairs": (c_int, [c_void_p, c_void_p, c_void_p]),
     "bfc_sync": (c_int, [c_void_p, c_void_p]),
     "bfc_graph_info": (c_int, [c_void_p, ctypes.POINTER(bfc_info)]),
     "bfc_export": (c_int, [c_void_p, c_int, c_void_p, c_void_p]),
@@ -183,6 +184,10 @@ def bfc_count_edges(g: int, stream: int, per_edge_dev: int, total_dev: int | Non
 def bfc_count_all(g: int, stream: int, per_u_dev: int | None, per_l_dev: int | None,
                   per_edge_dev: int, total_dev: int | None):
     _check(_lib.bfc_count_all(g, stream, per_u_dev, per_l_dev, per_edge_dev, total_dev), "bfc_count_all")
+
+
+def bfc_count_pairs(g: int, stream: int, total_dev: int):
+    _check(_lib.bfc_count_pairs(g, stream, total_dev), "bfc_count_pairs")
 
 
 def bfc_sync(g: int, stream: int = 0):

@@ -194,6 +194,11 @@ size_t max_scan_tmp_elems(int64_t n);
 cudaError_t max_scan_inclusive(const int32_t *in, int32_t *out, int64_t n, int32_t *tmp,
                                cudaStream_t s);
 
+// The same for int64 (pairs formulation: run starts of up to 2^32 keys).
+size_t max_scan_i64_tmp_elems(int64_t n);
+cudaError_t max_scan_inclusive_i64(const int64_t *in, int64_t *out, int64_t n, int64_t *tmp,
+                                   cudaStream_t s);
+
 // Stable LSD radix sort of (uint64 key, int32 value) pairs on key bits
 // [begin_bit, end_bit).  Ping-pongs between (k0, v0) and (k1, v1); returns
 // 0 if the result is in (k0, v0), 1 if in (k1, v1).  `hist` needs

@@ -319,6 +319,13 @@ cudaError_t max_scan_inclusive(const int32_t *in, int32_t *out, int64_t n, int32
     return scan_impl<int32_t, OpMax, true>(in, out, n, tmp, s);
 }
 
+size_t max_scan_i64_tmp_elems(int64_t n) { return tmp_levels<int64_t>(n) + 1; }
+
+cudaError_t max_scan_inclusive_i64(const int64_t *in, int64_t *out, int64_t n, int64_t *tmp,
+                                   cudaStream_t s) {
+    return scan_impl<int64_t, OpMax, true>(in, out, n, tmp, s);
+}
+
 size_t radix_hist_elems(int64_t n) {
     int64_t ntiles = (n + kSortTile - 1) / kSortTile;
     if (ntiles < 1) ntiles = 1;
