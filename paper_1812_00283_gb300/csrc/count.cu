@@ -1183,9 +1183,12 @@ __global__ void k_gather_vertices(const unsigned long long *__restrict__ pv,
 
 // ⋈_e from the two G* slots of every edge: the U-side slots [m, 2m) hold
 // each edge once, in rows that are permutations of the caller's rows (so
-// the stores stay inside one row), then the L-side slots [0, m) add theirs.
-// Every edge id occurs once per side, so neither pass needs atomics; the
-// second runs after the first on the same stream.
+// the stores stay inside one row), then the L-side slots [0, m) add theirs,
+// at edge ids in no useful order.  Every edge id occurs once per side, so the
+// second pass needs no atomicity; it adds with reductions anyway, which the
+// L2 carries out without returning the old value to the SM, so no thread
+// waits on the scattered reads.  The second runs after the first on the same
+// stream.
 __global__ void k_edges_from_slots_u(const unsigned long long *__restrict__ pe_slot,
                                      const int32_t *__restrict__ eid, int64_t m, uint64_t *per_edge) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -1197,7 +1200,7 @@ __global__ void k_edges_from_slots_l(const unsigned long long *__restrict__ pe_s
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
         const unsigned long long x = pe_slot[i];
-        if (x) per_edge[__ldg(eid + i)] += x;
+        if (x) atomicAdd(reinterpret_cast<unsigned long long *>(per_edge) + __ldg(eid + i), x);
     }
 }
 
