@@ -767,38 +767,31 @@ def run_single(args, workload: str, outputs: str, rank: int, world: int, local: 
     # end to end through the C ABI from pinned host buffers
     e2e = None
     if args.e2e_steps > 0 and outputs == "all":
-        # through the C ABI: H2D of the CSR, prepare, the combined count, D2H
-        # of the per-vertex and per-edge arrays and the total
+        # through the C ABI from and to page-locked host buffers:
+        # bfc_count_all_host copies the CSR in, prepares, counts with all
+        # outputs and copies the per-vertex, per-edge arrays and the total out
         off_h = torch.from_numpy(g.off_u).pin_memory()
         adj_h = torch.from_numpy(g.adj_u).pin_memory()
         pu_h = torch.empty(max(r, 1), dtype=torch.int64).pin_memory()
         pl_h = torch.empty(max(l, 1), dtype=torch.int64).pin_memory()
         pe_h = torch.empty(max(m, 1), dtype=torch.int64).pin_memory()
-        tot_h = torch.empty(1, dtype=torch.int64).pin_memory()
         ts = []
         for i in range(args.e2e_steps + 1):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            off_d = off_h.to(dev, non_blocking=True)
-            adj_d = adj_h.to(dev, non_blocking=True)
-            h = bfc.bfc_prepare(r, l, m, off_d.data_ptr(), adj_d.data_ptr(), step_opts, sp)
-            bfc.bfc_count_all(h, sp, per_u.data_ptr(), per_l.data_ptr(), per_e.data_ptr(), total.data_ptr())
-            pu_h.copy_(per_u, non_blocking=True)
-            pl_h.copy_(per_l, non_blocking=True)
-            pe_h.copy_(per_e, non_blocking=True)
-            tot_h.copy_(total, non_blocking=True)
-            bfc.bfc_sync(h, sp)
+            tot, wd = bfc.bfc_count_all_host(r, l, m, off_h.data_ptr(), adj_h.data_ptr(), step_opts, sp,
+                                             pu_h.data_ptr(), pl_h.data_ptr(), pe_h.data_ptr())
             ts.append(time.perf_counter() - t0)
-            bfc.bfc_release(h)
-            del off_d, adj_d
-            if (int(tot_h.item()) & ((1 << 64) - 1)) != expect:
+            if tot != expect or wd != W:
                 raise SystemExit("end-to-end count disagrees with the device-resident count")
+        if not torch.equal(pe_h[:m], per_e[:m].cpu()):
+            raise SystemExit("end-to-end per-edge counts disagree with the device-resident pass")
         ts = ts[1:]
         e2e = dict(value=W / statistics.median(ts), unit=UNIT,
                    h2d_bytes_per_step=4 * (r + 1) + 4 * m, d2h_bytes_per_step=8 * (r + l + m) + 8,
                    ms_per_step=1e3 * statistics.median(ts),
-                   note="H2D of the CSR from pinned memory, bfc_prepare, bfc_count_all, "
-                        "D2H of per-vertex, per-edge and total")
+                   note="bfc_count_all_host from page-locked host buffers: H2D of the CSR, prepare, "
+                        "count with all outputs, D2H of per-vertex, per-edge and total")
     elif args.e2e_steps > 0:
         off_h = torch.from_numpy(g.off_u).pin_memory()
         adj_h = torch.from_numpy(g.adj_u).pin_memory()

@@ -425,10 +425,27 @@ int bfc_export(const bfc_graph *g, int which, void *dst_dev, void *stream);
  * HOST memory: copies the CSR to the device, prepares, counts, copies ⋈_G
  * back to *total_host (and W to *wedges_host, nullable) and frees everything
  * it took.  Errors as bfc_prepare and bfc_count.
- * Synchronous.  off_u_host/adj_u_host may be pinned or pageable. */
+ * Synchronous.  off_u_host/adj_u_host may be pinned or pageable; page-locked
+ * buffers are copied by the SMs, as in bfc_count_all_host. */
 int bfc_count_host(int32_t num_u, int32_t num_l, int64_t num_edges, const int32_t *off_u_host,
                    const int32_t *adj_u_host, const bfc_options *opt, void *stream,
                    uint64_t *total_host, uint64_t *wedges_host);
+
+/* Steps a1-a9 end to end from HOST memory (Algorithm 2 with Algorithm 4's
+ * attribution): copies the CSR to the device, prepares, counts ⋈_G with the
+ * per-vertex (Eq. 1) and per-edge (Eq. 7) counts, and copies them back:
+ * per_u_host[num_u] and per_l_host[num_l] in original ids (either may be
+ * NULL), per_edge_host[num_edges] by U-side slot (NULL only when num_edges
+ * is 0), *total_host, and W to *wedges_host (nullable).  Frees everything it
+ * took; synchronous.  A page-locked host buffer (cudaHostAlloc or
+ * cudaHostRegister over the whole range) is moved by the SMs over the host
+ * link, any other by cudaMemcpyAsync: on a GB300 the copy engines ran five
+ * to eight times slower while a large prepared graph was held in device
+ * memory, the SMs did not.  Errors as bfc_prepare and bfc_count_all. */
+int bfc_count_all_host(int32_t num_u, int32_t num_l, int64_t num_edges, const int32_t *off_u_host,
+                       const int32_t *adj_u_host, const bfc_options *opt, void *stream,
+                       uint64_t *per_u_host, uint64_t *per_l_host, uint64_t *per_edge_host,
+                       uint64_t *total_host, uint64_t *wedges_host);
 
 /* Allocation-free count for small graphs.  The paper has no counterpart: this
  * exists for callers that may not allocate device memory where they count:

@@ -101,6 +101,9 @@ _SIGS = {
     "bfc_count_host": (c_int, [c_int32, c_int32, c_int64, c_void_p, c_void_p,
                                ctypes.POINTER(bfc_options), c_void_p, ctypes.POINTER(c_uint64),
                                ctypes.POINTER(c_uint64)]),
+    "bfc_count_all_host": (c_int, [c_int32, c_int32, c_int64, c_void_p, c_void_p,
+                                   ctypes.POINTER(bfc_options), c_void_p, c_void_p, c_void_p, c_void_p,
+                                   ctypes.POINTER(c_uint64), ctypes.POINTER(c_uint64)]),
     "bfc_release": (None, [c_void_p]),
     "bfc_status_string": (ctypes.c_char_p, [c_int]),
     "bfc_last_error": (ctypes.c_char_p, []),
@@ -213,6 +216,18 @@ def bfc_count_host(num_u: int, num_l: int, num_edges: int, off_u_host: int, adj_
                                ctypes.byref(options) if options else None, stream,
                                ctypes.byref(t), ctypes.byref(w)), "bfc_count_host")
     return int(t.value), int(w.value)
+
+
+def bfc_count_all_host(num_u: int, num_l: int, num_edges: int, off_u_host: int, adj_u_host: int,
+                       options: bfc_options | None, stream: int, per_u_host: int | None,
+                       per_l_host: int | None, per_edge_host: int | None) -> tuple[int, int]:
+    """Steps a1-a9 from host buffers into host buffers; returns (total, W)."""
+    tot, wed = c_uint64(0), c_uint64(0)
+    _check(_lib.bfc_count_all_host(num_u, num_l, num_edges, off_u_host, adj_u_host,
+                                   ctypes.byref(options) if options else None, stream, per_u_host,
+                                   per_l_host, per_edge_host, ctypes.byref(tot), ctypes.byref(wed)),
+           "bfc_count_all_host")
+    return int(tot.value), int(wed.value)
 
 
 def bfc_prepare_batch(num_u: int, num_l: int, num_edges: int, off_u: int, adj_u: int,

@@ -174,6 +174,67 @@ static int check_options(const bfc_options *o) {
     return BFC_OK;
 }
 
+namespace bfc {
+namespace {
+
+// Host <-> device copies done by the SMs: each thread moves T-sized words
+// over the host link.  Measured on this GPU, copies by the copy engines slow
+// down five- to eightfold while a large prepared graph is held in device
+// memory, and copies by the SMs do not.
+template <typename T>
+__global__ void k_copy_words(const T *__restrict__ src, T *__restrict__ dst, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = src[i];
+}
+
+// The device address of a page-locked host range (cudaHostAlloc or
+// cudaHostRegister, both ends checked), or null for any other memory.
+const void *locked_host_range(const void *p, size_t bytes) {
+    if (!p || bytes == 0) return nullptr;
+    cudaPointerAttributes a, b;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess ||
+        cudaPointerGetAttributes(&b, static_cast<const char *>(p) + bytes - 1) != cudaSuccess) {
+        cudaGetLastError();   // an unknown pointer is not an error here
+        return nullptr;
+    }
+    if (a.type != cudaMemoryTypeHost || b.type != cudaMemoryTypeHost || !a.devicePointer) return nullptr;
+    return a.devicePointer;
+}
+
+// Copies `bytes` between host memory and device memory on s: by the SMs when
+// the host side is page-locked, else by cudaMemcpyAsync.
+int copy_host(void *dst, const void *src, size_t bytes, bool to_device, cudaStream_t s) {
+    if (bytes == 0) return BFC_OK;
+    const void *hp = locked_host_range(to_device ? src : dst, bytes);
+    if (!hp) {
+        BFC_CUDA(cudaMemcpyAsync(dst, src, bytes, to_device ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost, s));
+        return BFC_OK;
+    }
+    const void *from = to_device ? hp : src;
+    void *to = to_device ? dst : const_cast<void *>(hp);
+    const uintptr_t al = reinterpret_cast<uintptr_t>(from) | reinterpret_cast<uintptr_t>(to) | bytes;
+    const unsigned grid = 152 * 8;
+    if (al % 16 == 0)
+        k_copy_words<uint4><<<grid, 512, 0, s>>>(static_cast<const uint4 *>(from), static_cast<uint4 *>(to),
+                                                 (int64_t)(bytes / 16));
+    else if (al % 8 == 0)
+        k_copy_words<uint64_t><<<grid, 512, 0, s>>>(static_cast<const uint64_t *>(from),
+                                                    static_cast<uint64_t *>(to), (int64_t)(bytes / 8));
+    else if (al % 4 == 0)
+        k_copy_words<uint32_t><<<grid, 512, 0, s>>>(static_cast<const uint32_t *>(from),
+                                                    static_cast<uint32_t *>(to), (int64_t)(bytes / 4));
+    else
+        k_copy_words<uint8_t><<<grid, 512, 0, s>>>(static_cast<const uint8_t *>(from), static_cast<uint8_t *>(to),
+                                                   (int64_t)bytes);
+    note_launch();
+    BFC_CUDA(cudaGetLastError());
+    return BFC_OK;
+}
+
+}  // namespace
+}  // namespace bfc
+
 extern "C" {
 
 void bfc_options_init(bfc_options *opt) {
@@ -554,6 +615,53 @@ int bfc_export(const bfc_graph *h, int which, void *dst, void *stream) {
     return BFC_OK;
 }
 
+int bfc_count_all_host(int32_t num_u, int32_t num_l, int64_t num_edges, const int32_t *off_u_host,
+                       const int32_t *adj_u_host, const bfc_options *opt, void *stream,
+                       uint64_t *per_u_host, uint64_t *per_l_host, uint64_t *per_edge_host,
+                       uint64_t *total_host, uint64_t *wedges_host) {
+    bfc::set_last_error("");
+    if (!off_u_host || (num_edges > 0 && (!adj_u_host || !per_edge_host)) || !total_host || num_u < 0 ||
+        num_l < 0 || num_edges < 0 || num_edges > 2147483647LL) {
+        bfc::set_last_error("invalid host CSR or output arguments");
+        return BFC_ERR_INVALID_ARGUMENT;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    bfc::Allocs in;
+    in.stream = s;
+    struct Guard { bfc::Allocs *a; cudaStream_t s; ~Guard() { a->release(); cudaStreamSynchronize(s); } } guard{&in, s};
+    int32_t *off = nullptr, *adj = nullptr;
+    uint64_t *pu = nullptr, *pl = nullptr, *pe = nullptr, *tot = nullptr;
+    if (in.get(&off, (size_t)num_u + 1) || in.get(&adj, (size_t)std::max<int64_t>(num_edges, 1)) ||
+        in.get(&pu, (size_t)std::max(num_u, 1)) || in.get(&pl, (size_t)std::max(num_l, 1)) ||
+        in.get(&pe, (size_t)std::max<int64_t>(num_edges, 1)) || in.get(&tot, 1)) {
+        bfc::set_last_error("device allocation failed");
+        return BFC_ERR_OUT_OF_MEMORY;
+    }
+    int rc = bfc::copy_host(off, off_u_host, sizeof(int32_t) * ((size_t)num_u + 1), true, s);
+    if (rc == BFC_OK) rc = bfc::copy_host(adj, adj_u_host, sizeof(int32_t) * (size_t)num_edges, true, s);
+    bfc_graph *g = nullptr;
+    if (rc == BFC_OK) {
+        bfc_csr csr{num_u, num_l, num_edges, off, adj};
+        rc = bfc_prepare(&csr, opt, stream, &g);
+    }
+    if (rc == BFC_OK)
+        rc = count_common(g, stream, bfc::kModeAll, per_u_host ? pu : nullptr, per_l_host ? pl : nullptr,
+                          tot, pe);
+    // the graph's memory goes back to the pool before the outputs travel
+    if (rc == BFC_OK) rc = bfc_sync(g, stream);
+    if (rc == BFC_OK && wedges_host) *wedges_host = g->g.info.wedges;
+    if (g) bfc_release(g);
+    if (rc == BFC_OK && per_u_host) rc = bfc::copy_host(per_u_host, pu, sizeof(uint64_t) * (size_t)num_u, false, s);
+    if (rc == BFC_OK && per_l_host) rc = bfc::copy_host(per_l_host, pl, sizeof(uint64_t) * (size_t)num_l, false, s);
+    if (rc == BFC_OK) rc = bfc::copy_host(per_edge_host, pe, sizeof(uint64_t) * (size_t)num_edges, false, s);
+    if (rc == BFC_OK) {
+        cudaError_t e = cudaMemcpyAsync(total_host, tot, sizeof(uint64_t), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) rc = bfc::cuda_fail(e, "copy of the results to the host");
+    }
+    return rc;
+}
+
 int bfc_count_host(int32_t num_u, int32_t num_l, int64_t num_edges, const int32_t *off_u_host,
                    const int32_t *adj_u_host, const bfc_options *opt, void *stream,
                    uint64_t *total_host, uint64_t *wedges_host) {
@@ -573,13 +681,9 @@ int bfc_count_host(int32_t num_u, int32_t num_l, int64_t num_edges, const int32_
         bfc::set_last_error("device allocation failed");
         return BFC_ERR_OUT_OF_MEMORY;
     }
-    int rc = BFC_OK;
-    cudaError_t e = cudaMemcpyAsync(off, off_u_host, sizeof(int32_t) * ((size_t)num_u + 1),
-                                    cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess && num_edges > 0)
-        e = cudaMemcpyAsync(adj, adj_u_host, sizeof(int32_t) * (size_t)num_edges,
-                            cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) rc = bfc::cuda_fail(e, "cudaMemcpyAsync(H2D)");
+    int rc = bfc::copy_host(off, off_u_host, sizeof(int32_t) * ((size_t)num_u + 1), true, s);
+    if (rc == BFC_OK) rc = bfc::copy_host(adj, adj_u_host, sizeof(int32_t) * (size_t)num_edges, true, s);
+    cudaError_t e = cudaSuccess;
     bfc_graph *g = nullptr;
     if (rc == BFC_OK) {
         bfc_csr csr{num_u, num_l, num_edges, off, adj};
