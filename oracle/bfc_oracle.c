@@ -772,3 +772,32 @@ int orc_vp_core_split(int32_t r, int32_t l, const int32_t *off, const int32_t *a
     free(p); free(a); free(b); graph_free(&g);
     return 0;
 }
+
+uint64_t orc_splitmix64(uint64_t seed, uint64_t k) {
+    uint64_t z = seed + k * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+int orc_sparsify(int32_t r, int32_t l, const int32_t *off, const int32_t *adj, uint64_t seed,
+                 uint64_t j, uint64_t threshold, int keep_all, int32_t *out_off, int32_t *out_adj,
+                 int64_t *kept) {
+    graph_t g;
+    int rc = graph_build(r, l, off, adj, &g);   /* checks the CSR */
+    if (rc) return rc;
+    graph_free(&g);
+    const uint64_t m = (uint64_t)off[r];
+    int64_t k = 0;
+    out_off[0] = 0;
+    for (int32_t u = 0; u < r; ++u) {
+        for (int32_t e = off[u]; e < off[u + 1]; ++e) {
+            /* one draw per (sample, edge): the edge survives with probability p */
+            if (keep_all || orc_splitmix64(seed, j * m + (uint64_t)e + 1) < threshold)
+                out_adj[k++] = adj[e];
+        }
+        out_off[u + 1] = (int32_t)k;
+    }
+    *kept = k;
+    return 0;
+}

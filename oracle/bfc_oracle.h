@@ -142,6 +142,23 @@ int orc_pairs_total(int32_t r, int32_t l, const int32_t *off, const int32_t *adj
 int orc_caterpillars(int32_t r, int32_t l, const int32_t *off, const int32_t *adj,
                      uint64_t *caterpillars);
 
+/* SplitMix64 (Steele, Lea and Flood, "Fast Splittable Pseudorandom Number
+ * Generators", OOPSLA 2014): the k-th output (k >= 1) of the generator seeded
+ * with `seed`, i.e. its mixing function applied to seed + k * 0x9E3779B97F4A7C15. */
+uint64_t orc_splitmix64(uint64_t seed, uint64_t k);
+
+/* Edge sparsification for approximate counting (Section 7: the exact counter
+ * is the inner block of a sampling estimator; each sample is a graph in which
+ * every edge is kept independently with probability p).  Sample j keeps the
+ * edge at U-side slot e iff orc_splitmix64(seed, j*m + e + 1) < threshold,
+ * threshold = floor(p * 2^64) given by the caller; keep_all = 1 keeps every
+ * edge (p = 1).  Writes the kept edges as a CSR over the same vertex sets:
+ * out_off[r+1], out_adj[m] (caller-owned; slots beyond *kept untouched),
+ * *kept = edges kept. */
+int orc_sparsify(int32_t r, int32_t l, const int32_t *off, const int32_t *adj, uint64_t seed,
+                 uint64_t j, uint64_t threshold, int keep_all, int32_t *out_off, int32_t *out_adj,
+                 int64_t *kept);
+
 #ifdef __cplusplus
 }
 #endif

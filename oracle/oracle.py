@@ -15,6 +15,8 @@ import itertools
 import os
 import subprocess
 import threading
+import types
+from fractions import Fraction
 
 import numpy as np
 
@@ -68,11 +70,15 @@ def _load():
                 "orc_vp_chunked": [c.c_int32, c.c_int32, _i32p, _i32p, c.c_int32, _u64p],
                 "orc_vp_core_split": [c.c_int32, c.c_int32, _i32p, _i32p, c.c_int32, _u64p, _u64p, _u64p,
                                       _u64p],
+                "orc_sparsify": [c.c_int32, c.c_int32, _i32p, _i32p, c.c_uint64, c.c_uint64,
+                                 c.c_uint64, c.c_int, _i32p, _i32p, _i64p],
             }
             for name, args in sig.items():
                 f = getattr(lib, name)
                 f.argtypes = args
                 f.restype = c.c_int
+            lib.orc_splitmix64.argtypes = [c.c_uint64, c.c_uint64]
+            lib.orc_splitmix64.restype = c.c_uint64
             _lib = lib
     return _lib
 
@@ -307,3 +313,65 @@ def enumerate_butterflies(g) -> dict:
                 for e in es:
                     pe[slot[e]] += 1
     return dict(total=total, pv_u=pv_u, pv_l=pv_l, pe=pe)
+
+
+# ---------------------------------------------------------------------------
+# Approximate counting by edge sparsification (Section 7)
+# ---------------------------------------------------------------------------
+
+def splitmix64(seed: int, k: int) -> int:
+    """The k-th output (k >= 1) of SplitMix64 seeded with `seed` (C routine)."""
+    return int(_load().orc_splitmix64(seed & (2**64 - 1), k & (2**64 - 1)))
+
+
+def keep_threshold(p: float) -> tuple[int, bool]:
+    """(floor(p * 2^64), keep_all) for a keep probability 0 < p <= 1, in exact
+    rational arithmetic."""
+    if not (0.0 < p <= 1.0):
+        raise ValueError("keep probability must lie in (0, 1]")
+    if p == 1.0:
+        return 0, True
+    return int(Fraction(p) * 2**64), False
+
+
+def sparsify(g, p: float, seed: int, j: int):
+    """Sample j of graph g: every edge kept independently with probability p
+    (the keep rule of ``orc_sparsify``).  Returns a graph with the same vertex
+    sets and the kept edges (in their original order)."""
+    off, adj = _csr(g)
+    t, keep_all = keep_threshold(p)
+    m = max(g.num_edges, 1)
+    oo = np.zeros(g.num_u + 1, dtype=np.int32)
+    oa = np.zeros(m, dtype=np.int32)
+    kept = np.zeros(1, dtype=np.int64)
+    _check(_load().orc_sparsify(g.num_u, g.num_l, _p(off, _i32p), _p(adj, _i32p), seed & (2**64 - 1),
+                                int(j), t, int(keep_all), _p(oo, _i32p), _p(oa, _i32p),
+                                _p(kept, _i64p)), "sparsify")
+    k = int(kept[0])
+    return types.SimpleNamespace(num_u=g.num_u, num_l=g.num_l, num_edges=k, off_u=oo,
+                                 adj_u=oa[:k].copy())
+
+
+def sparsified_estimate(g, p: float, seed: int, samples: int, threads: int = 0) -> dict:
+    """The sampling estimator with the exact counter as its inner block: each
+    of `samples` sparsified graphs (sample j = ``sparsify(g, p, seed, j)``) is
+    counted by Algorithm 2; a butterfly survives a sample iff its four edges
+    do (probability p^4), so estimate = Σ_j ⋈(G_j) / (samples · p^4).
+    std_error = the sample standard deviation of ⋈(G_j) / p^4 over
+    sqrt(samples) (NaN for one sample)."""
+    if samples < 1:
+        raise ValueError("at least one sample")
+    counts, edges = [], []
+    for j in range(samples):
+        h = sparsify(g, p, seed, j)
+        counts.append(vp(h, threads=threads)["total"])
+        edges.append(h.num_edges)
+    p4 = p ** 4
+    est = float(sum(counts)) / (samples * p4)
+    if samples > 1:
+        mean = sum(counts) / samples
+        var = sum((c - mean) ** 2 for c in counts) / (samples - 1)
+        se = (var / samples) ** 0.5 / p4
+    else:
+        se = float("nan")
+    return dict(counts=counts, edges=edges, estimate=est, std_error=se)
