@@ -609,6 +609,12 @@ def main():
     ap.add_argument("--core-vertices", type=int, default=None,
                     help="total counts: the top-K priority core counted by the tensor-core product "
                          "(default: the library's automatic choice)")
+    ap.add_argument("--sparsify-samples", type=int, default=16,
+                    help="approximate counting on the 20M-edge power-law graph: samples per estimate "
+                         "(0 = skip)")
+    ap.add_argument("--sparsify-p", type=float, nargs="+", default=[0.1, 0.05, 0.2],
+                    help="keep probabilities of the approximate-counting runs (the first is checked "
+                         "against the oracle)")
     ap.add_argument("--batch-graphs", type=int, default=4096)
     ap.add_argument("--serve-pool", type=int, default=256)
     ap.add_argument("--serve-requests", type=int, default=10000)
@@ -644,10 +650,99 @@ def main():
         out["powerlaw_20m"]["config"] = {k: h["config"][k] for k in (
             "workload", "wedges_per_step", "butterflies", "prepare_ms_median", "count_ms_median",
             "count_only_wedges_per_s", "outputs", "oracle_agrees")}
+        if args.sparsify_samples > 0:
+            out["sparsified"] = run_sparsified(args, rank, dev, int(h["config"]["butterflies"]))
     if rank == 0:
         print(json.dumps(out), flush=True)
     dist_done(world)
     return 0
+
+
+def run_sparsified(args, rank: int, dev, exact: int, seed: int = 7) -> dict:
+    """Section 7's estimator with this counter as its inner block, on the
+    20M-edge power-law graph: args.sparsify_samples edge-sparsified copies
+    (each edge kept with probability p) sampled, prepared and counted as one
+    batch, then the estimate, per call of bfc_estimate_sparsified (inputs
+    resident, L2 flushed between calls); the count launch of the prepared
+    samples timed alone for its roofline."""
+    import torch
+
+    from paper_1812_00283_gb300 import bfc
+
+    g = make_graph("powerlaw_20m", rank, dev)
+    off = torch.from_numpy(g.off_u).to(dev)
+    adj = torch.from_numpy(g.adj_u).to(dev)
+    r, l, m = g.num_u, g.num_l, g.num_edges
+    stream = torch.cuda.current_stream()
+    sp = stream.cuda_stream
+    k = args.sparsify_samples
+    counts = torch.zeros(k, dtype=torch.int64, device=dev)
+    est = torch.zeros(2, dtype=torch.float64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    peaks = measured_peaks()
+    steps = max(1, min(args.steps, 5))
+    runs = []
+    for p in args.sparsify_p:
+        def call(ev=None):
+            if ev:
+                ev[0].record(stream)
+            bfc.bfc_estimate_sparsified(r, l, m, off.data_ptr(), adj.data_ptr(), p, seed, k, None, sp,
+                                        counts.data_ptr(), est.data_ptr())
+            if ev:
+                ev[1].record(stream)
+        for _ in range(args.warmup):
+            flush.fill_(1)
+            call()
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(steps)]
+        for i in range(steps):
+            flush.fill_(i & 0xff)
+            call(evs[i])
+        torch.cuda.synchronize()
+        ms = statistics.median(e[0].elapsed_time(e[1]) for e in evs)
+        e, se = est.cpu().tolist()
+        # the count launch over the prepared samples, alone
+        h = bfc.bfc_prepare_sparsified(r, l, m, off.data_ptr(), adj.data_ptr(), p, seed, k, None, sp)
+        info = bfc.bfc_graph_info(h)
+        tot2 = torch.zeros(k, dtype=torch.int64, device=dev)
+        bfc.bfc_count_batch(h, sp, tot2.data_ptr())
+        cev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(3)]
+        for c in cev:
+            flush.fill_(2)
+            c[0].record(stream)
+            bfc.bfc_count_batch(h, sp, tot2.data_ptr())
+            c[1].record(stream)
+        bfc.bfc_sync(h, sp)
+        bfc.bfc_release(h)
+        if not torch.equal(tot2, counts):
+            raise SystemExit("sampled counts differ between the one-call and the prepared path")
+        if not runs:
+            first = counts.clone()
+        cnt_ms = statistics.median(c[0].elapsed_time(c[1]) for c in cev)
+        Ws, ms_, ns = int(info["wedges"]), int(info["num_edges"]), int(info["num_u"]) + int(info["num_l"])
+        B = algorithmic_bytes(Ws, ms_, ns, "total")
+        runs.append(dict(p=p, samples=k, ms_per_estimate=ms, samples_per_s=k / (ms / 1e3),
+                         sampled_wedges_per_s=Ws / (ms / 1e3), sampled_edges=ms_, sampled_wedges=Ws,
+                         estimate=e, std_error=se, rel_error=(e - exact) / exact if exact else None,
+                         count_ms=cnt_ms,
+                         count_roofline=dict(bound="hbm", achieved=B / (cnt_ms / 1e3) / 1e9,
+                                             peak=peaks["hbm_gbs"], unit="GB/s",
+                                             frac=B / (cnt_ms / 1e3) / 1e9 / peaks["hbm_gbs"],
+                                             kernel="k_count (bfc_count_batch over the samples)",
+                                             algorithmic_bytes_per_launch=B)))
+    out = dict(workload="powerlaw_20m", exact=exact, seed=seed, runs=runs,
+               note="bfc_estimate_sparsified: sampling (SplitMix64 per sample and edge), prepare of "
+                    "the samples as one batch, one count launch, estimate; median of "
+                    f"{steps} calls after {args.warmup} warm-up calls, L2 flushed between calls")
+    if rank == 0 and not args.no_cpu_baseline and runs:
+        import oracle
+        p = args.sparsify_p[0]
+        t0 = time.perf_counter()
+        ref = oracle.vp(oracle.sparsify(g, p, seed, 0), threads=os.cpu_count() or 1)
+        dt = time.perf_counter() - t0
+        out["cpu_baseline"] = dict(value=1e3 * dt, unit="ms per sample", cores=os.cpu_count() or 1,
+                                   kind="oracle", sample=f"sample 0 of p={p}: oracle sparsify + Algorithm 2")
+        out["oracle_agrees"] = ref["total"] == int(first.cpu().numpy().view("uint64")[0])
+    return out
 
 
 def run_single(args, workload: str, outputs: str, rank: int, world: int, local: int, dev,

@@ -331,6 +331,54 @@ int bfc_batch_plan_run(bfc_batch_plan *plan, const int32_t *off_u_dev, const int
  * for it).  NULL is ignored. */
 void bfc_batch_plan_destroy(bfc_batch_plan *plan);
 
+/* ---- Approximate counting by edge sparsification --------------------------
+ * Section 7 uses the exact counter as the inner block of a sampling
+ * estimator: each sample is a graph in which every edge of G is kept
+ * independently with probability p, and is counted exactly.  A butterfly
+ * survives a sample iff its four edges do, so E[⋈(G_j)] = p^4 · ⋈(G) and
+ *     estimate = Σ_j ⋈(G_j) / (num_samples · p^4).
+ * Keep rule: sample j (0 <= j < num_samples) keeps the edge at U-side slot e
+ * iff the (j·num_edges + e + 1)-th output of SplitMix64 (Steele, Lea and
+ * Flood, OOPSLA 2014) seeded with `seed` is below floor(p · 2^64); p = 1
+ * keeps every edge.  The counts of the samples are exact (uint64); the
+ * number of samples an (ε, δ) guarantee needs is the caller's choice.
+ *
+ * bfc_prepare_sparsified draws the samples from the U-side CSR
+ * (off_u_dev[num_u + 1], adj_u_dev[num_edges], device, int32, read only)
+ * and prepares them as ONE batch (bfc_prepare_batch) of num_samples
+ * disjoint graphs: sample j has U vertices [j·num_u, (j+1)·num_u) and L
+ * vertices [j·num_l, (j+1)·num_l) of the prepared union.  Count it with
+ * bfc_count_batch (totals_dev[j] = ⋈(G_j)); bfc_batch_wedges and
+ * bfc_graph_info describe the samples.  sample_edges_dev (nullable, device,
+ * uint64[num_samples]) receives the edges each sample kept.
+ * Requires 0 < p <= 1, num_samples >= 1, num_samples · (num_u + num_l) below
+ * 2^31 - 1 and at most 2^31 - 1 kept edges over all samples
+ * (BFC_ERR_INVALID_ARGUMENT otherwise); offsets that are not a CSR of
+ * num_edges slots, or L ids outside [0, num_l), give BFC_ERR_INVALID_GRAPH
+ * before any sample is written.  Synchronises `stream`; the sampled union is
+ * transient (freed in stream order once prepared). */
+int bfc_prepare_sparsified(int32_t num_u, int32_t num_l, int64_t num_edges, const int32_t *off_u_dev,
+                           const int32_t *adj_u_dev, double p, uint64_t seed, int32_t num_samples,
+                           const bfc_options *opt, void *stream, uint64_t *sample_edges_dev,
+                           bfc_graph **out);
+
+/* The estimator from the samples' exact counts (sample_counts_dev,
+ * uint64[num_samples], device): estimate_dev[0] = Σ c_j / (num_samples ·
+ * p^4), estimate_dev[1] = its standard error, the sample standard deviation
+ * of c_j / p^4 over sqrt(num_samples) (NaN for one sample).  estimate_dev is
+ * double[2], device, caller-owned.  Asynchronous (one kernel on `stream`). */
+int bfc_sparsified_estimate(const uint64_t *sample_counts_dev, int32_t num_samples, double p,
+                            void *stream, double *estimate_dev);
+
+/* All of it in one call: bfc_prepare_sparsified, bfc_count_batch into
+ * sample_counts_dev (uint64[num_samples], device, caller-owned),
+ * bfc_sparsified_estimate into estimate_dev (double[2], device, nullable),
+ * then the prepared samples are released.  Synchronises `stream`. */
+int bfc_estimate_sparsified(int32_t num_u, int32_t num_l, int64_t num_edges, const int32_t *off_u_dev,
+                            const int32_t *adj_u_dev, double p, uint64_t seed, int32_t num_samples,
+                            const bfc_options *opt, void *stream, uint64_t *sample_counts_dev,
+                            double *estimate_dev);
+
 /* ---- Serving: continuous batching of counting requests -------------------
  * Requests (one graph each, U-side CSR in HOST memory) may arrive at any time
  * from any thread.  Worker threads (one CUDA stream each) take the oldest

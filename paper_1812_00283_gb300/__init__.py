@@ -9,7 +9,7 @@ from __future__ import annotations
 
 import importlib
 
-__all__ = ["bfc", "BfcError", "ButterflyGraph", "count_butterflies"]
+__all__ = ["bfc", "BfcError", "ButterflyGraph", "count_butterflies", "estimate_butterflies"]
 
 
 def __getattr__(name):
@@ -187,3 +187,25 @@ def count_butterflies(off_u, adj_u, num_u: int, num_l: int, options=None) -> int
         return g.count()
     finally:
         g.release()
+
+
+def estimate_butterflies(off_u, adj_u, num_u: int, num_l: int, p: float, num_samples: int,
+                         seed: int = 0, options=None, stream=None) -> dict:
+    """Approximate ⋈_G from num_samples edge-sparsified copies (each edge kept
+    with probability p), each counted exactly (Section 7's estimator with this
+    counter as its inner block).  Returns the samples' exact counts (uint64
+    as an int64 CUDA tensor), the estimate and its standard error."""
+    import torch
+    if off_u.dtype != torch.int32 or adj_u.dtype != torch.int32:
+        raise TypeError("off_u and adj_u must be int32")
+    if not (off_u.is_cuda and adj_u.is_cuda):
+        raise TypeError("off_u and adj_u must be CUDA tensors")
+    off_u, adj_u = off_u.contiguous(), adj_u.contiguous()
+    sp, s = _stream(stream)
+    counts = torch.zeros(int(num_samples), dtype=torch.int64, device=off_u.device)
+    est = torch.zeros(2, dtype=torch.float64, device=off_u.device)
+    _lib().bfc_estimate_sparsified(int(num_u), int(num_l), int(adj_u.numel()), off_u.data_ptr(),
+                                   adj_u.data_ptr() if adj_u.numel() else 0, p, int(seed),
+                                   int(num_samples), options, sp, counts.data_ptr(), est.data_ptr())
+    e = est.cpu().tolist()
+    return dict(counts=counts, estimate=e[0], std_error=e[1])

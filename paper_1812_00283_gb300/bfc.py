@@ -133,6 +133,13 @@ _SIGS = {
     "bfc_server_destroy": (None, [c_void_p]),
     "bfc_count_small_noalloc": (c_int, [c_int32, c_int32, c_int64, c_void_p, c_void_p, c_void_p,
                                         c_void_p, c_void_p]),
+    "bfc_prepare_sparsified": (c_int, [c_int32, c_int32, c_int64, c_void_p, c_void_p, ctypes.c_double,
+                                       c_uint64, c_int32, ctypes.POINTER(bfc_options), c_void_p, c_void_p,
+                                       ctypes.POINTER(c_void_p)]),
+    "bfc_sparsified_estimate": (c_int, [c_void_p, c_int32, ctypes.c_double, c_void_p, c_void_p]),
+    "bfc_estimate_sparsified": (c_int, [c_int32, c_int32, c_int64, c_void_p, c_void_p, ctypes.c_double,
+                                        c_uint64, c_int32, ctypes.POINTER(bfc_options), c_void_p, c_void_p,
+                                        c_void_p]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -269,6 +276,34 @@ def bfc_count_batch(g: int, stream: int, totals_dev: int, total_dev: int | None 
 
 def bfc_batch_wedges(g: int, stream: int, wedges_dev: int):
     _check(_lib.bfc_batch_wedges(g, stream, wedges_dev), "bfc_batch_wedges")
+
+
+def bfc_prepare_sparsified(num_u: int, num_l: int, num_edges: int, off_u: int, adj_u: int, p: float,
+                           seed: int, num_samples: int, options: bfc_options | None = None,
+                           stream: int = 0, sample_edges_dev: int | None = None) -> int:
+    """num_samples edge-sparsified copies of a graph (keep probability p),
+    prepared as one batch; returns a graph handle for bfc_count_batch."""
+    h = c_void_p()
+    _check(_lib.bfc_prepare_sparsified(num_u, num_l, num_edges, off_u, adj_u, float(p),
+                                       seed & 0xFFFFFFFFFFFFFFFF, num_samples,
+                                       ctypes.byref(options) if options else None, stream,
+                                       sample_edges_dev, ctypes.byref(h)), "bfc_prepare_sparsified")
+    return h.value
+
+
+def bfc_sparsified_estimate(sample_counts_dev: int, num_samples: int, p: float, stream: int,
+                            estimate_dev: int):
+    _check(_lib.bfc_sparsified_estimate(sample_counts_dev, num_samples, float(p), stream, estimate_dev),
+           "bfc_sparsified_estimate")
+
+
+def bfc_estimate_sparsified(num_u: int, num_l: int, num_edges: int, off_u: int, adj_u: int, p: float,
+                            seed: int, num_samples: int, options: bfc_options | None, stream: int,
+                            sample_counts_dev: int, estimate_dev: int | None = None):
+    _check(_lib.bfc_estimate_sparsified(num_u, num_l, num_edges, off_u, adj_u, float(p),
+                                        seed & 0xFFFFFFFFFFFFFFFF, num_samples,
+                                        ctypes.byref(options) if options else None, stream,
+                                        sample_counts_dev, estimate_dev), "bfc_estimate_sparsified")
 
 
 def bfc_autotune(g: int, stream: int = 0, iters: int = 2) -> bfc_options:

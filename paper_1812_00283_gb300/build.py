@@ -17,7 +17,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libbfc.so")
 SOURCES = ["api.cu", "prepare.cu", "count.cu", "scan_sort.cu", "noalloc.cu", "server.cu", "microbench.cu",
-           "derived.cu", "core.cu", "pairs.cu"]
+           "derived.cu", "core.cu", "pairs.cu", "sparsify.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -143,6 +143,8 @@ struct Graph {
     // chunk-boundary table: for vertex v of G*, entry c is the position in
     // N(v) of the first neighbour whose rank in its layer is >= c * kChunkUnit
     int32_t *coff = nullptr;
+    int64_t *coff_start = nullptr;   // a batch's table while it is built: first entry of each vertex
+    int32_t *ctb = nullptr;          // a batch's table: first entry of each slot's middle (-1: none)
     int32_t coff_u1 = 0;   // entries per L vertex (its neighbours are U vertices)
     int32_t coff_l1 = 0;   // entries per U vertex
     // batch of graphs prepared as one disjoint union

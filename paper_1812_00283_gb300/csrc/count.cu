@@ -62,6 +62,7 @@ struct CountParams {
     unsigned long long *pv;            // [n] in G* ids
     unsigned long long *pe;            // [2m] by G* slot (each edge has two)
     const int32_t *__restrict__ coff;  // chunk-boundary table (nullable; Algorithm 2 only)
+    const int32_t *__restrict__ ctb;   // a batch's table: first entry of each slot's middle, -1 if none (else null)
     const int32_t *__restrict__ gstar; // graph of each G* vertex (batch mode)
     const int32_t *__restrict__ vbase; // first id of x's graph in x's layer (batch mode)
     const int32_t *__restrict__ vend;  // one past the last id of x's graph in x's layer (batch mode)
@@ -366,7 +367,7 @@ __device__ __forceinline__ void batch_runs(const CountParams &p, int64_t e0, int
                                            int32_t core_lo_v = 0x7fffffff) {
     constexpr int kPer = Batch<Pos, kThreads>::kPer;
     const int tid = t.tid;
-    int32_t pl[kPer];
+    int32_t pl[kPer], ct[kPer];
     Pos src[kPer];
     int64_t b[kPer];
     bool has[kPer];
@@ -382,6 +383,7 @@ __device__ __forceinline__ void batch_runs(const CountParams &p, int64_t e0, int
         // run of ends: prefix of N(v) below x (Algorithm 2) or the
         // suffix above both x and v (Algorithm 3)
         b[i] = has[i] ? __ldg(p.sbeg + bs.e[i]) : 0;
+        ct[i] = (kDense && has[i] && p.ctb) ? __ldg(p.ctb + bs.e[i]) : -1;
     }
     // a core start: a core middle's run stops before its core ends (they are
     // the top of the run, and the product counts those wedges)
@@ -396,10 +398,17 @@ __device__ __forceinline__ void batch_runs(const CountParams &p, int64_t e0, int
         s0[i] = 0;
         s1[i] = pl[i];
         if (kDense && has[i] && pl[i] > 0) {
+            const int32_t v = bs.v[i];
+            int64_t tb = -1;
             if (p.coff) {
-                const int32_t v = bs.v[i];
-                const int64_t tb = v < p.l ? (int64_t)v * p.coff_u1
-                                           : (int64_t)p.l * p.coff_u1 + (int64_t)(v - p.l) * p.coff_l1;
+                if (p.ctb) {   // a batch: entries only for the middles of its chunked dense starts
+                    tb = ct[i];
+                } else {
+                    tb = v < p.l ? (int64_t)v * p.coff_u1
+                                 : (int64_t)p.l * p.coff_u1 + (int64_t)(v - p.l) * p.coff_l1;
+                }
+            }
+            if (tb >= 0) {
                 if (flags & 1) s0[i] = __ldg(p.coff + tb + lo / kChunkUnit);
                 if (flags & 2) s1[i] = __ldg(p.coff + tb + hi / kChunkUnit);
                 if (core_lo_v != 0x7fffffff) {   // chunk bounds past a shortened run
@@ -1272,6 +1281,7 @@ int launch_count(Graph *g, cudaStream_t s, int mode, unsigned long long *pv_proj
     // is where Algorithm 2's runs start
     p.coff = g->opt.orientation == 0 ? g->coff : nullptr;
     p.coff_u1 = g->coff_u1; p.coff_l1 = g->coff_l1;
+    p.ctb = g->ctb;
     p.gstar = g->gstar; p.vbase = g->vbase; p.vend = g->vend; p.sbeg = g->sbeg; p.gtot = gtot;
     p.retry = g->retry; p.retry_cap = g->retry_cap; p.retry_static = g->retry_static;
     p.retry_on = g->may_retry ? 1 : 0;

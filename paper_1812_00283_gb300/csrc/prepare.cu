@@ -582,6 +582,83 @@ __global__ void k_coff_slots(const int64_t *__restrict__ off, const int32_t *__r
     }
 }
 
+// A batch's table.  The middles of every dense start with several chunks
+// (one warp per start: its cut[x] lower-priority neighbours).
+__global__ void k_coff_mark(const int32_t *__restrict__ order, int64_t n_dense, const int64_t *__restrict__ nch,
+                            const int64_t *__restrict__ off, const int32_t *__restrict__ adj,
+                            const int32_t *__restrict__ cut, int32_t *mark) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = w0; i < n_dense; i += nw) {
+        if (nch[i] <= 1) continue;
+        const int32_t x = order[i];
+        const int64_t e0 = off[x];
+        for (int64_t e = e0 + lane; e < e0 + cut[x]; e += 32) mark[adj[e]] = 1;
+    }
+}
+
+// entries of a marked v: the chunks of its graph's neighbour layer, plus one
+// (the neighbours' layer range is that of any neighbour w: vend[w] - vbase[w])
+__global__ void k_coff_sizes(const int32_t *__restrict__ mark, const int64_t *__restrict__ off,
+                             const int32_t *__restrict__ adj, const int32_t *__restrict__ vbase,
+                             const int32_t *__restrict__ vend, int32_t n, int64_t *cnt) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        int64_t c = 0;
+        if (mark[v] && off[v + 1] > off[v]) {
+            const int32_t w = adj[off[v]];
+            c = (int64_t)(vend[w] - vbase[w] + kChunkUnit - 1) / kChunkUnit + 1;
+        }
+        cnt[v] = c;
+    }
+}
+
+// every entry of v starts at "past the end of N(v)"
+__global__ void k_coff_fill_var(const int64_t *__restrict__ off, const int64_t *__restrict__ cstart, int32_t n,
+                                int32_t *coff) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t d = (int32_t)(off[v + 1] - off[v]);
+        for (int64_t c = cstart[v]; c < cstart[v + 1]; ++c) coff[c] = d;
+    }
+}
+
+// entry c of a marked v = first position in N(v) whose neighbour id is at
+// least (first id of the neighbours' graph range) + c * unit
+__global__ void k_coff_slots_var(const int64_t *__restrict__ off, const int32_t *__restrict__ adj,
+                                 const int32_t *__restrict__ rows, int64_t slots,
+                                 const int32_t *__restrict__ vbase, const int64_t *__restrict__ cstart,
+                                 int32_t *coff) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < slots;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t v = rows[p];
+        const int64_t tb = cstart[v], te = cstart[v + 1];
+        if (te == tb) continue;
+        const int64_t b = off[v];
+        const int32_t lbe = vbase[adj[b]];
+        const int32_t cp = (adj[p] - lbe) / kChunkUnit;
+        const int32_t cprev = p == b ? -1 : (adj[p - 1] - lbe) / kChunkUnit;
+        for (int32_t c = cprev + 1; c <= cp && tb + c < te; ++c) coff[tb + c] = (int32_t)(p - b);
+    }
+}
+
+// the first entry of each middle of those starts, at the middle's slot
+__global__ void k_coff_slot_bases(const int32_t *__restrict__ order, int64_t n_dense,
+                                  const int64_t *__restrict__ nch, const int64_t *__restrict__ off,
+                                  const int32_t *__restrict__ adj, const int32_t *__restrict__ cut,
+                                  const int64_t *__restrict__ cstart, int32_t *ctb) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = w0; i < n_dense; i += nw) {
+        if (nch[i] <= 1) continue;
+        const int32_t x = order[i];
+        const int64_t e0 = off[x];
+        for (int64_t e = e0 + lane; e < e0 + cut[x]; e += 32) ctb[e] = (int32_t)cstart[adj[e]];
+    }
+}
+
 unsigned grid_stride_blocks(int64_t n) {
     int64_t b = (n + kT - 1) / kT;
     if (b > 152 * 64) b = 152 * 64;
@@ -748,7 +825,49 @@ static int schedule_graph(Graph *g, cudaStream_t s, int32_t warp_max_work, int32
         const int32_t u1 = (int32_t)((r + kChunkUnit - 1) / kChunkUnit) + 1;
         const int32_t l1 = (int32_t)((l + kChunkUnit - 1) / kChunkUnit) + 1;
         const int64_t entries = (int64_t)l * u1 + (int64_t)r * l1;
-        // (not for batches: their chunks are relative to each graph's rank range)
+        if (!g->coff && g->num_graphs > 0 && h_dense_items > n_dense) {
+            // a batch: entries only for the middles of starts with several
+            // chunks, as many as the chunks of their graph's neighbour layer
+            // (+1), found through a per-vertex start array
+            int32_t *mark;
+            int64_t *ecnt;
+            GET(tmp, mark, n);
+            GET(tmp, ecnt, (int64_t)n + 1);
+            GET(g->mem, g->coff_start, (int64_t)n + 1);
+            BFC_CUDA(cudaMemsetAsync(mark, 0, sizeof(int32_t) * (size_t)n, s));
+            k_coff_mark<<<grid_stride_blocks(n_dense * 32), kT, 0, s>>>(order, n_dense, nch, g->off, g->adj,
+                                                                         g->cut, mark); note_launch();
+            k_coff_sizes<<<grid_stride_blocks(n), kT, 0, s>>>(mark, g->off, g->adj, g->vbase, g->vend, n, ecnt); note_launch();
+            BFC_CUDA(cudaGetLastError());
+            BFC_CUDA(scan_exclusive<int64_t>(ecnt, g->coff_start, n, scan64_tmp, s));
+            int64_t ventries = 0;
+            BFC_CUDA(cudaMemcpyAsync(&ventries, g->coff_start + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+            BFC_CUDA(cudaStreamSynchronize(s));
+            if (ventries <= kChunkTableMaxEntries) {   // else searches
+                if (!rows_star) {
+                    int32_t *rs;
+                    GET(tmp, rs, 2 * m);
+                    k_rows_from_off<<<grid_stride_blocks((int64_t)n * 32), kT, 0, s>>>(g->off, n, rs); note_launch();
+                    BFC_CUDA(cudaGetLastError());
+                    rows_star = rs;
+                }
+                GET(g->mem, g->coff, std::max<int64_t>(ventries, 1));
+                k_coff_fill_var<<<grid_stride_blocks(n), kT, 0, s>>>(g->off, g->coff_start, n, g->coff); note_launch();
+                BFC_CUDA(cudaGetLastError());
+                k_coff_slots_var<<<grid_stride_blocks(2 * m), kT, 0, s>>>(g->off, g->adj, rows_star, 2 * m,
+                                                                          g->vbase, g->coff_start, g->coff); note_launch();
+                BFC_CUDA(cudaGetLastError());
+                // each middle slot of those starts holds its middle's first
+                // entry (-1 elsewhere), read with the slot's other arrays
+                GET(g->mem, g->ctb, 2 * m);
+                BFC_CUDA(cudaMemsetAsync(g->ctb, 0xff, sizeof(int32_t) * (size_t)(2 * m), s));
+                k_coff_slot_bases<<<grid_stride_blocks(n_dense * 32), kT, 0, s>>>(order, n_dense, nch, g->off, g->adj,
+                                                                                   g->cut, g->coff_start, g->ctb); note_launch();
+                BFC_CUDA(cudaGetLastError());
+            }
+            g->mem.drop(g->coff_start);
+            g->coff_start = nullptr;
+        }
         if (!g->coff && g->num_graphs == 0 && h_dense_items > n_dense && entries <= kChunkTableMaxEntries) {
             if (!rows_star) {
                 int32_t *rs;
@@ -762,7 +881,8 @@ static int schedule_graph(Graph *g, cudaStream_t s, int32_t warp_max_work, int32
             g->coff_l1 = l1;
             k_coff_fill<<<grid_stride_blocks(entries), kT, 0, s>>>(g->off, l, u1, l1, entries, g->coff); note_launch();
             BFC_CUDA(cudaGetLastError());
-            k_coff_slots<<<grid_stride_blocks(2 * m), kT, 0, s>>>(g->off, g->adj, rows_star, 2 * m, l, u1, l1, g->coff); note_launch();
+            k_coff_slots<<<grid_stride_blocks(2 * m), kT, 0, s>>>(g->off, g->adj, rows_star, 2 * m, l, u1, l1,
+                                                                  g->coff); note_launch();
             BFC_CUDA(cudaGetLastError());
         }
     } else {

@@ -71,6 +71,29 @@ def test_batch_totals_match_oracle(opts):
     assert whole == sum(r["total"] for r in refs)
 
 
+@pytest.mark.parametrize("opts", [{}, dict(warp_max_work=0, hash_max_work=0)])
+def test_batch_chunked_dense_items_match_oracle(opts):
+    # layers above 98,304 vertices in two graphs of different shapes: heavy
+    # starts count their ends in several dense chunks, whose run bounds come
+    # from the chunk-boundary table relative to each graph's range
+    from paper_1812_00283_gb300 import bfc
+    graphs = [G.complete_bipartite(3, 4),
+              G.chung_lu_bipartite(150_000, 5_000, 400_000, 1.8, 2.5, 71),
+              G.chung_lu_bipartite(200, 300, 2_000, 2.1, 2.1, 72),
+              G.chung_lu_bipartite(6_000, 120_000, 300_000, 2.5, 1.8, 73),
+              G.from_edges(4, 5, [], [])]
+    b = G.union_batch(graphs)
+    h, keep = _prepare(b, bfc.bfc_options_init(**opts) if opts else None)
+    try:
+        info = bfc.bfc_graph_info(h)
+        tot, whole = _count(h, b.num_graphs)
+    finally:
+        bfc.bfc_release(h)
+    refs = [oracle.vp(g)["total"] for g in graphs]
+    assert info["dense_items"] > info["dense_starts"] > 0
+    assert [int(x) for x in tot] == refs and whole == sum(refs)
+
+
 def test_batch_autotune_and_graph_capture():
     from paper_1812_00283_gb300 import bfc
     graphs = _batch_graphs(k=60, seed=1)
