@@ -31,8 +31,16 @@ constexpr int kTeamSlots = 4096;                          // team hash: 16 KB ke
 constexpr int kTeamFitWork = kTeamSlots / 4 * 3;          // 3,072: a start this light always fits a team table
 constexpr int kTeamMaxWork = 16384;                       // upper limit of team_max_work
 constexpr uint32_t kNarrowMaxCut = 65535;                 // counts fit 16 bits when cut <= this
+constexpr int kDense8 = kCounterBytes;                    // 196,608 packed 8-bit counters
+constexpr uint32_t kByteMaxCut = 255;                     // counts fit 8 bits when cut <= this
 constexpr int kChunkUnit = kDense32;                      // end-range chunk unit of the boundary table
 static_assert(kDense16 % kChunkUnit == 0, "narrow chunks must be whole table units");
+static_assert(kDense8 % kChunkUnit == 0, "byte chunks must be whole table units");
+// the end-range chunk of a dense start whose counts are at most `bound` (its
+// middles): 32-bit, 16-bit or 8-bit counters in the same shared memory
+__host__ __device__ constexpr int32_t dense_chunk_span(int64_t bound) {
+    return bound > (int64_t)kNarrowMaxCut ? kDense32 : (bound > (int64_t)kByteMaxCut ? kDense16 : kDense8);
+}
 constexpr int64_t kChunkTableMaxEntries = 1ll << 29;      // 2 GB of int32 at most
 
 // device error bits (graph-owned error word)

@@ -16,9 +16,11 @@
 // (Section 6.2's dynamic scheduling with the exact per-start work):
 //   A. CTA items, the whole CTA on one item:
 //      dense (u, c)  count_wedge is a dense array over the c-th chunk of u's
-//                    end range (16-bit counts when at most 65,535 middles,
-//                    else 32-bit).  Chunks split the END range, so every pair
-//                    is aggregated by exactly one item and C(count, 2) is
+//                    end range (8-bit counts when at most 255 middles,
+//                    16-bit when at most 65,535, else 32-bit: the same
+//                    shared memory holds 196,608, 98,304 or 49,152 of
+//                    them).  Chunks split the END range, so every pair is
+//                    aggregated by exactly one item and C(count, 2) is
 //                    never split;
 //      hash (u)      an open-addressing table of up to 32,768 slots.
 //      Without a second walk the dense items are streamed: each item takes
@@ -257,7 +259,30 @@ __device__ __forceinline__ uint32_t get16(const uint32_t *w32, int idx) {
     return (w32[idx >> 1] >> sh) & 0xffffu;
 }
 
-enum CounterKind { kDenseNarrow = 0, kDenseWide = 1, kHash = 2 };
+// 8-bit counters packed four per 32-bit word (a start whose counts stay below 256)
+__device__ __forceinline__ uint32_t inc8(uint32_t *w32, int idx) {
+    const uint32_t sh = (uint32_t)(idx & 3) << 3;
+    uint32_t old = atomicAdd(w32 + (idx >> 2), 1u << sh);
+    return (old >> sh) & 0xffu;
+}
+__device__ __forceinline__ uint32_t get8(const uint32_t *w32, int idx) {
+    const uint32_t sh = (uint32_t)(idx & 3) << 3;
+    return (w32[idx >> 2] >> sh) & 0xffu;
+}
+
+enum CounterKind { kDenseNarrow = 0, kDenseWide = 1, kHash = 2, kDenseByte = 3 };
+
+// the dense counter kind of a start with at most `bound` middles, its chunk
+// span (dense_chunk_span) and the bytes to clear for `span` counters
+__device__ __forceinline__ int dense_kind(int64_t bound) {
+    return bound > (int64_t)kNarrowMaxCut ? kDenseWide : (bound > (int64_t)kByteMaxCut ? kDenseNarrow : kDenseByte);
+}
+__device__ __forceinline__ int dense_clear_bytes(int kind, int32_t span) {
+    return kind == kDenseWide ? span * 4 : (kind == kDenseNarrow ? ((span + 1) >> 1) * 4 : ((span + 3) >> 2) * 4);
+}
+__device__ __forceinline__ uint32_t dense_get(int kind, const uint32_t *w32, int idx) {
+    return kind == kDenseWide ? w32[idx] : (kind == kDenseNarrow ? get16(w32, idx) : get8(w32, idx));
+}
 
 // The counter operation for one wedge whose end id is w and whose end sits at
 // adjacency slot pos.  First walk: increment count_wedge(w), return the old
@@ -291,8 +316,9 @@ __device__ __forceinline__ unsigned long long wedge_op(const CountParams &p, int
     } else {
         const int idx = w - lb - lo;
         if ((uint32_t)idx >= (uint32_t)span) { atomicOr(p.err, kErrBounds); return 0; }
-        if (!kSecond) return (KIND == kDenseWide) ? atomicAdd(w32 + idx, 1u) : inc16(w32, idx);
-        c = (KIND == kDenseWide) ? w32[idx] : get16(w32, idx);
+        if (!kSecond)
+            return (KIND == kDenseWide) ? atomicAdd(w32 + idx, 1u) : (KIND == kDenseByte ? inc8(w32, idx) : inc16(w32, idx));
+        c = (KIND == kDenseWide) ? w32[idx] : (KIND == kDenseByte ? get8(w32, idx) : get16(w32, idx));
     }
     // δ = count − 1 for the edge (middle, w); the caller sums it per middle
     const unsigned long long delta = (unsigned long long)c - 1ull;
@@ -696,12 +722,13 @@ __device__ __forceinline__ void end_contributions(const CountParams &p, int32_t 
             }
         }
     } else {
-        // 16 bytes per thread and step (8 narrow or 4 wide counters);
+        // 16 bytes per thread and step (16 byte, 8 narrow or 4 wide counters);
         // a word whose counts are all below 2 adds nothing.  The
         // clear before the walk covered whole 16-byte words.
         const uint4 *q4 = reinterpret_cast<const uint4 *>(ctr);
-        constexpr int kPerQ = (KIND == kDenseWide) ? 4 : 8;
-        constexpr uint32_t kAtLeast2 = (KIND == kDenseWide) ? 0xFFFFFFFEu : 0xFFFEFFFEu;
+        constexpr int kPerQ = (KIND == kDenseWide) ? 4 : (KIND == kDenseByte ? 16 : 8);
+        constexpr uint32_t kAtLeast2 = (KIND == kDenseWide) ? 0xFFFFFFFEu
+                                                            : (KIND == kDenseByte ? 0xFEFEFEFEu : 0xFFFEFFFEu);
         const int32_t span = hi - lo;
         unsigned long long *pvb = p.pv + lb + lo;
         for (int32_t j = t.tid; j * kPerQ < span; j += kThreads) {
@@ -713,6 +740,13 @@ __device__ __forceinline__ void end_contributions(const CountParams &p, int32_t 
                 if (KIND == kDenseWide) {
                     const int32_t i = j * 4 + k;
                     if (wv[k] >= 2 && i < span) atomicAdd(pvb + i, c2(wv[k]));
+                } else if (KIND == kDenseByte) {
+#pragma unroll
+                    for (int bb = 0; bb < 4; ++bb) {
+                        const int32_t i = j * 16 + 4 * k + bb;
+                        const uint32_t c = (wv[k] >> (8 * bb)) & 0xFFu;
+                        if (c >= 2 && i < span) atomicAdd(pvb + i, c2(c));
+                    }
                 } else {
                     const int32_t i = j * 8 + 2 * k;
                     const uint32_t c0 = wv[k] & 0xFFFFu, c1 = wv[k] >> 16;
@@ -777,8 +811,8 @@ template <int MODE, typename Pos, class SH>
 __device__ unsigned long long dense_all_chunks(const CountParams &p, int32_t x, unsigned char *ctr,
                                                SH &sh, const Team<kCountThreads> &t) {
     const int32_t lb = range_lo(p, x);
-    const bool wide = middles(p, x) > (int64_t)kNarrowMaxCut;
-    const int32_t S = wide ? kDense32 : kDense16;
+    const int kind = dense_kind(middles(p, x));
+    const int32_t S = dense_chunk_span(middles(p, x));
     const int32_t first = p.orient ? x + 1 - lb : 0;
     const int32_t last = p.orient ? range_hi(p, x) - lb : x - lb;   // ends in [lb + first, lb + last)
     unsigned long long acc = 0;
@@ -786,10 +820,11 @@ __device__ unsigned long long dense_all_chunks(const CountParams &p, int32_t x, 
         const int32_t lo = max(c * S, first), hi = min((c + 1) * S, last);
         const int32_t span = hi - lo;
         const int flags = (lo > first ? 1 : 0) | (hi < last ? 2 : 0);
-        team_fill(ctr, wide ? span * 4 : ((span + 1) >> 1) * 4, 0u, t);
+        team_fill(ctr, dense_clear_bytes(kind, span), 0u, t);
         t.sync();
-        acc += wide ? item_body<MODE, kDenseWide, Pos>(p, x, lb, lo, hi, flags, 0, ctr, sh, t)
-                    : item_body<MODE, kDenseNarrow, Pos>(p, x, lb, lo, hi, flags, 0, ctr, sh, t);
+        acc += kind == kDenseWide ? item_body<MODE, kDenseWide, Pos>(p, x, lb, lo, hi, flags, 0, ctr, sh, t)
+             : kind == kDenseNarrow ? item_body<MODE, kDenseNarrow, Pos>(p, x, lb, lo, hi, flags, 0, ctr, sh, t)
+                                    : item_body<MODE, kDenseByte, Pos>(p, x, lb, lo, hi, flags, 0, ctr, sh, t);
         t.sync();
     }
     return acc;
@@ -820,16 +855,17 @@ __device__ unsigned long long cta_item(const CountParams &p, int2 item, unsigned
     if (item.y >= 0) {          // dense items exist only for Algorithm 2
         const int32_t lb = range_lo(p, x);
         const int32_t R = x - lb;   // the ends are the R vertices below x
-        const bool wide = (uint32_t)p.cut[x] > kNarrowMaxCut;
-        const int32_t S = wide ? kDense32 : kDense16;
+        const int kind = dense_kind(p.cut[x]);
+        const int32_t S = dense_chunk_span(p.cut[x]);
         const int32_t lo = item.y * S;
         const int32_t hi = min(R, lo + S);
         const int32_t span = hi - lo;
         const int flags = (lo > 0 ? 1 : 0) | (hi < R ? 2 : 0);
-        team_fill(ctr, wide ? span * 4 : ((span + 1) >> 1) * 4, 0u, t);
+        team_fill(ctr, dense_clear_bytes(kind, span), 0u, t);
         t.sync();
-        acc = wide ? item_body<MODE, kDenseWide, Pos>(p, x, lb, lo, hi, flags, 0, ctr, sh, t)
-                   : item_body<MODE, kDenseNarrow, Pos>(p, x, lb, lo, hi, flags, 0, ctr, sh, t);
+        acc = kind == kDenseWide ? item_body<MODE, kDenseWide, Pos>(p, x, lb, lo, hi, flags, 0, ctr, sh, t)
+            : kind == kDenseNarrow ? item_body<MODE, kDenseNarrow, Pos>(p, x, lb, lo, hi, flags, 0, ctr, sh, t)
+                                   : item_body<MODE, kDenseByte, Pos>(p, x, lb, lo, hi, flags, 0, ctr, sh, t);
     } else {
         acc = hash_item<MODE, Pos>(p, x, ctr, kHashMaxSlots, sh, t);
         if (sh.overflow) {
@@ -863,8 +899,8 @@ __device__ unsigned long long dense_stream(const CountParams &p, int64_t &it, un
         const int32_t x = item.x;
         const int32_t lb = range_lo(p, x);
         const int32_t R = x - lb;   // the ends are the R vertices below x
-        const bool wide = (uint32_t)p.cut[x] > kNarrowMaxCut;
-        const int32_t S = wide ? kDense32 : kDense16;
+        const int kind = dense_kind(p.cut[x]);
+        const int32_t S = dense_chunk_span(p.cut[x]);
         const int32_t lo = item.y * S;
         const int32_t hi = min(R, lo + S);
         const int32_t span = hi - lo;
@@ -887,14 +923,18 @@ __device__ unsigned long long dense_stream(const CountParams &p, int64_t &it, un
             BatchSlots<Pos, kCountThreads> bs;
             int32_t total;
             int nnz;
-            const int zero_bytes = mb > 0 ? 0 : (wide ? span * 4 : ((span + 1) >> 1) * 4);
+            const int zero_bytes = mb > 0 ? 0 : dense_clear_bytes(kind, span);
             batch_runs<true, false, Pos>(p, e0, nmid, mb, lb, lo, hi, flags, ctr, zero_bytes, sh, t, bs,
                                          &total, &nnz, core_lo_v);
             t.sync();
-            item_acc += wide ? batch_windows<MODE, kDenseWide, false, Pos>(p, lb, lo, span, 0, ctr, total,
-                                                                          nnz, nullptr, sh, t)
-                             : batch_windows<MODE, kDenseNarrow, false, Pos>(p, lb, lo, span, 0, ctr, total,
-                                                                            nnz, nullptr, sh, t);
+            item_acc += kind == kDenseWide
+                            ? batch_windows<MODE, kDenseWide, false, Pos>(p, lb, lo, span, 0, ctr, total, nnz,
+                                                                          nullptr, sh, t)
+                        : kind == kDenseNarrow
+                            ? batch_windows<MODE, kDenseNarrow, false, Pos>(p, lb, lo, span, 0, ctr, total, nnz,
+                                                                            nullptr, sh, t)
+                            : batch_windows<MODE, kDenseByte, false, Pos>(p, lb, lo, span, 0, ctr, total, nnz,
+                                                                          nullptr, sh, t);
             mb += kB;
         } while (mb < nmid);
         if (core_x) {
@@ -913,7 +953,7 @@ __device__ unsigned long long dense_stream(const CountParams &p, int64_t &it, un
             for (int32_t w = max(lb + lo, clo_x) + t.tid; w < w_hi; w += kCountThreads) {
                 const unsigned long long a = __ldg(arow + (w - clo_x));
                 const int idx = w - lb - lo;
-                const unsigned long long b = wide ? w32[idx] : get16(w32, idx);
+                const unsigned long long b = dense_get(kind, w32, idx);
                 e += a * b + (a * (a - 1)) / 2;   // a = 0 gives 0
             }
             item_acc += e;

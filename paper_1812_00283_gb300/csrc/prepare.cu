@@ -507,7 +507,7 @@ __global__ void k_classify(const uint64_t *__restrict__ work, int32_t n, uint64_
 __device__ __forceinline__ int32_t dense_chunks(int32_t x, int32_t l, int32_t cut,
                                                 const int32_t *vbase) {
     const int64_t R = x - (vbase ? vbase[x] : (x >= l ? l : 0));
-    const int64_t S = cut > (int32_t)kNarrowMaxCut ? kDense32 : kDense16;
+    const int64_t S = dense_chunk_span(cut);
     return (int32_t)((R + S - 1) / S);
 }
 

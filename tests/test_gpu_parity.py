@@ -207,6 +207,16 @@ def test_multi_chunk_end_ranges(wide):
     assert got["info"]["dense_items"] > got["info"]["dense_starts"]
 
 
+@pytest.mark.parametrize("opts", [{}, dict(warp_max_work=0, hash_max_work=0)])
+def test_byte_counter_chunks(opts):
+    # dense starts with at most 255 middles count in 8-bit counters: a
+    # 400k-vertex U layer spans several 196,608-counter chunks (46 such
+    # starts with the default bins)
+    g = G.chung_lu_bipartite(400_000, 2_000, 3_000_000, 2.5, 1.8, 91, max_u=2000)
+    got, ref = _check_against_oracle(g, _opts(**opts))
+    assert got["info"]["dense_items"] > got["info"]["dense_starts"]
+
+
 @pytest.mark.parametrize("wide", [0, 1])
 def test_multi_chunk_retry_pass(wide):
     # Algorithm 3 with every start sent to the chunked dense pass: low starts
