@@ -41,6 +41,24 @@ static_assert(kDense8 % kChunkUnit == 0, "byte chunks must be whole table units"
 __host__ __device__ constexpr int32_t dense_chunk_span(int64_t bound) {
     return bound > (int64_t)kNarrowMaxCut ? kDense32 : (bound > (int64_t)kByteMaxCut ? kDense16 : kDense8);
 }
+// Algorithm 2's dense chunk of start x that begins at end offset lo (a
+// multiple of kChunkUnit) of its end range [lb, lb + R) in G*: the widest span
+// whose counters hold every count in it.  count_wedge(x, w) is at most
+// min(cut[x], deg(w)), and within a layer G* orders vertices by Definition 3's
+// priority, so degrees do not decrease with the id and the chunk's last end
+// bounds every count of the chunk.  Returns the chunk's end; *bits = 8, 16 or
+// 32.  `off` is G*'s offset array.
+__device__ __forceinline__ int32_t dense_chunk_end(int32_t lo, int32_t R, int64_t cut, const int64_t *off,
+                                                   int32_t lb, int *bits) {
+    int32_t hi = (int32_t)((int64_t)lo + kDense8 < R ? lo + kDense8 : R);
+    int64_t top = off[lb + hi] - off[lb + hi - 1];
+    if ((cut < top ? cut : top) <= (int64_t)kByteMaxCut) { *bits = 8; return hi; }
+    hi = (int32_t)((int64_t)lo + kDense16 < R ? lo + kDense16 : R);
+    top = off[lb + hi] - off[lb + hi - 1];
+    if ((cut < top ? cut : top) <= (int64_t)kNarrowMaxCut) { *bits = 16; return hi; }
+    *bits = 32;
+    return (int32_t)((int64_t)lo + kDense32 < R ? lo + kDense32 : R);
+}
 constexpr int64_t kChunkTableMaxEntries = 1ll << 29;      // 2 GB of int32 at most
 
 // device error bits (graph-owned error word)

@@ -15,13 +15,14 @@
 // shared memory.  Three phases, each fed by its own queue, heaviest first
 // (Section 6.2's dynamic scheduling with the exact per-start work):
 //   A. CTA items, the whole CTA on one item:
-//      dense (u, c)  count_wedge is a dense array over the c-th chunk of u's
-//                    end range (8-bit counts when at most 255 middles,
-//                    16-bit when at most 65,535, else 32-bit: the same
-//                    shared memory holds 196,608, 98,304 or 49,152 of
-//                    them).  Chunks split the END range, so every pair is
-//                    aggregated by exactly one item and C(count, 2) is
-//                    never split;
+//      dense (u, lo) count_wedge is a dense array over the chunk of u's end
+//                    range that starts at offset lo: 8-bit counts when
+//                    every count of the chunk is at most 255, 16-bit when at
+//                    most 65,535, else 32-bit (the same shared memory holds
+//                    196,608, 98,304 or 49,152 of them; a count is at most
+//                    min(cut[u], deg of the chunk's last end)).  Chunks
+//                    split the END range, so every pair is aggregated by
+//                    exactly one item and C(count, 2) is never split;
 //      hash (u)      an open-addressing table of up to 32,768 slots.
 //      Without a second walk the dense items are streamed: each item takes
 //      the next from the queue and clears the counters inside its first
@@ -855,10 +856,10 @@ __device__ unsigned long long cta_item(const CountParams &p, int2 item, unsigned
     if (item.y >= 0) {          // dense items exist only for Algorithm 2
         const int32_t lb = range_lo(p, x);
         const int32_t R = x - lb;   // the ends are the R vertices below x
-        const int kind = dense_kind(p.cut[x]);
-        const int32_t S = dense_chunk_span(p.cut[x]);
-        const int32_t lo = item.y * S;
-        const int32_t hi = min(R, lo + S);
+        const int32_t lo = item.y;   // the chunk's first end offset
+        int bits;
+        const int32_t hi = dense_chunk_end(lo, R, p.cut[x], p.off, lb, &bits);
+        const int kind = bits == 32 ? kDenseWide : (bits == 16 ? kDenseNarrow : kDenseByte);
         const int32_t span = hi - lo;
         const int flags = (lo > 0 ? 1 : 0) | (hi < R ? 2 : 0);
         team_fill(ctr, dense_clear_bytes(kind, span), 0u, t);
@@ -899,10 +900,10 @@ __device__ unsigned long long dense_stream(const CountParams &p, int64_t &it, un
         const int32_t x = item.x;
         const int32_t lb = range_lo(p, x);
         const int32_t R = x - lb;   // the ends are the R vertices below x
-        const int kind = dense_kind(p.cut[x]);
-        const int32_t S = dense_chunk_span(p.cut[x]);
-        const int32_t lo = item.y * S;
-        const int32_t hi = min(R, lo + S);
+        const int32_t lo = item.y;   // the chunk's first end offset
+        int bits;
+        const int32_t hi = dense_chunk_end(lo, R, p.cut[x], p.off, lb, &bits);
+        const int kind = bits == 32 ? kDenseWide : (bits == 16 ? kDenseNarrow : kDenseByte);
         const int32_t span = hi - lo;
         const int flags = (lo > 0 ? 1 : 0) | (hi < R ? 2 : 0);
         const int64_t e0 = p.off[x];

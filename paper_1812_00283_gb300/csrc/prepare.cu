@@ -504,26 +504,35 @@ __global__ void k_classify(const uint64_t *__restrict__ work, int32_t n, uint64_
     }
 }
 
-__device__ __forceinline__ int32_t dense_chunks(int32_t x, int32_t l, int32_t cut,
-                                                const int32_t *vbase) {
-    const int64_t R = x - (vbase ? vbase[x] : (x >= l ? l : 0));
-    const int64_t S = dense_chunk_span(cut);
-    return (int32_t)((R + S - 1) / S);
+// the dense chunks of start x (dense_chunk_end from offset 0 up); with `out`,
+// each chunk's item (x, first end offset) is written there
+__device__ __forceinline__ int32_t dense_chunks(int32_t x, int32_t l, int32_t cut, const int64_t *off,
+                                                const int32_t *vbase, int2 *out = nullptr) {
+    const int32_t lb = vbase ? vbase[x] : (x >= l ? l : 0);
+    const int32_t R = x - lb;
+    int32_t k = 0;
+    for (int32_t lo = 0; lo < R; ++k) {
+        int bits;
+        const int32_t hi = dense_chunk_end(lo, R, cut, off, lb, &bits);
+        if (out) out[k] = make_int2(x, lo);
+        lo = hi;
+    }
+    return k;
 }
 
 __global__ void k_chunk_counts(const int32_t *__restrict__ order, int64_t n_dense, int32_t l,
-                               const int32_t *__restrict__ cut, const int32_t *__restrict__ vbase,
-                               int64_t *nch) {
+                               const int32_t *__restrict__ cut, const int64_t *__restrict__ off,
+                               const int32_t *__restrict__ vbase, int64_t *nch) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_dense) return;
     int32_t x = order[i];
-    nch[i] = dense_chunks(x, l, cut[x], vbase);
+    nch[i] = dense_chunks(x, l, cut[x], off, vbase);
 }
 
 // starts in descending work order: dense (chunked), CTA hash, team, warp
 __global__ void k_emit_items(const int32_t *__restrict__ order, int64_t n_dense, int64_t n_hash,
                              int64_t n_team, int64_t n_warp, const int64_t *__restrict__ nch_scan,
-                             int32_t l, const int32_t *__restrict__ cut,
+                             int32_t l, const int32_t *__restrict__ cut, const int64_t *__restrict__ off,
                              const int32_t *__restrict__ vbase, int2 *cta_items,
                              int32_t *team_items, int32_t *warp_items) {
     const int64_t total_dense = nch_scan[n_dense];
@@ -532,9 +541,7 @@ __global__ void k_emit_items(const int32_t *__restrict__ order, int64_t n_dense,
          i += (int64_t)gridDim.x * blockDim.x) {
         int32_t x = order[i];
         if (i < n_dense) {
-            int64_t o = nch_scan[i];
-            int32_t k = dense_chunks(x, l, cut[x], vbase);
-            for (int32_t c = 0; c < k; ++c) cta_items[o + c] = make_int2(x, c);
+            dense_chunks(x, l, cut[x], off, vbase, cta_items + nch_scan[i]);
         } else if (i < n_dense + n_hash) {
             cta_items[total_dense + (i - n_dense)] = make_int2(x, -1);
         } else if (i < n_dense + n_hash + n_team) {
@@ -802,7 +809,7 @@ static int schedule_graph(Graph *g, cudaStream_t s, int32_t warp_max_work, int32
         BFC_CUDA(cudaStreamSynchronize(s));
         n_dense = (int64_t)hc[0]; n_hash = (int64_t)hc[1]; n_team = (int64_t)hc[2]; n_warp = (int64_t)hc[3];
         if (n_dense > 0) {
-            k_chunk_counts<<<blocks_for(n_dense), kT, 0, s>>>(order, n_dense, l, g->cut, g->vbase, nch); note_launch();
+            k_chunk_counts<<<blocks_for(n_dense), kT, 0, s>>>(order, n_dense, l, g->cut, g->off, g->vbase, nch); note_launch();
             BFC_CUDA(cudaGetLastError());
         }
         // the sorted keys are no longer needed; the other key buffer holds the scan
@@ -817,7 +824,7 @@ static int schedule_graph(Graph *g, cudaStream_t s, int32_t warp_max_work, int32
         GET(g->mem, g->warp_items, std::max<int64_t>(n_warp, 1));
         if (n_dense + n_hash + n_team + n_warp > 0) {
             k_emit_items<<<grid_stride_blocks(n_dense + n_hash + n_team + n_warp), kT, 0, s>>>(
-                order, n_dense, n_hash, n_team, n_warp, nch_scan, l, g->cut, g->vbase, g->cta_items,
+                order, n_dense, n_hash, n_team, n_warp, nch_scan, l, g->cut, g->off, g->vbase, g->cta_items,
                 g->team_items, g->warp_items); note_launch();
             BFC_CUDA(cudaGetLastError());
         }
