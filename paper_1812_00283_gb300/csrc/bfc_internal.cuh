@@ -33,9 +33,12 @@ constexpr int kTeamMaxWork = 16384;                       // upper limit of team
 constexpr uint32_t kNarrowMaxCut = 65535;                 // counts fit 16 bits when cut <= this
 constexpr int kDense8 = kCounterBytes;                    // 196,608 packed 8-bit counters
 constexpr uint32_t kByteMaxCut = 255;                     // counts fit 8 bits when cut <= this
+constexpr int kDense4 = kCounterBytes * 2;                // 393,216 packed 4-bit counters
+constexpr uint32_t kNibbleMax = 15;                       // counts fit 4 bits when at most this
 constexpr int kChunkUnit = kDense32;                      // end-range chunk unit of the boundary table
 static_assert(kDense16 % kChunkUnit == 0, "narrow chunks must be whole table units");
 static_assert(kDense8 % kChunkUnit == 0, "byte chunks must be whole table units");
+static_assert(kDense4 % kChunkUnit == 0, "nibble chunks must be whole table units");
 // the end-range chunk of a dense start whose counts are at most `bound` (its
 // middles): 32-bit, 16-bit or 8-bit counters in the same shared memory
 __host__ __device__ constexpr int32_t dense_chunk_span(int64_t bound) {
@@ -46,12 +49,15 @@ __host__ __device__ constexpr int32_t dense_chunk_span(int64_t bound) {
 // whose counters hold every count in it.  count_wedge(x, w) is at most
 // min(cut[x], deg(w)), and within a layer G* orders vertices by Definition 3's
 // priority, so degrees do not decrease with the id and the chunk's last end
-// bounds every count of the chunk.  Returns the chunk's end; *bits = 8, 16 or
-// 32.  `off` is G*'s offset array.
+// bounds every count of the chunk.  Returns the chunk's end; *bits = 4, 8, 16
+// or 32.  `off` is G*'s offset array.
 __device__ __forceinline__ int32_t dense_chunk_end(int32_t lo, int32_t R, int64_t cut, const int64_t *off,
                                                    int32_t lb, int *bits) {
-    int32_t hi = (int32_t)((int64_t)lo + kDense8 < R ? lo + kDense8 : R);
+    int32_t hi = (int32_t)((int64_t)lo + kDense4 < R ? lo + kDense4 : R);
     int64_t top = off[lb + hi] - off[lb + hi - 1];
+    if ((cut < top ? cut : top) <= (int64_t)kNibbleMax) { *bits = 4; return hi; }
+    hi = (int32_t)((int64_t)lo + kDense8 < R ? lo + kDense8 : R);
+    top = off[lb + hi] - off[lb + hi - 1];
     if ((cut < top ? cut : top) <= (int64_t)kByteMaxCut) { *bits = 8; return hi; }
     hi = (int32_t)((int64_t)lo + kDense16 < R ? lo + kDense16 : R);
     top = off[lb + hi] - off[lb + hi - 1];

@@ -16,11 +16,12 @@
 // (Section 6.2's dynamic scheduling with the exact per-start work):
 //   A. CTA items, the whole CTA on one item:
 //      dense (u, lo) count_wedge is a dense array over the chunk of u's end
-//                    range that starts at offset lo: 8-bit counts when
-//                    every count of the chunk is at most 255, 16-bit when at
-//                    most 65,535, else 32-bit (the same shared memory holds
-//                    196,608, 98,304 or 49,152 of them; a count is at most
-//                    min(cut[u], deg of the chunk's last end)).  Chunks
+//                    range that starts at offset lo: 4-bit counts when
+//                    every count of the chunk is at most 15, 8-bit when at
+//                    most 255, 16-bit when at most 65,535, else 32-bit (the
+//                    same shared memory holds 393,216, 196,608, 98,304 or
+//                    49,152 of them; a count is at most min(cut[u], deg of
+//                    the chunk's last end)).  Chunks
 //                    split the END range, so every pair is aggregated by
 //                    exactly one item and C(count, 2) is never split;
 //      hash (u)      an open-addressing table of up to 32,768 slots.
@@ -271,7 +272,18 @@ __device__ __forceinline__ uint32_t get8(const uint32_t *w32, int idx) {
     return (w32[idx >> 2] >> sh) & 0xffu;
 }
 
-enum CounterKind { kDenseNarrow = 0, kDenseWide = 1, kHash = 2, kDenseByte = 3 };
+// 4-bit counters packed eight per 32-bit word (a chunk whose counts stay below 16)
+__device__ __forceinline__ uint32_t inc4(uint32_t *w32, int idx) {
+    const uint32_t sh = (uint32_t)(idx & 7) << 2;
+    uint32_t old = atomicAdd(w32 + (idx >> 3), 1u << sh);
+    return (old >> sh) & 0xfu;
+}
+__device__ __forceinline__ uint32_t get4(const uint32_t *w32, int idx) {
+    const uint32_t sh = (uint32_t)(idx & 7) << 2;
+    return (w32[idx >> 3] >> sh) & 0xfu;
+}
+
+enum CounterKind { kDenseNarrow = 0, kDenseWide = 1, kHash = 2, kDenseByte = 3, kDenseNibble = 4 };
 
 // the dense counter kind of a start with at most `bound` middles, its chunk
 // span (dense_chunk_span) and the bytes to clear for `span` counters
@@ -279,10 +291,16 @@ __device__ __forceinline__ int dense_kind(int64_t bound) {
     return bound > (int64_t)kNarrowMaxCut ? kDenseWide : (bound > (int64_t)kByteMaxCut ? kDenseNarrow : kDenseByte);
 }
 __device__ __forceinline__ int dense_clear_bytes(int kind, int32_t span) {
-    return kind == kDenseWide ? span * 4 : (kind == kDenseNarrow ? ((span + 1) >> 1) * 4 : ((span + 3) >> 2) * 4);
+    return kind == kDenseWide ? span * 4
+         : kind == kDenseNarrow ? ((span + 1) >> 1) * 4
+         : kind == kDenseByte ? ((span + 3) >> 2) * 4 : ((span + 7) >> 3) * 4;
 }
 __device__ __forceinline__ uint32_t dense_get(int kind, const uint32_t *w32, int idx) {
-    return kind == kDenseWide ? w32[idx] : (kind == kDenseNarrow ? get16(w32, idx) : get8(w32, idx));
+    return kind == kDenseWide ? w32[idx]
+         : kind == kDenseNarrow ? get16(w32, idx) : (kind == kDenseByte ? get8(w32, idx) : get4(w32, idx));
+}
+__device__ __forceinline__ int kind_of_bits(int bits) {
+    return bits == 32 ? kDenseWide : (bits == 16 ? kDenseNarrow : (bits == 8 ? kDenseByte : kDenseNibble));
 }
 
 // The counter operation for one wedge whose end id is w and whose end sits at
@@ -318,8 +336,10 @@ __device__ __forceinline__ unsigned long long wedge_op(const CountParams &p, int
         const int idx = w - lb - lo;
         if ((uint32_t)idx >= (uint32_t)span) { atomicOr(p.err, kErrBounds); return 0; }
         if (!kSecond)
-            return (KIND == kDenseWide) ? atomicAdd(w32 + idx, 1u) : (KIND == kDenseByte ? inc8(w32, idx) : inc16(w32, idx));
-        c = (KIND == kDenseWide) ? w32[idx] : (KIND == kDenseByte ? get8(w32, idx) : get16(w32, idx));
+            return (KIND == kDenseWide) ? atomicAdd(w32 + idx, 1u)
+                 : (KIND == kDenseByte) ? inc8(w32, idx) : (KIND == kDenseNibble ? inc4(w32, idx) : inc16(w32, idx));
+        c = (KIND == kDenseWide) ? w32[idx]
+          : (KIND == kDenseByte) ? get8(w32, idx) : (KIND == kDenseNibble ? get4(w32, idx) : get16(w32, idx));
     }
     // δ = count − 1 for the edge (middle, w); the caller sums it per middle
     const unsigned long long delta = (unsigned long long)c - 1ull;
@@ -723,13 +743,14 @@ __device__ __forceinline__ void end_contributions(const CountParams &p, int32_t 
             }
         }
     } else {
-        // 16 bytes per thread and step (16 byte, 8 narrow or 4 wide counters);
+        // 16 bytes per thread and step (32 nibble, 16 byte, 8 narrow or 4 wide counters);
         // a word whose counts are all below 2 adds nothing.  The
         // clear before the walk covered whole 16-byte words.
         const uint4 *q4 = reinterpret_cast<const uint4 *>(ctr);
-        constexpr int kPerQ = (KIND == kDenseWide) ? 4 : (KIND == kDenseByte ? 16 : 8);
+        constexpr int kPerQ = (KIND == kDenseWide) ? 4 : (KIND == kDenseByte ? 16 : (KIND == kDenseNibble ? 32 : 8));
         constexpr uint32_t kAtLeast2 = (KIND == kDenseWide) ? 0xFFFFFFFEu
-                                                            : (KIND == kDenseByte ? 0xFEFEFEFEu : 0xFFFEFFFEu);
+                                     : (KIND == kDenseByte) ? 0xFEFEFEFEu
+                                     : (KIND == kDenseNibble) ? 0xEEEEEEEEu : 0xFFFEFFFEu;
         const int32_t span = hi - lo;
         unsigned long long *pvb = p.pv + lb + lo;
         for (int32_t j = t.tid; j * kPerQ < span; j += kThreads) {
@@ -746,6 +767,14 @@ __device__ __forceinline__ void end_contributions(const CountParams &p, int32_t 
                     for (int bb = 0; bb < 4; ++bb) {
                         const int32_t i = j * 16 + 4 * k + bb;
                         const uint32_t c = (wv[k] >> (8 * bb)) & 0xFFu;
+                        if (c >= 2 && i < span) atomicAdd(pvb + i, c2(c));
+                    }
+                } else if (KIND == kDenseNibble) {
+                    if ((wv[k] & kAtLeast2) == 0) continue;
+#pragma unroll
+                    for (int bb = 0; bb < 8; ++bb) {
+                        const int32_t i = j * 32 + 8 * k + bb;
+                        const uint32_t c = (wv[k] >> (4 * bb)) & 0xFu;
                         if (c >= 2 && i < span) atomicAdd(pvb + i, c2(c));
                     }
                 } else {
@@ -859,14 +888,15 @@ __device__ unsigned long long cta_item(const CountParams &p, int2 item, unsigned
         const int32_t lo = item.y;   // the chunk's first end offset
         int bits;
         const int32_t hi = dense_chunk_end(lo, R, p.cut[x], p.off, lb, &bits);
-        const int kind = bits == 32 ? kDenseWide : (bits == 16 ? kDenseNarrow : kDenseByte);
+        const int kind = kind_of_bits(bits);
         const int32_t span = hi - lo;
         const int flags = (lo > 0 ? 1 : 0) | (hi < R ? 2 : 0);
         team_fill(ctr, dense_clear_bytes(kind, span), 0u, t);
         t.sync();
         acc = kind == kDenseWide ? item_body<MODE, kDenseWide, Pos>(p, x, lb, lo, hi, flags, 0, ctr, sh, t)
             : kind == kDenseNarrow ? item_body<MODE, kDenseNarrow, Pos>(p, x, lb, lo, hi, flags, 0, ctr, sh, t)
-                                   : item_body<MODE, kDenseByte, Pos>(p, x, lb, lo, hi, flags, 0, ctr, sh, t);
+            : kind == kDenseByte ? item_body<MODE, kDenseByte, Pos>(p, x, lb, lo, hi, flags, 0, ctr, sh, t)
+                                 : item_body<MODE, kDenseNibble, Pos>(p, x, lb, lo, hi, flags, 0, ctr, sh, t);
     } else {
         acc = hash_item<MODE, Pos>(p, x, ctr, kHashMaxSlots, sh, t);
         if (sh.overflow) {
@@ -903,7 +933,7 @@ __device__ unsigned long long dense_stream(const CountParams &p, int64_t &it, un
         const int32_t lo = item.y;   // the chunk's first end offset
         int bits;
         const int32_t hi = dense_chunk_end(lo, R, p.cut[x], p.off, lb, &bits);
-        const int kind = bits == 32 ? kDenseWide : (bits == 16 ? kDenseNarrow : kDenseByte);
+        const int kind = kind_of_bits(bits);
         const int32_t span = hi - lo;
         const int flags = (lo > 0 ? 1 : 0) | (hi < R ? 2 : 0);
         const int64_t e0 = p.off[x];
@@ -934,8 +964,11 @@ __device__ unsigned long long dense_stream(const CountParams &p, int64_t &it, un
                         : kind == kDenseNarrow
                             ? batch_windows<MODE, kDenseNarrow, false, Pos>(p, lb, lo, span, 0, ctr, total, nnz,
                                                                             nullptr, sh, t)
-                            : batch_windows<MODE, kDenseByte, false, Pos>(p, lb, lo, span, 0, ctr, total, nnz,
-                                                                          nullptr, sh, t);
+                        : kind == kDenseByte
+                            ? batch_windows<MODE, kDenseByte, false, Pos>(p, lb, lo, span, 0, ctr, total, nnz,
+                                                                          nullptr, sh, t)
+                            : batch_windows<MODE, kDenseNibble, false, Pos>(p, lb, lo, span, 0, ctr, total, nnz,
+                                                                            nullptr, sh, t);
             mb += kB;
         } while (mb < nmid);
         if (core_x) {
