@@ -146,6 +146,24 @@ def test_prepare_arrays(gi):
     assert np.array_equal(got["work"], P["work"])
 
 
+@pytest.mark.parametrize("gi", range(3))
+def test_long_list_graphs(gi):
+    # one side's lists average 256 entries or more (Algorithm 2's run lengths
+    # are searched in long lists): G*, cut, work and every output
+    g = [G.chung_lu_bipartite(60_000, 500, 200_000, 2.5, 1.8, 5),
+         G.chung_lu_bipartite(400, 50_000, 150_000, 1.8, 2.5, 6),
+         G.shuffle_lists(G.complete_bipartite(300, 40), 3)][gi]
+    assert g.num_edges >= 256 * min(g.num_u, g.num_l)
+    got = run_gpu(g, export=True, vertices=True, edges=True)
+    P = oracle.projection(g)
+    for k in ("off", "adj", "eid", "cut", "work"):
+        assert np.array_equal(got[k], P[k]), k
+    ref = oracle.vp(g, vertices=True, edges=True)
+    assert got["total"] == ref["total"] and got["total_all"] == ref["total"]
+    assert np.array_equal(got["all_pv_u"], ref["pv_u"]) and np.array_equal(got["all_pv_l"], ref["pv_l"])
+    assert np.array_equal(got["pe"], ref["pe"]) and np.array_equal(got["all_pe"], ref["pe"])
+
+
 # U lists on both sides of each construction threshold (warp ranking up to 32
 # neighbours, warp sort up to 256, CTA sort up to 4,096, radix above), with
 # repeated degrees so that Definition 3's tie-break decides ranks
